@@ -1,0 +1,395 @@
+"""Benchmark of the G-prox PDHG hot path on one GB300 (or N replicas).
+
+Workload: the 4096 x 4096 ROF problem (noisy disks + rectangle, sigma = 0.1,
+lambda = 8) and the 4096 x 4096 L1-EMD problem (two 8-Gaussian mixtures with a
+1e-3 floor), FP32 state, FP64 gap reductions.  One step = 10 G-prox PDHG
+iterations of each problem including one duality-gap check each (the chunk a
+solve runs between stopping tests).  value = grid-point-iterations per second
+over the whole job (all ranks), inputs resident in HBM.  Every plane is 64 MB
+and each problem's working set is ~1 GB, larger than the 129 MB L2, so no L2
+flush is needed between steps.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Multi-GPU (torchrun): independent replicas,
+one per GPU, timed between barriers (max over ranks).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt-iters/s + time to rel. gap 1e-5 at 4096² (frac. of HBM roofline)"
+UNIT = "grid-pt-iters/s"
+N_DEFAULT = 4096
+ITERS_PER_STEP = 10
+LAMBDA = 8.0
+
+# Algorithmic DRAM bytes per grid point for one launch of each kernel class
+# (FP32 words read + written, each operand touched once).
+BYTES_PER_POINT = {
+    "dct_rows_fwd": 8,     # read b, write row spectrum
+    "dct_cols_solve": 8,   # read + write the plane in place
+    "dct_rows_inv": 8,     # read spectrum, write x
+    "rof_fused": 28,       # read u, p(2), I; write p(2), r
+    "emd_fused": 44,       # read q, s(2), p(2), g; write s(2), p(2), d  (gap steps add m(2), e)
+}
+
+# ncu DRAM traffic (read + write bytes per launch) of the dominant kernel, from
+# the committed profile summary; valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {}
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1805_09453_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _inputs(N):
+    from paper_1805_09453_gb300 import synth
+
+    I = synth.rof_image(N, 0)
+    f0, f1 = synth.gaussian_mixture_pair(N, 1)
+    return I, f0, f1
+
+
+def cpu_baseline_oracle(N, n_iter=1):
+    """The FP64 oracle as it stands, one iteration of each problem at N (bounded sample)."""
+    import numpy as np
+
+    from oracle import gprox_oracle as O
+
+    I, f0, f1 = _inputs(N)
+    t0 = time.perf_counter()
+    tau, sigma, _ = O.rof_step_rule(I, LAMBDA)
+    st = O.rof_init(I)
+    t1 = time.perf_counter()
+    O.rof_iterate(st, I.astype(np.float64), LAMBDA, tau, sigma, n_iter)
+    t2 = time.perf_counter()
+    se = O.emd_init(f0, f1)
+    t3 = time.perf_counter()
+    O.emd_iterate(se, 1.0, 1.0, n_iter)
+    t4 = time.perf_counter()
+    secs = (t2 - t1) + (t4 - t3)
+    return {"value": 2 * n_iter * N * N / secs, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{n_iter} FP64 oracle iteration(s) of ROF and of EMD at {N}x{N} (setup excluded), "
+                      f"scipy.fft with all {os.cpu_count()} host threads",
+            "seconds": secs}
+
+
+def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle as it stands, on the host cores."""
+    import numpy as np
+
+    from oracle import gprox_oracle as O
+
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    N = args.size
+    I, f0, f1 = _inputs(N)
+    I64 = I.astype(np.float64)
+    tau, sigma, _ = O.rof_step_rule(I, LAMBDA)
+    sr = O.rof_init(I64)
+    se = O.emd_init(f0, f1)
+
+    def step():
+        t0 = time.perf_counter()
+        O.rof_iterate(sr, I64, LAMBDA, tau, sigma, 1)
+        O.emd_iterate(se, 1.0, 1.0, 1)
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        step()
+    t = sum(step() for _ in range(args.steps))
+    value = args.steps * 2 * N * N / t
+    sample = f"{args.steps} steps of 1 ROF + 1 EMD FP64 oracle iteration at {N}x{N} (no gap check)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"ROF + L1-EMD G-prox PDHG, {N}x{N}, FP64 CPU oracle, 1 iteration of each per step",
+                       "N": N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1805_09453_gb300 import build, gprox
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        build.build()
+    if ws > 1:
+        dist.barrier()
+    N = args.size
+    I, f0, f1 = _inputs(N)
+    Id = torch.from_numpy(I).to(dev)
+    f0d = torch.from_numpy(f0).to(dev)
+    f1d = torch.from_numpy(f1).to(dev)
+    h = gprox.Handle(local)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        # step sizes: ROF rule (sections 3.1 / 4.1), EMD tau = sigma = 1 (section 4.2)
+        u0 = torch.empty((N, N), device=dev)
+        st, rep = gprox.rof_solve(h, Id, u0, None, LAMBDA, gprox.default_opts(max_iters=0, tol_rel_gap=0.0))
+        h.check(st)
+        tau_rof = rep["tau"]
+        srof = gprox.State(h, "rof", N, I=Id, lam=LAMBDA, tau=tau_rof)
+        semd = gprox.State(h, "emd", N, f0=f0d, f1=f1d, tau=1.0)
+
+        def step():
+            srof.step(ITERS_PER_STEP)
+            g1 = srof.gap()
+            semd.step(ITERS_PER_STEP)
+            g2 = semd.gap()
+            return g1, g2
+
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+        gprox.profile(h, True)
+        clocks = ClockSampler(local) if rank == 0 else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            g_rof, g_emd = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        cl = clocks.stop() if clocks else None
+        gprox.profile(h, False)
+        ms = e0.elapsed_time(e1)
+        prof = gprox.profile_read(h)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = ws * args.steps * 2 * ITERS_PER_STEP * N * N
+    value = units / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (largest summed device time)
+    peak, peak_kind = _peaks()
+    name = max((k for k in prof if k in BYTES_PER_POINT), key=lambda k: prof[k][0])
+    kms, kn = prof[name]
+    avg_s = kms / 1e3 / max(kn, 1)
+    bytes_launch = BYTES_PER_POINT[name] * N * N
+    achieved = bytes_launch / avg_s / 1e9
+    tr = NCU_TRAFFIC.get(name)
+    traffic = tr["bytes"] if tr and tr.get("src") == _src_hash() else None
+    roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                "bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3}
+    kernels = {k: {"ms_total": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}
+    launches = int(sum(v[1] for v in prof.values()))
+
+    # whole-iteration HBM fraction (algorithmic bytes of all passes / step time)
+    it_bytes = (3 * 8 + 28) * N * N + (3 * 8 + 44) * N * N  # ROF + EMD per iteration
+    whole_frac = (it_bytes * ITERS_PER_STEP * args.steps / (ms_max / 1e3) / 1e9) / peak
+
+    # end to end through the public solve calls with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        Ih = torch.from_numpy(I).pin_memory()
+        f0h = torch.from_numpy(f0).pin_memory()
+        f1h = torch.from_numpy(f1).pin_memory()
+        uh = torch.empty((N, N), dtype=torch.float32).pin_memory()
+        mh = torch.empty((2, N, N), dtype=torch.float32).pin_memory()
+        Ib, f0b, f1b = torch.empty_like(Id), torch.empty_like(f0d), torch.empty_like(f1d)
+        ub = torch.empty((N, N), device=dev)
+        mb = torch.empty((2, N, N), device=dev)
+        opts = gprox.default_opts(max_iters=ITERS_PER_STEP, gap_every=ITERS_PER_STEP, tol_rel_gap=0.0)
+        ke = max(1, min(args.steps, 20))
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                Ib.copy_(Ih, non_blocking=True)
+                f0b.copy_(f0h, non_blocking=True)
+                f1b.copy_(f1h, non_blocking=True)
+                h.check(gprox.rof_solve(h, Ib, ub, None, LAMBDA, opts)[0])
+                h.check(gprox.emd_solve(h, f0b, f1b, mb, None, None, opts)[0])
+                uh.copy_(ub, non_blocking=True)
+                mh.copy_(mb, non_blocking=True)
+            stream.synchronize()
+
+        for _ in range(2):
+            e2e_step()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            e2e_step()
+        te = torch.tensor([time.perf_counter() - t0], device=dev, dtype=torch.float64)
+        if ws > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": ws * ke * 2 * ITERS_PER_STEP * N * N / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": 3 * N * N * 4, "d2h_bytes_per_step": 3 * N * N * 4,
+               "steps": ke, "what": "rof_solve + emd_solve (10 iterations each, setup included) from pinned host "
+                                    "inputs, u and m copied back"}
+
+    # time to relative gap 1e-5 (solve calls from device inputs, CUDA graphs on)
+    ttg = None
+    if not args.no_ttg:
+        ttg = {}
+        with torch.cuda.stream(stream):
+            m = torch.empty((2, N, N), device=dev)
+            o = gprox.default_opts(max_iters=args.ttg_cap, tol_rel_gap=1e-5, use_graph=1)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, o)
+            ttg["emd"] = {"seconds": time.perf_counter() - t0, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
+                          "status": rep["status_name"], "mass_residual": rep["mass_residual"]}
+            u = torch.empty((N, N), device=dev)
+            t0 = time.perf_counter()
+            st, rep = gprox.rof_solve(h, Id, u, None, LAMBDA, o)
+            ttg["rof"] = {"seconds": time.perf_counter() - t0, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
+                          "status": rep["status_name"], "tau": rep["tau"]}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ROF (lambda=8, noisy shapes) + L1-EMD (8-Gaussian mixtures) G-prox PDHG, "
+                                   f"{N}x{N}, {ITERS_PER_STEP} iterations of each per step incl. one gap check",
+                       "N": N, "iters_per_step": ITERS_PER_STEP, "parallelism": f"replicas{ws}",
+                       "l2": "no flush: inputs and working set (~1 GB per problem) exceed the 129 MB L2"},
+            "roofline": roofline, "whole_iteration_hbm_frac": whole_frac, "kernels": kernels,
+            "gpu_launches": launches, "clocks": cl, "e2e": e2e, "time_to_gap": ttg,
+            "last_gap": {"rof": g_rof["rel_gap"], "emd": g_emd["rel_gap"]}}
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline_oracle(N, 1)
+        line["cpu_baseline"].pop("seconds", None)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    srof.close()
+    semd.close()
+    h.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ttg", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ttg-cap", type=int, default=20000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

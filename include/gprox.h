@@ -1,0 +1,226 @@
+/*
+ * gprox.h -- C ABI of the GB300 (sm_103a) G-prox PDHG library.
+ *
+ * The library solves, on one GPU, the two problems of Jacobs, Leger, Li and
+ * Osher, "Solving large-scale optimization problems with a convergence rate
+ * independent of grid size" (arXiv 1805.09453), with their preconditioned
+ * primal-dual method (Algorithm 2, "G-prox PDHG", section 3):
+ *   - ROF total-variation denoising, section 3.1 (updates of u, p, pbar);
+ *   - the L1 earth mover's / Beckmann problem, section 3.2 (Hodge split
+ *     m = u + grad psi, Leray-projected u update, projected p update).
+ *
+ * Discretisation (the paper does not print one; every choice below is the
+ * reading the library and its tests use):
+ *   - N x N cell-centred grid on [0,1]^2, h = 1/N, row-major float32 planes,
+ *     row index i = y (slow), column index j = x (fast);
+ *   - grad = forward differences with a zero last slot (zero Neumann flux),
+ *     div = -grad^T (backward differences), Laplacian = div grad (5-point
+ *     Neumann).  Then K^T K = -Laplacian exactly and the cosine basis of the
+ *     even reflection (Appendix A) diagonalises the u-step;
+ *   - vector fields are two consecutive planes (x component, then y): the
+ *     slots [i][N-1] of the x plane and [N-1][j] of the y plane are
+ *     structurally zero; inputs there are ignored, outputs there are 0;
+ *   - inner products, objectives and gaps are h^2-weighted (L2 on [0,1]^2).
+ *
+ * Conventions for every entry point:
+ *   - array arguments are DEVICE pointers (cudaMalloc / torch CUDA memory) of
+ *     float32, owned by the caller; the library never frees them.  Host
+ *     pointers are rejected with GP_ERR_ARG.  Pointers must be 4-byte
+ *     aligned; 16-byte alignment together with N % 4 == 0 selects the
+ *     vectorised kernels, anything else the scalar ones (same results);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is ordered on that stream; solver calls synchronise
+ *     it only at duality-gap checks and on return;
+ *   - a handle owns its workspace, DCT tables and scratch; one handle must
+ *     not be used by two host threads or two streams at the same time;
+ *   - functions return a gp_status and never abort or throw.  On an error
+ *     other than GP_ERR_MAXITER the output arrays are unspecified;
+ *     gp_last_error(handle) returns a description of the last failure.
+ */
+#ifndef GPROX_H
+#define GPROX_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GP_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define GP_API __attribute__((visibility("default")))
+#else
+#define GP_API
+#endif
+
+typedef enum gp_status {
+  GP_OK = 0,
+  GP_ERR_ARG = 1,         /* bad size, pointer, option or state */
+  GP_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+  GP_ERR_MAXITER = 3,     /* tolerance not reached within max_iters (outputs hold the last iterate) */
+  GP_ERR_NONFINITE = 4,   /* NaN / Inf met in an objective or gap reduction */
+  GP_ERR_DIVERGED = 5,    /* relative gap grew 10x over 5 consecutive checks */
+  GP_ERR_MASS = 6,        /* EMD densities differ in total mass by more than 1e-3 relative */
+  GP_ERR_UNSUPPORTED = 7  /* option not available in this build (e.g. a precision mode) */
+} gp_status;
+
+/* Arithmetic of the cosine-transform (Helmholtz / Poisson) solve. */
+typedef enum gp_prec {
+  GP_PREC_FP32 = 0,        /* FP32 fast cosine transform (power-of-two N) or FP32 dense transform */
+  GP_PREC_SPLIT_BF16 = 1,  /* dense transform on tensor cores, hi+lo bf16 split, FP32 accumulate */
+  GP_PREC_SPLIT_FP16 = 2   /* dense transform on tensor cores, hi+lo fp16 split, FP32 accumulate */
+} gp_prec;
+
+typedef struct gp_opts {
+  int max_iters;       /* iteration cap (>= 0; default 1000) */
+  int gap_every;       /* duality-gap check every k iterations (>= 1; default 10) */
+  double tol_rel_gap;  /* stop once (P - D) / max(|P|,|D|) <= tol; <= 0: run exactly max_iters */
+  double tau;          /* primal step; <= 0 selects the paper's rule (ROF section 4.1, EMD tau = 1) */
+  double sigma;        /* dual step; <= 0 selects 1 / tau */
+  double tau_scale;    /* multiplier on the rule's tau (<= 0 means 1) */
+  double eps;          /* ROF rule tolerance epsilon (default 1e-3) */
+  int prec;            /* gp_prec of the cosine-transform solve */
+  int use_graph;       /* replay the k iterations between gap checks as a CUDA graph */
+  int warm_start;      /* 0: zero initial state; 1: take the caller's u / p (ROF) or p (EMD) arrays as the start */
+} gp_opts;
+
+typedef struct gp_report {
+  int iters;             /* iterations run */
+  int status;            /* gp_status of the solve */
+  double primal;         /* P at the last check: ROF energy or EMD cost sum |m| h^2 */
+  double dual;           /* D at the last check (a lower bound on the optimum) */
+  double rel_gap;        /* (P - D) / max(|P|, |D|) */
+  double mass_residual;  /* EMD: h^2 sum |div m - (f0 - f1)| / h^2 sum |f0 - f1|; ROF: 0 */
+  double tau, sigma;     /* step sizes used */
+  double seconds;        /* host wall time of the call */
+} gp_report;
+
+typedef struct gp_handle_s* gp_handle;
+typedef struct gp_state_s* gp_state;
+
+/* Library ABI version (GP_ABI_VERSION of the build). */
+GP_API int gp_abi_version(void);
+
+/* Fill `opts` with the defaults listed in gp_opts. */
+GP_API void gp_default_opts(gp_opts* opts);
+
+/* Create a handle bound to CUDA device `device`.  Allocates no device memory
+ * yet (workspace grows on first use).  Returns GP_ERR_ARG for a NULL `out`
+ * or a device index out of range. */
+GP_API gp_status gp_create(gp_handle* out, int device);
+
+/* Release a handle and all memory it owns (synchronises the device). NULL is a no-op. */
+GP_API gp_status gp_destroy(gp_handle h);
+
+/* Text of the last error on this handle ("" if none).  Valid until the next call on `h`. */
+GP_API const char* gp_last_error(gp_handle h);
+
+/*
+ * dct2_poisson: solve (alpha - Laplacian) x = b on the N x N grid with zero
+ * Neumann conditions -- the linear solve inside the G-prox u-step
+ * (section 3.1: (lambda tau Id - Laplacian)^{-1}; section 3.2: the
+ * Laplacian^{-1} of the Leray projection and of the Hodge split), done in the
+ * cosine basis that the even reflection of Appendix A gives:
+ *     x = C^T [ (C b C^T) / (alpha + mu_k + mu_l) ] C,
+ *     mu_k = (4/h^2) sin^2(pi k / 2N),  C = orthonormal DCT-II.
+ *   b      device, N*N float32, read only.
+ *   x      device, N*N float32, written (may equal b).
+ *   N      1 <= N <= 8192.
+ *   alpha  >= 0.  alpha == 0: the constant mode of b is dropped and x has zero mean.
+ *   prec   gp_prec.  GP_PREC_FP32 uses the fast transform when N is a power of
+ *          two in [16, 8192], else the dense one.
+ * Errors: GP_ERR_ARG (N, alpha, pointers), GP_ERR_UNSUPPORTED (prec), GP_ERR_CUDA.
+ */
+GP_API gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alpha,
+                       int prec, void* stream);
+
+/*
+ * rof_solve: minimise the ROF energy ||u||_TV + lambda/2 ||u - I||^2
+ * (section 3.1) with G-prox PDHG:
+ *     u_{n+1} = (lambda tau - Lap)^{-1} (lambda tau I + tau div pbar_n - Lap u_n)
+ *     p_{n+1} = (p_n + sigma grad u_{n+1}) / max(1, |p_n + sigma grad u_{n+1}|)
+ *     pbar_{n+1} = 2 p_{n+1} - p_n
+ * Step rule when opts->tau <= 0 (section 4.1 with the section-3.1 bound on
+ * ||u*||_TV): tau = min(sqrt(lambda) T / sqrt(eps), ||grad I||_L2),
+ * T = min(||I||_TV, lambda/2 ||I - mean I||^2), sigma = 1/tau.
+ *   I       device, N*N, the image (read only).
+ *   u       device, N*N, out: the last primal iterate (in: start if warm_start).
+ *   p       device, 2*N*N (x plane, y plane), out: the last dual iterate
+ *           (in: start if warm_start); may be NULL when warm_start == 0.
+ *   lambda  > 0 fidelity weight.
+ *   opts    NULL = defaults.  report: may be NULL.
+ * Returns GP_OK when the tolerance was met (or max_iters ran with tol <= 0),
+ * GP_ERR_MAXITER if not, GP_ERR_NONFINITE / GP_ERR_DIVERGED on breakdown.
+ */
+GP_API gp_status rof_solve(gp_handle h, const float* I, float* u, float* p, int N, double lambda,
+                    const gp_opts* opts, gp_report* report, void* stream);
+
+/*
+ * emd_solve: L1 earth mover's distance min sum_x |m(x)| h^2 s.t. div m = f0 - f1
+ * (section 3.2, isotropic 2-norm) with G-prox PDHG on m = u + grad psi:
+ *     Lap psi = f0 - f1,  m_0 = grad psi
+ *     m_{n+1} = m_n - tau (pbar_n - grad Lap^{-1} div pbar_n)     (Leray projection)
+ *     p_{n+1} = proj(p_n + sigma m_{n+1}),  pbar_{n+1} = 2 p_{n+1} - p_n
+ * Default steps tau = sigma = 1 (section 4.2, bounded densities).  The dual
+ * bound is D = (phi, f1 - f0) / max(1, max |grad phi|) with phi = Lap^{-1} div p.
+ *   f0, f1  device, N*N densities with equal total mass (|diff| <= 1e-3 relative
+ *           else GP_ERR_MASS); a tiny mass mismatch is dropped with the constant mode.
+ *   m       device, 2*N*N, out: the last flux iterate m_n.
+ *   p       device, 2*N*N or NULL: out: last dual iterate; in: start if warm_start.
+ *   phi     device, N*N or NULL: out: the dual potential Lap^{-1} div p_n of the last check.
+ * Returns as rof_solve.
+ */
+GP_API gp_status emd_solve(gp_handle h, const float* f0, const float* f1, float* m, float* p, float* phi,
+                    int N, const gp_opts* opts, gp_report* report, void* stream);
+
+/*
+ * Explicit solver states for step-by-step driving (checkpoint / resume, tests,
+ * external schedulers).  A state owns its device buffers and keeps pointers
+ * to the caller's inputs (I, or f0 / f1), which must outlive it.
+ *
+ * gp_state_create_rof / _emd: u0 (or m0), p0, pbar0 may be NULL: defaults are
+ * u0 = 0, m0 = grad psi, p0 = 0, pbar0 = p0.  tau > 0, sigma > 0 required.
+ * EMD iterates stay on the affine set {div m = f0 - f1} (m = u + grad psi with
+ * u divergence-free, section 3.2): the first step projects a caller's m0 onto
+ * it, m0 + grad Lap^{-1}(f0 - f1 - div m0), which changes a feasible m0 by
+ * nothing.  Each EMD step solves Lap q = (f0 - f1) - div(m_n - tau pbar_n) and
+ * sets m_{n+1} = m_n - tau pbar_n + grad q: on the affine set this equals the
+ * section-3.2 update m_n - tau (pbar_n - grad Lap^{-1} div pbar_n), and in
+ * floating point it keeps solve errors from accumulating in div m.
+ * pd_step runs n_steps >= 0 G-prox iterations (section 3, Algorithm 2) with
+ * the cosine solve in precision `prec`.  gp_state_read copies the current
+ * primal (u: N*N, or m: 2*N*N) and p (2*N*N) into caller device buffers
+ * (either may be NULL).  gp_state_gap evaluates P, D, gap (and the EMD mass
+ * residual) of the current iterate and synchronises `stream`.
+ */
+GP_API gp_status gp_state_create_rof(gp_handle h, gp_state* out, const float* I, int N, double lambda,
+                              double tau, double sigma, const float* u0, const float* p0,
+                              const float* pbar0, void* stream);
+GP_API gp_status gp_state_create_emd(gp_handle h, gp_state* out, const float* f0, const float* f1, int N,
+                              double tau, double sigma, const float* m0, const float* p0,
+                              const float* pbar0, void* stream);
+GP_API gp_status pd_step(gp_handle h, gp_state s, int n_steps, int prec, void* stream);
+GP_API gp_status gp_state_read(gp_handle h, gp_state s, float* primal, float* p, void* stream);
+GP_API gp_status gp_state_gap(gp_handle h, gp_state s, gp_report* report, void* stream);
+GP_API gp_status gp_state_destroy(gp_state s);
+
+/*
+ * Launch profiler (tracing).  gp_profile(h, 1) clears the counters and starts
+ * recording: every kernel the handle launches is bracketed by CUDA events on
+ * its stream (CUDA-graph replay is disabled while recording); gp_profile(h, 0)
+ * stops.  gp_profile_query returns, for kernel class `kernel` in
+ * [0, gp_profile_kernels()), its name (static string), the summed device time
+ * in ms and the number of kernel launches recorded (it waits for the recorded
+ * events).  Classes: dct_rows_fwd, dct_cols_solve, dct_rows_inv (the three
+ * passes of the fast cosine solve), dct_dense, rof_fused, emd_fused, reduce,
+ * setup.  The paper has no counterpart (it reports wall-clock totals only).
+ */
+GP_API gp_status gp_profile(gp_handle h, int enable);
+GP_API int gp_profile_kernels(void);
+GP_API gp_status gp_profile_query(gp_handle h, int kernel, const char** name, double* total_ms,
+                                  long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GPROX_H */

@@ -1,0 +1,926 @@
+// C ABI of the library: handles, solver states, the solve loops and the
+// duality-gap stopping test.  All device work is issued on the caller's
+// stream; the host synchronises only when it needs the gap scalars.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <string>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+#include "gp_internal.cuh"
+#include "stencil.cuh"
+
+using namespace gp;
+
+enum { KIND_ROF = 1, KIND_EMD = 2 };
+
+// Kernel classes recorded by the launch profiler.
+enum {
+  PK_DCT_ROWS_FWD = 0,
+  PK_DCT_COLS,
+  PK_DCT_ROWS_INV,
+  PK_DCT_DENSE,
+  PK_ROF_FUSED,
+  PK_EMD_FUSED,
+  PK_REDUCE,
+  PK_SETUP,
+  PK_COUNT
+};
+static const char* kProfNames[PK_COUNT] = {"dct_rows_fwd", "dct_cols_solve", "dct_rows_inv", "dct_dense",
+                                           "rof_fused",    "emd_fused",      "reduce",       "setup"};
+// Kernel launches behind one recorded launch of a class.
+static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 5, 1, 1, 1, 1};
+
+struct Profiler {
+  bool on = false;
+  struct Rec {
+    int id;
+    cudaEvent_t a, b;
+  };
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<Rec> recs;
+  long long launches[PK_COUNT] = {0};
+  double ms[PK_COUNT] = {0};
+  bool resolved = true;
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+};
+
+struct gp_handle_s {
+  int device = 0;
+  std::string err;
+  std::map<int, DctPlan> plans;
+  float* ws = nullptr;  // solve scratch for dct2_poisson
+  size_t ws_floats = 0;
+  double* part = nullptr;  // per-block partial sums of handle-level reductions
+  size_t part_cap = 0;
+  double* dres = nullptr;  // device result scalars
+  double* hres = nullptr;  // pinned host copy
+  std::map<std::pair<int, int>, gp_state_s*> cache;  // solver workspaces keyed by (kind, N)
+  Profiler prof;
+  bool capturing = false;
+};
+
+struct gp_state_s {
+  gp_handle h = nullptr;
+  int kind = 0, N = 0, n = 0, cur = 0;
+  double lam = 0, tau = 0, sigma = 0;
+  const float* I = nullptr;
+  const float* f0 = nullptr;
+  const float* f1 = nullptr;
+  float* prim = nullptr;  // ROF: u (N^2); EMD: q (N^2)
+  float* r = nullptr;     // ROF: next right-hand side; EMD: d = g - div s (= tau div pbar)
+  float* p[2] = {nullptr, nullptr};
+  float* s[2] = {nullptr, nullptr};  // EMD only
+  float* m = nullptr;                // EMD: flux of the current iterate (after a gap step)
+  float* e = nullptr;                // EMD: -div p of the current iterate (after a gap step)
+  float* phi = nullptr;              // EMD: dual potential
+  float* g = nullptr;                // EMD: f0 - f1
+  float* tmp = nullptr;              // solve scratch, 2 N^2
+  double* part = nullptr;            // this state's per-block partial sums
+  bool vec = false;
+  bool partials_valid = false;  // part holds the fused gap partials of the current iterate
+  double mass_den = 0;          // EMD: sum |f0 - f1| (mass-residual normaliser)
+  std::vector<void*> allocs;
+  // CUDA graphs of k-step chunks, keyed by (k, cur, prec, gap_last)
+  std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+gp_status fail(gp_handle h, gp_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+gp_status cuda_fail(gp_handle h, cudaError_t e, const char* where) {
+  return fail(h, GP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GP_CUDA(h, expr)                                     \
+  do {                                                       \
+    cudaError_t _e = (expr);                                 \
+    if (_e != cudaSuccess) return cuda_fail((h), _e, #expr); \
+  } while (0)
+
+// Launch through the profiler: when it is on (and no graph is being
+// captured), CUDA events bracket the launch on its stream.
+template <typename F>
+cudaError_t plaunch(gp_handle h, int id, cudaStream_t st, F&& f) {
+  Profiler& P = h->prof;
+  const bool rec = P.on && !h->capturing;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (rec) {
+    a = P.next();
+    b = P.next();
+    cudaEventRecord(a, st);
+  }
+  cudaError_t e = f();
+  if (rec) {
+    cudaEventRecord(b, st);
+    P.recs.push_back({id, a, b});
+    P.resolved = false;
+  }
+  if (P.on) P.launches[id] += kProfLaunches[id];
+  return e;
+}
+
+bool is_device_ptr(const void* p, int device) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+gp_status check_ptr(gp_handle h, const void* p, const char* name) {
+  if (!is_device_ptr(p, h->device))
+    return fail(h, GP_ERR_ARG, std::string(name) + " is not a device pointer of the handle's device");
+  if (((uintptr_t)p & 3u) != 0) return fail(h, GP_ERR_ARG, std::string(name) + " is not 4-byte aligned");
+  return GP_OK;
+}
+
+gp_status get_plan(gp_handle h, int N, const DctPlan** out) {
+  auto it = h->plans.find(N);
+  if (it == h->plans.end()) {
+    DctPlan p;
+    cudaError_t e = dct_plan_init(p, N);
+    if (e != cudaSuccess) {
+      dct_plan_free(p);
+      return cuda_fail(h, e, "dct_plan_init");
+    }
+    it = h->plans.emplace(N, p).first;
+  }
+  *out = &it->second;
+  return GP_OK;
+}
+
+gp_status ensure_part(gp_handle h, size_t n) {
+  if (n <= h->part_cap) return GP_OK;
+  if (h->part) cudaFree(h->part);
+  h->part = nullptr;
+  h->part_cap = 0;
+  GP_CUDA(h, cudaMalloc(&h->part, n * sizeof(double)));
+  h->part_cap = n;
+  return GP_OK;
+}
+
+gp_status ensure_res(gp_handle h) {
+  if (!h->dres) GP_CUDA(h, cudaMalloc(&h->dres, 16 * sizeof(double)));
+  if (!h->hres) GP_CUDA(h, cudaMallocHost(&h->hres, 16 * sizeof(double)));
+  return GP_OK;
+}
+
+// x = scale (alpha - Lap)^{-1} b with the plan of size N; `tmp` holds 2 N^2.
+gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double alpha, double scale, int prec,
+                bool allow_fast, cudaStream_t st) {
+  const DctPlan* p = nullptr;
+  gp_status s = get_plan(h, N, &p);
+  if (s != GP_OK) return s;
+  if (prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
+  const float a = (float)alpha, sc = (float)scale;
+  if (p->fft && allow_fast) {
+    GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return dct_fft_pass(*p, 0, b, tmp, a, sc, st); }));
+    GP_CUDA(h, plaunch(h, PK_DCT_COLS, st, [&] { return dct_fft_pass(*p, 1, tmp, tmp, a, sc, st); }));
+    GP_CUDA(h, plaunch(h, PK_DCT_ROWS_INV, st, [&] { return dct_fft_pass(*p, 2, tmp, x, a, sc, st); }));
+  } else {
+    if (!p->C) return fail(h, GP_ERR_ARG, "no dense transform for this size");
+    GP_CUDA(h, plaunch(h, PK_DCT_DENSE, st, [&] { return dct_solve_dense_fp32(*p, b, x, tmp, a, sc, st); }));
+  }
+  return GP_OK;
+}
+
+size_t fused_blocks(int N, bool vec) {
+  dim3 g = fused_grid(N, vec ? 4 : 1);
+  return (size_t)g.x * g.y;
+}
+
+size_t state_part_size(int N) {
+  // fused partials (<= 4 per block; the scalar layout has the most blocks), then dual partials
+  return fused_blocks(N, false) * 4 + (size_t)reduce_blocks_1d((size_t)N * N) * 4;
+}
+
+// Copy `nq` reduced scalars to the host and wait for them.
+gp_status fetch(gp_handle h, int nq, cudaStream_t st) {
+  GP_CUDA(h, cudaMemcpyAsync(h->hres, h->dres, nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(h, cudaStreamSynchronize(st));
+  return GP_OK;
+}
+
+void drop_graphs(gp_state s) {
+  for (auto& kv : s->graphs) cudaGraphExecDestroy(kv.second);
+  s->graphs.clear();
+}
+
+void free_state(gp_state s) {
+  if (!s) return;
+  drop_graphs(s);
+  for (void* p : s->allocs) cudaFree(p);
+  delete s;
+}
+
+gp_status alloc_state(gp_handle h, int kind, int N, gp_state* out) {
+  gp_state s = new gp_state_s();
+  s->h = h;
+  s->kind = kind;
+  s->N = N;
+  const size_t NN = (size_t)N * N;
+  auto A = [&](float** dst, size_t n) -> cudaError_t {
+    cudaError_t e = cudaMalloc(dst, n * sizeof(float));
+    if (e == cudaSuccess) s->allocs.push_back(*dst);
+    return e;
+  };
+  cudaError_t e = cudaSuccess;
+  if (!e) e = A(&s->prim, NN);
+  if (!e) e = A(&s->r, NN);
+  if (!e) e = A(&s->p[0], 2 * NN);
+  if (!e) e = A(&s->p[1], 2 * NN);
+  if (!e) e = A(&s->tmp, 2 * NN);
+  if (kind == KIND_EMD) {
+    if (!e) e = A(&s->s[0], 2 * NN);
+    if (!e) e = A(&s->s[1], 2 * NN);
+    if (!e) e = A(&s->m, 2 * NN);
+    if (!e) e = A(&s->e, NN);
+    if (!e) e = A(&s->phi, NN);
+    if (!e) e = A(&s->g, NN);
+  }
+  if (!e) {
+    e = cudaMalloc(&s->part, state_part_size(N) * sizeof(double));
+    if (e == cudaSuccess) s->allocs.push_back(s->part);
+  }
+  if (e != cudaSuccess) {
+    free_state(s);
+    return cuda_fail(h, e, "state allocation");
+  }
+  *out = s;
+  return GP_OK;
+}
+
+// --------------------------------------------------------------- ROF state
+gp_status rof_setup(gp_state s, const float* I, double lam, double tau, double sigma, const float* u0,
+                    const float* p0, const float* pbar0, cudaStream_t st) {
+  gp_handle h = s->h;
+  const int N = s->N;
+  const size_t NN = (size_t)N * N;
+  if (s->I != I || s->lam != lam || s->tau != tau || s->sigma != sigma) drop_graphs(s);
+  s->I = I;
+  s->lam = lam;
+  s->tau = tau;
+  s->sigma = sigma;
+  s->n = 0;
+  s->cur = 0;
+  s->partials_valid = false;
+  s->vec = (N % 4 == 0) && aligned16(I);
+  if (u0) GP_CUDA(h, cudaMemcpyAsync(s->prim, u0, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  else GP_CUDA(h, cudaMemsetAsync(s->prim, 0, NN * sizeof(float), st));
+  if (p0) GP_CUDA(h, cudaMemcpyAsync(s->p[0], p0, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  else GP_CUDA(h, cudaMemsetAsync(s->p[0], 0, 2 * NN * sizeof(float), st));
+  // pbar0 is staged in p[1], which the first step overwrites
+  const float* pb = s->p[0];
+  if (pbar0) {
+    GP_CUDA(h, cudaMemcpyAsync(s->p[1], pbar0, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    pb = s->p[1];
+  }
+  RofParams P{N, (float)N, (float)((double)N * N), (float)(lam * tau), (float)tau, (float)sigma};
+  GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_rof_init(I, s->prim, pb, s->p[0], s->r, P, st); }));
+  return GP_OK;
+}
+
+gp_status rof_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cudaStream_t st) {
+  gp_handle h = s->h;
+  const int N = s->N;
+  RofParams P{N, (float)N, (float)((double)N * N), (float)(s->lam * s->tau), (float)s->tau, (float)s->sigma};
+  for (int k = 0; k < n_steps; ++k) {
+    gp_status r = solve(h, N, s->r, s->prim, s->tmp, s->lam * s->tau, 1.0, prec, true, st);
+    if (r != GP_OK) return r;
+    const bool g = gap_last && (k == n_steps - 1);
+    float* pin = s->p[s->cur];
+    float* pout = s->p[1 - s->cur];
+    GP_CUDA(h, plaunch(h, PK_ROF_FUSED, st,
+                       [&] { return launch_rof_fused(s->prim, pin, s->I, pout, s->r, s->part, P, s->vec, g, st); }));
+    s->cur = 1 - s->cur;
+    s->n++;
+  }
+  return GP_OK;
+}
+
+gp_status emd_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cudaStream_t st) {
+  gp_handle h = s->h;
+  const int N = s->N;
+  EmdParams P{N, (float)N, (float)s->tau, (float)s->sigma};
+  for (int k = 0; k < n_steps; ++k) {
+    // q = Lap^{-1} d  <=>  (0 - Lap) q = -d
+    gp_status r = solve(h, N, s->r, s->prim, s->tmp, 0.0, -1.0, prec, true, st);
+    if (r != GP_OK) return r;
+    const bool g = gap_last && (k == n_steps - 1);
+    const int c = s->cur;
+    GP_CUDA(h, plaunch(h, PK_EMD_FUSED, st, [&] {
+              return launch_emd_fused(s->prim, s->s[c], s->p[c], s->g, s->s[1 - c], s->p[1 - c], s->r, s->m, s->e,
+                                      s->part, P, s->vec, g, st);
+            }));
+    s->cur = 1 - s->cur;
+    s->n++;
+  }
+  return GP_OK;
+}
+
+// k iterations, optionally replayed from a CUDA graph of the same chunk.
+gp_status run_steps(gp_state s, int k, int prec, bool gap_last, bool use_graph, cudaStream_t st) {
+  gp_handle h = s->h;
+  auto direct = [&](int kk) {
+    return s->kind == KIND_ROF ? rof_steps_direct(s, kk, prec, gap_last, st)
+                               : emd_steps_direct(s, kk, prec, gap_last, st);
+  };
+  if (k <= 0) return GP_OK;
+  if (!use_graph || st == nullptr || h->prof.on) {
+    gp_status r = direct(k);
+    if (r == GP_OK) s->partials_valid = gap_last;
+    return r;
+  }
+  const auto key = std::make_tuple(k, s->cur, prec, gap_last ? 1 : 0);
+  auto it = s->graphs.find(key);
+  if (it == s->graphs.end()) {
+    // First use: run the chunk directly (creates plans, sets kernel
+    // attributes), then capture the same chunk for the next calls.
+    const int cur0 = s->cur;
+    gp_status r = direct(k);
+    if (r != GP_OK) return r;
+    s->partials_valid = gap_last;
+    const int cur1 = s->cur, n1 = s->n;
+    s->cur = cur0;
+    cudaGraph_t g = nullptr;
+    GP_CUDA(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    h->capturing = true;
+    r = direct(k);
+    h->capturing = false;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    s->cur = cur1;
+    s->n = n1;
+    if (r != GP_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    s->graphs[key] = ex;
+    return GP_OK;
+  }
+  GP_CUDA(h, cudaGraphLaunch(it->second, st));
+  if (k & 1) s->cur = 1 - s->cur;
+  s->n += k;
+  s->partials_valid = gap_last;
+  return GP_OK;
+}
+
+// --------------------------------------------------------------- EMD state
+gp_status emd_setup(gp_state s, const float* f0, const float* f1, double tau, double sigma, const float* m0,
+                    const float* p0, const float* pbar0, cudaStream_t st) {
+  gp_handle h = s->h;
+  const int N = s->N;
+  const size_t NN = (size_t)N * N;
+  if (s->f0 != f0 || s->f1 != f1 || s->tau != tau || s->sigma != sigma) drop_graphs(s);
+  s->f0 = f0;
+  s->f1 = f1;
+  s->tau = tau;
+  s->sigma = sigma;
+  s->n = 0;
+  s->cur = 0;
+  s->partials_valid = false;
+  s->vec = N % 4 == 0;  // all fused-kernel operands are state buffers
+  GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_sub(f0, f1, s->g, NN, st); }));
+  if (m0) {
+    GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_copy_field(m0, s->m, N, st); }));
+  } else {
+    // Hodge split (section 3.2): Lap psi = f0 - f1 = g  <=>  (0 - Lap) psi = -g; m0 = grad psi
+    gp_status r = solve(h, N, s->g, s->phi, s->tmp, 0.0, -1.0, GP_PREC_FP32, true, st);
+    if (r != GP_OK) return r;
+    GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_grad(s->phi, s->m, N, st); }));
+  }
+  if (p0) GP_CUDA(h, cudaMemcpyAsync(s->p[0], p0, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  else GP_CUDA(h, cudaMemsetAsync(s->p[0], 0, 2 * NN * sizeof(float), st));
+  const float* pb = s->p[0];
+  if (pbar0) {
+    GP_CUDA(h, cudaMemcpyAsync(s->p[1], pbar0, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    pb = s->p[1];
+  }
+  EmdParams P{N, (float)N, (float)tau, (float)sigma};
+  GP_CUDA(h, plaunch(h, PK_SETUP, st,
+                     [&] { return launch_emd_init(s->m, pb, s->p[0], s->s[0], s->g, s->r, P, st); }));
+  return GP_OK;
+}
+
+void finish_report(gp_report* rep, double P, double D) {
+  rep->primal = P;
+  rep->dual = D;
+  const double sc = fmax(fabs(P), fabs(D));
+  rep->rel_gap = sc > 0 ? (P - D) / sc : 0.0;
+}
+
+// Gap of the current iterate.  Uses the fused partials when the last step
+// left them, else recomputes the terms with the unfused kernels.
+gp_status state_gap(gp_state s, gp_report* rep, int prec, cudaStream_t st) {
+  gp_handle h = s->h;
+  const int N = s->N;
+  const size_t NN = (size_t)N * N;
+  gp_status r = ensure_res(h);
+  if (r != GP_OK) return r;
+  const double h2 = 1.0 / ((double)N * N);
+  const bool fused = s->partials_valid;
+  const int nb = fused ? (int)fused_blocks(N, s->vec) : reduce_blocks_1d(NN);
+  if (s->kind == KIND_ROF) {
+    if (!fused)
+      GP_CUDA(h, plaunch(h, PK_REDUCE, st,
+                         [&] { return launch_rof_gap(s->prim, s->p[s->cur], s->I, N, s->part, nb, st); }));
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 4, 0u, h->dres, st); }));
+    if ((r = fetch(h, 4, st)) != GP_OK) return r;
+    finish_report(rep, h2 * (h->hres[0] + 0.5 * s->lam * h->hres[1]),
+                  -h2 * h->hres[2] - h2 * h->hres[3] / (2.0 * s->lam));
+    rep->mass_residual = 0.0;
+    return GP_OK;
+  }
+  if (!fused)
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] {
+              return launch_emd_primal(s->m, s->p[s->cur], s->f0, s->f1, s->e, N, s->part, nb, st);
+            }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 2, 0u, h->dres, st); }));
+  // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p = e
+  if ((r = solve(h, N, s->e, s->phi, s->tmp, 0.0, 1.0, prec, true, st)) != GP_OK) return r;
+  const int nd = reduce_blocks_1d(NN);
+  double* pd = s->part + (size_t)nb * 4;
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_emd_dual(s->phi, s->f0, s->f1, N, pd, nd, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(pd, nd, 2, 2u, h->dres + 2, st); }));
+  if ((r = fetch(h, 4, st)) != GP_OK) return r;
+  finish_report(rep, h2 * h->hres[0], h2 * h->hres[2] / fmax(1.0, h->hres[3]));
+  rep->mass_residual = s->mass_den > 0 ? h->hres[1] / s->mass_den : h->hres[1];
+  return GP_OK;
+}
+
+// sum f0, sum f1 and sum |f0 - f1| of an EMD pair (FP64).
+gp_status mass_stats(gp_handle h, const float* f0, const float* f1, int N, double out[3], cudaStream_t st) {
+  const size_t NN = (size_t)N * N;
+  const int nb = reduce_blocks_1d(NN);
+  gp_status r = ensure_part(h, (size_t)nb * 3);
+  if (r != GP_OK) return r;
+  if ((r = ensure_res(h)) != GP_OK) return r;
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_mass_stats(f0, f1, NN, h->part, nb, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 3, 0u, h->dres, st); }));
+  if ((r = fetch(h, 3, st)) != GP_OK) return r;
+  for (int q = 0; q < 3; ++q) out[q] = h->hres[q];
+  return GP_OK;
+}
+
+gp_status check_mass(gp_handle h, const double ms[3]) {
+  if (!isfinite(ms[0]) || !isfinite(ms[1])) return fail(h, GP_ERR_NONFINITE, "non-finite density");
+  const double sc = fmax(fabs(ms[0]), fabs(ms[1]));
+  if (fabs(ms[0] - ms[1]) > 1e-3 * sc)
+    return fail(h, GP_ERR_MASS, "f0 and f1 differ in total mass by more than 1e-3 relative");
+  return GP_OK;
+}
+
+// ROF step rule (sections 3.1 and 4.1).
+gp_status rof_rule(gp_handle h, const float* I, int N, double lambda, const gp_opts& o, double* tau_out,
+                   cudaStream_t st) {
+  const size_t NN = (size_t)N * N;
+  const int nb = reduce_blocks_1d(NN);
+  gp_status r = ensure_part(h, (size_t)nb * 3);
+  if (r != GP_OK) return r;
+  if ((r = ensure_res(h)) != GP_OK) return r;
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_rof_stats(I, N, h->part, nb, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 3, 0u, h->dres, st); }));
+  if ((r = fetch(h, 3, st)) != GP_OK) return r;
+  const double h2 = 1.0 / ((double)N * N);
+  const double tv = h2 * h->hres[0];
+  const double grad_l2 = sqrt(h2 * h->hres[1]);
+  const double mean = h->hres[2] / (double)NN;
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_sq_dev(I, NN, (float)mean, h->part, nb, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 1, 0u, h->dres, st); }));
+  if ((r = fetch(h, 1, st)) != GP_OK) return r;
+  const double fid = 0.5 * lambda * h2 * h->hres[0];
+  if (!isfinite(tv) || !isfinite(fid)) return fail(h, GP_ERR_NONFINITE, "non-finite image");
+  const double eps = o.eps > 0 ? o.eps : 1e-3;
+  double tau = fmin(sqrt(lambda) * fmin(tv, fid) / sqrt(eps), grad_l2);
+  if (!(tau > 0)) tau = 1.0;  // constant image
+  *tau_out = tau * (o.tau_scale > 0 ? o.tau_scale : 1.0);
+  return GP_OK;
+}
+
+struct Timer {
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  double s() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+};
+
+gp_status check_opts(gp_handle h, const gp_opts* o) {
+  if (o->max_iters < 0) return fail(h, GP_ERR_ARG, "max_iters < 0");
+  if (o->gap_every < 1) return fail(h, GP_ERR_ARG, "gap_every < 1");
+  if (o->prec < 0 || o->prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
+  if (o->warm_start < 0 || o->warm_start > 1) return fail(h, GP_ERR_ARG, "unknown warm_start");
+  return GP_OK;
+}
+
+gp_state cached_state(gp_handle h, int kind, int N, gp_status* st) {
+  auto key = std::make_pair(kind, N);
+  auto it = h->cache.find(key);
+  if (it != h->cache.end()) {
+    *st = GP_OK;
+    return it->second;
+  }
+  gp_state s = nullptr;
+  *st = alloc_state(h, kind, N, &s);
+  if (*st != GP_OK) return nullptr;
+  h->cache[key] = s;
+  return s;
+}
+
+// Divergence: the relative gap stayed above 10x its running minimum for 5
+// consecutive checks while above 1e-2.
+struct DivergenceWatch {
+  double best = INFINITY;
+  int bad = 0;
+  bool update(double g) {
+    if (g < best) best = g;
+    bad = (g > 10.0 * best && g > 1e-2) ? bad + 1 : 0;
+    return bad >= 5;
+  }
+};
+
+// Chunked solve loop shared by rof_solve / emd_solve: run gap_every
+// iterations (the last one with the fused gap reductions), check, repeat.
+gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st) {
+  gp_handle h = s->h;
+  DivergenceWatch watch;
+  gp_status status = o.tol_rel_gap > 0 ? GP_ERR_MAXITER : GP_OK;
+  rep->primal = rep->dual = rep->rel_gap = rep->mass_residual = NAN;
+  gp_status r;
+  if (o.max_iters == 0 && (r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
+  while (s->n < o.max_iters) {
+    const int k = std::min(o.gap_every, o.max_iters - s->n);
+    if ((r = run_steps(s, k, o.prec, true, o.use_graph != 0, st)) != GP_OK) return r;
+    if ((r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
+    if (!isfinite(rep->primal) || !isfinite(rep->dual)) {
+      status = GP_ERR_NONFINITE;
+      fail(h, status, "non-finite objective: the iteration broke down");
+      break;
+    }
+    if (o.tol_rel_gap > 0 && rep->rel_gap <= o.tol_rel_gap) {
+      status = GP_OK;
+      break;
+    }
+    if (watch.update(rep->rel_gap)) {
+      status = GP_ERR_DIVERGED;
+      fail(h, status, "relative gap diverged");
+      break;
+    }
+  }
+  rep->iters = s->n;
+  rep->tau = s->tau;
+  rep->sigma = s->sigma;
+  rep->status = status;
+  return status;
+}
+
+bool solve_status_has_outputs(gp_status s) {
+  return s == GP_OK || s == GP_ERR_MAXITER || s == GP_ERR_DIVERGED || s == GP_ERR_NONFINITE;
+}
+
+}  // namespace
+
+// =================================================================== ABI
+extern "C" {
+
+int gp_abi_version(void) { return GP_ABI_VERSION; }
+
+void gp_default_opts(gp_opts* o) {
+  if (!o) return;
+  o->max_iters = 1000;
+  o->gap_every = 10;
+  o->tol_rel_gap = 1e-5;
+  o->tau = 0.0;
+  o->sigma = 0.0;
+  o->tau_scale = 1.0;
+  o->eps = 1e-3;
+  o->prec = GP_PREC_FP32;
+  o->use_graph = 0;
+  o->warm_start = 0;
+}
+
+gp_status gp_create(gp_handle* out, int device) {
+  if (!out) return GP_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return GP_ERR_CUDA;
+  }
+  if (device < 0 || device >= n) return GP_ERR_ARG;
+  gp_handle h = new gp_handle_s();
+  h->device = device;
+  *out = h;
+  return GP_OK;
+}
+
+gp_status gp_destroy(gp_handle h) {
+  if (!h) return GP_OK;
+  DeviceGuard g(h->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : h->cache) free_state(kv.second);
+  for (auto& kv : h->plans) dct_plan_free(kv.second);
+  for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+  if (h->ws) cudaFree(h->ws);
+  if (h->part) cudaFree(h->part);
+  if (h->dres) cudaFree(h->dres);
+  if (h->hres) cudaFreeHost(h->hres);
+  delete h;
+  return GP_OK;
+}
+
+const char* gp_last_error(gp_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alpha, int prec, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
+  if (!(alpha >= 0.0) || !isfinite(alpha)) return fail(h, GP_ERR_ARG, "alpha must be finite and >= 0");
+  if (prec < 0 || prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  gp_status r;
+  if ((r = check_ptr(h, b, "b")) != GP_OK) return r;
+  if ((r = check_ptr(h, x, "x")) != GP_OK) return r;
+  const DctPlan* p = nullptr;
+  if ((r = get_plan(h, N, &p)) != GP_OK) return r;
+  const bool aligned = aligned16(b) && aligned16(x);
+  if (p->fft && !aligned) return fail(h, GP_ERR_ARG, "b and x must be 16-byte aligned for power-of-two N");
+  const size_t need = 2 * (size_t)N * N;
+  if (h->ws_floats < need) {
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_floats = 0;
+    GP_CUDA(h, cudaMalloc(&h->ws, need * sizeof(float)));
+    h->ws_floats = need;
+  }
+  return solve(h, N, b, x, h->ws, alpha, 1.0, prec, true, (cudaStream_t)stream);
+}
+
+gp_status gp_state_create_rof(gp_handle h, gp_state* out, const float* I, int N, double lambda, double tau,
+                              double sigma, const float* u0, const float* p0, const float* pbar0, void* stream) {
+  if (!h || !out) return GP_ERR_ARG;
+  h->err.clear();
+  *out = nullptr;
+  if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
+  if (!(lambda > 0) || !(tau > 0) || !(sigma > 0)) return fail(h, GP_ERR_ARG, "lambda, tau, sigma must be > 0");
+  DeviceGuard g(h->device);
+  gp_status r;
+  if ((r = check_ptr(h, I, "I")) != GP_OK) return r;
+  if (u0 && (r = check_ptr(h, u0, "u0")) != GP_OK) return r;
+  if (p0 && (r = check_ptr(h, p0, "p0")) != GP_OK) return r;
+  if (pbar0 && (r = check_ptr(h, pbar0, "pbar0")) != GP_OK) return r;
+  gp_state s = nullptr;
+  if ((r = alloc_state(h, KIND_ROF, N, &s)) != GP_OK) return r;
+  if ((r = rof_setup(s, I, lambda, tau, sigma, u0, p0, pbar0, (cudaStream_t)stream)) != GP_OK) {
+    free_state(s);
+    return r;
+  }
+  *out = s;
+  return GP_OK;
+}
+
+gp_status gp_state_create_emd(gp_handle h, gp_state* out, const float* f0, const float* f1, int N, double tau,
+                              double sigma, const float* m0, const float* p0, const float* pbar0, void* stream) {
+  if (!h || !out) return GP_ERR_ARG;
+  h->err.clear();
+  *out = nullptr;
+  if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
+  if (!(tau > 0) || !(sigma > 0)) return fail(h, GP_ERR_ARG, "tau, sigma must be > 0");
+  DeviceGuard g(h->device);
+  gp_status r;
+  if ((r = check_ptr(h, f0, "f0")) != GP_OK) return r;
+  if ((r = check_ptr(h, f1, "f1")) != GP_OK) return r;
+  if (m0 && (r = check_ptr(h, m0, "m0")) != GP_OK) return r;
+  if (p0 && (r = check_ptr(h, p0, "p0")) != GP_OK) return r;
+  if (pbar0 && (r = check_ptr(h, pbar0, "pbar0")) != GP_OK) return r;
+  gp_state s = nullptr;
+  if ((r = alloc_state(h, KIND_EMD, N, &s)) != GP_OK) return r;
+  double ms[3];
+  if ((r = mass_stats(h, f0, f1, N, ms, (cudaStream_t)stream)) != GP_OK || (r = check_mass(h, ms)) != GP_OK ||
+      (r = emd_setup(s, f0, f1, tau, sigma, m0, p0, pbar0, (cudaStream_t)stream)) != GP_OK) {
+    free_state(s);
+    return r;
+  }
+  s->mass_den = ms[2];
+  *out = s;
+  return GP_OK;
+}
+
+gp_status pd_step(gp_handle h, gp_state s, int n_steps, int prec, void* stream) {
+  if (!h || !s || s->h != h) return h ? fail(h, GP_ERR_ARG, "state does not belong to handle") : GP_ERR_ARG;
+  h->err.clear();
+  if (n_steps < 0) return fail(h, GP_ERR_ARG, "n_steps < 0");
+  if (prec < 0 || prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
+  DeviceGuard g(h->device);
+  if (n_steps == 0) return GP_OK;
+  // The last step of every call also leaves the gap partials (and, for EMD,
+  // m and -div p) of the new iterate, so the state can be read or checked.
+  return run_steps(s, n_steps, prec, true, false, (cudaStream_t)stream);
+}
+
+gp_status gp_state_read(gp_handle h, gp_state s, float* primal, float* p, void* stream) {
+  if (!h || !s || s->h != h) return GP_ERR_ARG;
+  h->err.clear();
+  DeviceGuard g(h->device);
+  gp_status r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t NN = (size_t)s->N * s->N;
+  if (primal) {
+    if ((r = check_ptr(h, primal, "primal")) != GP_OK) return r;
+    if (s->kind == KIND_ROF)
+      GP_CUDA(h, cudaMemcpyAsync(primal, s->prim, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else
+      GP_CUDA(h, cudaMemcpyAsync(primal, s->m, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  }
+  if (p) {
+    if ((r = check_ptr(h, p, "p")) != GP_OK) return r;
+    GP_CUDA(h, cudaMemcpyAsync(p, s->p[s->cur], 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  }
+  return GP_OK;
+}
+
+gp_status gp_state_gap(gp_handle h, gp_state s, gp_report* rep, void* stream) {
+  if (!h || !s || s->h != h || !rep) return GP_ERR_ARG;
+  h->err.clear();
+  DeviceGuard g(h->device);
+  Timer t;
+  memset(rep, 0, sizeof(*rep));
+  gp_status r = state_gap(s, rep, GP_PREC_FP32, (cudaStream_t)stream);
+  rep->iters = s->n;
+  rep->tau = s->tau;
+  rep->sigma = s->sigma;
+  rep->status = r;
+  rep->seconds = t.s();
+  return r;
+}
+
+gp_status gp_state_destroy(gp_state s) {
+  if (!s) return GP_OK;
+  DeviceGuard g(s->h->device);
+  cudaDeviceSynchronize();
+  free_state(s);
+  return GP_OK;
+}
+
+gp_status rof_solve(gp_handle h, const float* I, float* u, float* p, int N, double lambda, const gp_opts* opts,
+                    gp_report* report, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  Timer t;
+  gp_opts o;
+  gp_default_opts(&o);
+  if (opts) o = *opts;
+  gp_report rep;
+  memset(&rep, 0, sizeof(rep));
+  gp_status r = check_opts(h, &o);
+  if (r != GP_OK) return r;
+  if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
+  if (!(lambda > 0) || !isfinite(lambda)) return fail(h, GP_ERR_ARG, "lambda must be finite and > 0");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  if ((r = check_ptr(h, I, "I")) != GP_OK) return r;
+  if ((r = check_ptr(h, u, "u")) != GP_OK) return r;
+  if (p && (r = check_ptr(h, p, "p")) != GP_OK) return r;
+  if (o.warm_start && !p) return fail(h, GP_ERR_ARG, "warm_start needs p");
+  cudaStream_t st = (cudaStream_t)stream;
+  double tau = o.tau;
+  if (!(tau > 0) && (r = rof_rule(h, I, N, lambda, o, &tau, st)) != GP_OK) return r;
+  const double sigma = o.sigma > 0 ? o.sigma : 1.0 / tau;
+  gp_state s = cached_state(h, KIND_ROF, N, &r);
+  if (!s) return r;
+  if ((r = rof_setup(s, I, lambda, tau, sigma, o.warm_start ? u : nullptr, o.warm_start ? p : nullptr, nullptr,
+                     st)) != GP_OK)
+    return r;
+  gp_status status = run_loop(s, o, &rep, st);
+  if (!solve_status_has_outputs(status)) return status;
+  const size_t NN = (size_t)N * N;
+  GP_CUDA(h, cudaMemcpyAsync(u, s->prim, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  if (p) GP_CUDA(h, cudaMemcpyAsync(p, s->p[s->cur], 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(h, cudaStreamSynchronize(st));
+  rep.seconds = t.s();
+  if (report) *report = rep;
+  return status;
+}
+
+gp_status emd_solve(gp_handle h, const float* f0, const float* f1, float* m, float* p, float* phi, int N,
+                    const gp_opts* opts, gp_report* report, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  Timer t;
+  gp_opts o;
+  gp_default_opts(&o);
+  if (opts) o = *opts;
+  gp_report rep;
+  memset(&rep, 0, sizeof(rep));
+  gp_status r = check_opts(h, &o);
+  if (r != GP_OK) return r;
+  if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  if ((r = check_ptr(h, f0, "f0")) != GP_OK) return r;
+  if ((r = check_ptr(h, f1, "f1")) != GP_OK) return r;
+  if ((r = check_ptr(h, m, "m")) != GP_OK) return r;
+  if (p && (r = check_ptr(h, p, "p")) != GP_OK) return r;
+  if (phi && (r = check_ptr(h, phi, "phi")) != GP_OK) return r;
+  if (o.warm_start && !p) return fail(h, GP_ERR_ARG, "warm_start needs p");
+  cudaStream_t st = (cudaStream_t)stream;
+  double ms[3];
+  if ((r = mass_stats(h, f0, f1, N, ms, st)) != GP_OK) return r;
+  if ((r = check_mass(h, ms)) != GP_OK) return r;
+  // section 4.2: tau = sigma = 1 for bounded densities
+  const double tau = o.tau > 0 ? o.tau : (o.tau_scale > 0 ? o.tau_scale : 1.0);
+  const double sigma = o.sigma > 0 ? o.sigma : 1.0 / tau;
+  gp_state s = cached_state(h, KIND_EMD, N, &r);
+  if (!s) return r;
+  if ((r = emd_setup(s, f0, f1, tau, sigma, nullptr, o.warm_start ? p : nullptr, nullptr, st)) != GP_OK) return r;
+  s->mass_den = ms[2];
+  gp_status status = run_loop(s, o, &rep, st);
+  if (!solve_status_has_outputs(status)) return status;
+  const size_t NN = (size_t)N * N;
+  GP_CUDA(h, cudaMemcpyAsync(m, s->m, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  if (p) GP_CUDA(h, cudaMemcpyAsync(p, s->p[s->cur], 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  if (phi) GP_CUDA(h, cudaMemcpyAsync(phi, s->phi, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(h, cudaStreamSynchronize(st));
+  rep.seconds = t.s();
+  if (report) *report = rep;
+  return status;
+}
+
+// ------------------------------------------------------------ profiling
+gp_status gp_profile(gp_handle h, int enable) {
+  if (!h) return GP_ERR_ARG;
+  Profiler& P = h->prof;
+  if (enable) {
+    P.used = 0;
+    P.recs.clear();
+    for (int i = 0; i < PK_COUNT; ++i) {
+      P.launches[i] = 0;
+      P.ms[i] = 0;
+    }
+    P.resolved = true;
+  }
+  P.on = enable != 0;
+  return GP_OK;
+}
+
+int gp_profile_kernels(void) { return PK_COUNT; }
+
+gp_status gp_profile_query(gp_handle h, int kernel, const char** name, double* total_ms, long long* launches) {
+  if (!h || kernel < 0 || kernel >= PK_COUNT) return GP_ERR_ARG;
+  DeviceGuard g(h->device);
+  Profiler& P = h->prof;
+  if (!P.resolved) {
+    for (auto& rc : P.recs) {
+      cudaError_t e = cudaEventSynchronize(rc.b);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, rc.a, rc.b) == cudaSuccess) P.ms[rc.id] += ms;
+    }
+    P.recs.clear();
+    P.resolved = true;
+  }
+  if (name) *name = kProfNames[kernel];
+  if (total_ms) *total_ms = P.ms[kernel];
+  if (launches) *launches = P.launches[kernel];
+  return GP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "gprox.h"
+
+namespace gp {
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Neumaier (compensated) FP32 accumulator: per-thread partial sums whose
+// error does not grow with the number of terms; each thread's result is
+// widened to FP64 before the cross-thread reduction.
+struct CSum {
+  float s, c;
+  __device__ __forceinline__ CSum() : s(0.f), c(0.f) {}
+  __device__ __forceinline__ void add(float x) {
+    float t = s + x;
+    if (fabsf(s) >= fabsf(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Per-solve cosine-transform plan (one per grid size N, owned by the handle).
+struct DctPlan {
+  int N = 0;
+  bool fft = false;          // power-of-two fast transform available
+  float2* tw = nullptr;      // e^{-2 pi i m / N}, m < N          (fft)
+  float2* wq = nullptr;      // e^{-i pi k / (2N)}, k <= N/2       (fft)
+  float* mu = nullptr;       // (4/h^2) sin^2(pi k / 2N), k < N
+  float* C = nullptr;        // orthonormal DCT-II matrix, N x N   (dense)
+};
+
+// Launchers (dct.cu)
+cudaError_t dct_plan_init(DctPlan& p, int N);
+void dct_plan_free(DctPlan& p);
+// One pass of the fast solve x = scale * (alpha - Lap)^{-1} b:
+//   pass 0: tmp = row DCT-II of b          (in = b,   out = tmp)
+//   pass 1: column solve in place on tmp    (out = tmp)
+//   pass 2: x = row inverse DCT-II of tmp   (in = tmp, out = x)
+// b may alias x.
+cudaError_t dct_fft_pass(const DctPlan& p, int pass, const float* in, float* out, float alpha, float scale,
+                         cudaStream_t st);
+// Dense-matrix form (any N): tmp must hold 2*N*N floats.
+cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp,
+                                 float alpha, float scale, cudaStream_t st);
+
+// Reduction helpers (stencil.cu)
+constexpr int kRedThreads = 256;
+constexpr int kMaxQ = 4;
+
+}  // namespace gp

@@ -1,0 +1,677 @@
+// Pointwise / stencil part of one G-prox PDHG iteration, fused per problem,
+// and the FP64 objective / gap reductions.
+//
+// Discretisation (shared with the cosine solve): forward-difference grad with
+// zero last slots, div = -grad^T, Lap = div grad, h = 1/N.
+//
+// ROF (section 3.1).  Given u_{n+1} (output of the solve) and p_n:
+//     p_{n+1} = proj(p_n + sigma grad u_{n+1}),  pbar = 2 p_{n+1} - p_n,
+//     r_{n+1} = lambda tau I + tau div pbar - Lap u_{n+1}
+// (the right-hand side of the next u-step), one HBM pass: read u, p, I,
+// write p', r.
+//
+// EMD (section 3.2) in the variables s_n = m_n - tau pbar_n and d_n = div pbar_n.
+// Given q_n = Lap^{-1} d_n (output of the solve):
+//     m_{n+1} = m_n - tau (pbar_n - grad q_n) = s_n + tau grad q_n
+//     p_{n+1} = proj(p_n + sigma m_{n+1}),  pbar_{n+1} = 2 p_{n+1} - p_n
+//     s_{n+1} = m_{n+1} - tau pbar_{n+1},    d_{n+1} = div pbar_{n+1}
+// one HBM pass: read q, s, p, write s', p', d.  This is the Leray-projected
+// update of the paper algebraically rearranged so that pbar never has to be
+// stored; m is written only on gap-check iterations.
+//
+// Thread layout: a thread owns V consecutive cells of a row (V = 4 with
+// 128-bit loads when N % 4 == 0 and pointers are 16-byte aligned, else 1)
+// and walks RB rows down, carrying the previous row's values in registers;
+// the left neighbour column and the row above the strip are recomputed.
+#include "gp_internal.cuh"
+#include "stencil.cuh"
+
+namespace gp {
+namespace {
+
+template <int V>
+__device__ __forceinline__ void ldv(float* d, const float* __restrict__ p) {
+  if constexpr (V == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+  } else {
+#pragma unroll
+    for (int c = 0; c < V; ++c) d[c] = p[c];
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void stv(float* __restrict__ p, const float* s) {
+  if constexpr (V == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(s[0], s[1], s[2], s[3]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < V; ++c) p[c] = s[c];
+  }
+}
+
+// Row window: w[0] = col j0-1, w[1..V] = cols j0..j0+V-1, w[V+1] = col j0+V
+// (out-of-grid entries are 0 and never used).
+template <int V>
+__device__ __forceinline__ void load_row(float (&w)[V + 2], const float* __restrict__ base, int row, int N,
+                                         int j0) {
+  if (row < 0 || row >= N) {
+#pragma unroll
+    for (int c = 0; c < V + 2; ++c) w[c] = 0.f;
+    return;
+  }
+  const float* r = base + (size_t)row * N;
+  ldv<V>(&w[1], r + j0);
+  w[0] = j0 > 0 ? r[j0 - 1] : 0.f;
+  w[V + 1] = j0 + V < N ? r[j0 + V] : 0.f;
+}
+
+__device__ __forceinline__ void proj2(float qx, float qy, float& px, float& py) {
+  const float n2 = qx * qx + qy * qy;
+  if (n2 > 1.f) {
+    const float s = rsqrtf(n2);
+    px = qx * s;
+    py = qy * s;
+  } else {
+    px = qx;
+    py = qy;
+  }
+}
+
+// Block reduction of NQ doubles; op bit q set = max, else sum.  Thread 0 writes
+// the block's partials to part[block * NQ + q].
+template <int NQ>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NQ], unsigned maxmask, double* __restrict__ part) {
+  __shared__ double sh[32][NQ];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nthreads = blockDim.x * blockDim.y;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  (void)nthreads;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    double x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double y = __shfl_down_sync(0xffffffffu, x, o);
+      x = ((maxmask >> q) & 1u) ? fmax(x, y) : x + y;
+    }
+    v[q] = x;
+  }
+  const int w = tid >> 5;
+  (void)warp;
+  if ((tid & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sh[w][q] = v[q];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double x = lane < nw ? sh[lane][q] : (((maxmask >> q) & 1u) ? -1e300 : 0.0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_down_sync(0xffffffffu, x, o);
+        x = ((maxmask >> q) & 1u) ? fmax(x, y) : x + y;
+      }
+      if (lane == 0) part[(size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NQ + q] = x;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ ROF
+template <int V, int RB, bool GAP>
+__global__ void __launch_bounds__(128) k_rof_fused(const float* __restrict__ u, const float* __restrict__ pin,
+                                                   const float* __restrict__ I, float* __restrict__ pout,
+                                                   float* __restrict__ r, double* __restrict__ part,
+                                                   RofParams P) {
+  const int N = P.N;
+  const size_t NN = (size_t)N * N;
+  const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  const int i0 = blockIdx.y * RB;
+  CSum s_tv, s_fid, s_id, s_dd;
+  if (j0 < N) {
+    const float* __restrict__ pxin = pin;
+    const float* __restrict__ pyin = pin + NN;
+    float ua[V + 2], ub[V + 2], uc[V + 2];
+    float pby_up[V], p1y_up[V];
+    load_row<V>(ub, u, i0, N, j0);
+    load_row<V>(uc, u, i0 + 1, N, j0);
+    if (i0 > 0) {
+      // recompute p_{n+1} on the row above the strip (only its y part is used)
+      load_row<V>(ua, u, i0 - 1, N, j0);
+      float pnx[V], pny[V];
+      ldv<V>(pnx, pxin + (size_t)(i0 - 1) * N + j0);
+      ldv<V>(pny, pyin + (size_t)(i0 - 1) * N + j0);
+#pragma unroll
+      for (int c = 0; c < V; ++c) {
+        const int j = j0 + c;
+        const float gx = (j < N - 1) ? (ua[c + 2] - ua[c + 1]) * P.invh : 0.f;
+        const float gy = (ub[c + 1] - ua[c + 1]) * P.invh;
+        float px1, py1;
+        proj2(pnx[c] + P.sigma * gx, pny[c] + P.sigma * gy, px1, py1);
+        pby_up[c] = 2.f * py1 - pny[c];
+        p1y_up[c] = py1;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < V + 2; ++c) ua[c] = 0.f;
+#pragma unroll
+      for (int c = 0; c < V; ++c) { pby_up[c] = 0.f; p1y_up[c] = 0.f; }
+    }
+    const int iend = min(i0 + RB, N);
+    for (int i = i0; i < iend; ++i) {
+      const size_t ro = (size_t)i * N;
+      float pnx[V + 1], pny[V + 1];
+      ldv<V>(&pnx[1], pxin + ro + j0);
+      ldv<V>(&pny[1], pyin + ro + j0);
+      pnx[0] = j0 > 0 ? pxin[ro + j0 - 1] : 0.f;
+      pny[0] = j0 > 0 ? pyin[ro + j0 - 1] : 0.f;
+      float Iv[V];
+      ldv<V>(Iv, I + ro + j0);
+      float p1x[V + 1], p1y[V + 1], pbx[V + 1], pby[V + 1], gxs[V + 1], gys[V + 1];
+#pragma unroll
+      for (int c = 0; c <= V; ++c) {
+        const int j = j0 - 1 + c;
+        const float gx = (j < N - 1) ? (ub[c + 1] - ub[c]) * P.invh : 0.f;
+        const float gy = (i < N - 1) ? (uc[c] - ub[c]) * P.invh : 0.f;
+        proj2(pnx[c] + P.sigma * gx, pny[c] + P.sigma * gy, p1x[c], p1y[c]);
+        pbx[c] = 2.f * p1x[c] - pnx[c];
+        pby[c] = 2.f * p1y[c] - pny[c];
+        gxs[c] = gx;
+        gys[c] = gy;
+      }
+      float rv[V], ox[V], oy[V];
+#pragma unroll
+      for (int c = 1; c <= V; ++c) {
+        const int j = j0 + c - 1;
+        const bool xr = j < N - 1, xl = j > 0, yd = i < N - 1, yu = i > 0;
+        ox[c - 1] = xr ? p1x[c] : 0.f;
+        oy[c - 1] = yd ? p1y[c] : 0.f;
+        const float dx = (xr ? pbx[c] : 0.f) - (xl ? pbx[c - 1] : 0.f);
+        const float dy = (yd ? pby[c] : 0.f) - (yu ? pby_up[c - 1] : 0.f);
+        const float uo = ub[c];
+        float lap = 0.f;
+        if (xr) lap += ub[c + 1] - uo;
+        if (xl) lap += ub[c - 1] - uo;
+        if (yd) lap += uc[c] - uo;
+        if (yu) lap += ua[c] - uo;
+        rv[c - 1] = P.lt * Iv[c - 1] + P.tau * (dx + dy) * P.invh - lap * P.invh2;
+        if constexpr (GAP) {
+          s_tv.add(sqrtf(gxs[c] * gxs[c] + gys[c] * gys[c]));
+          const float e = uo - Iv[c - 1];
+          s_fid.add(e * e);
+          const float d1 = ((xr ? p1x[c] : 0.f) - (xl ? p1x[c - 1] : 0.f) + (yd ? p1y[c] : 0.f) -
+                            (yu ? p1y_up[c - 1] : 0.f)) * P.invh;
+          s_id.add(Iv[c - 1] * d1);
+          s_dd.add(d1 * d1);
+        }
+      }
+      stv<V>(pout + ro + j0, ox);
+      stv<V>(pout + NN + ro + j0, oy);
+      stv<V>(r + ro + j0, rv);
+#pragma unroll
+      for (int c = 0; c < V; ++c) {
+        pby_up[c] = pby[c + 1];
+        p1y_up[c] = p1y[c + 1];
+      }
+#pragma unroll
+      for (int c = 0; c < V + 2; ++c) {
+        ua[c] = ub[c];
+        ub[c] = uc[c];
+      }
+      load_row<V>(uc, u, i + 2, N, j0);
+    }
+  }
+  if constexpr (GAP) {
+    double v[4] = {s_tv.value(), s_fid.value(), s_id.value(), s_dd.value()};
+    block_reduce_store<4>(v, 0u, part);
+  }
+}
+
+// ------------------------------------------------------------------ EMD
+// Affine form of the Leray step: with g = f0 - f1 and s_n = m_n - tau pbar_n,
+//     q_n = Lap^{-1} (g - div s_n),   m_{n+1} = s_n + grad q_n.
+// For a feasible m_n (div m_n = g) this is m_n - tau (pbar_n - grad Lap^{-1} div pbar_n),
+// the update of section 3.2; in floating point it re-imposes div m = g at
+// every step instead of carrying each step's solve error forward.
+template <int V, int RB, bool GAP>
+__global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ q, const float* __restrict__ sin_,
+                                                   const float* __restrict__ pin, const float* __restrict__ g,
+                                                   float* __restrict__ sout, float* __restrict__ pout,
+                                                   float* __restrict__ d, float* __restrict__ m,
+                                                   float* __restrict__ e, double* __restrict__ part, EmdParams P) {
+  const int N = P.N;
+  const size_t NN = (size_t)N * N;
+  const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+  const int i0 = blockIdx.y * RB;
+  CSum s_m, s_mass;
+  if (j0 < N) {
+    const float* __restrict__ sx = sin_;
+    const float* __restrict__ sy = sin_ + NN;
+    const float* __restrict__ px = pin;
+    const float* __restrict__ py = pin + NN;
+    float qa[V + 2], qb[V + 2];
+    float sy_up[V], p1y_up[V], my_up[V];  // row above: new s_y, new p_y, m_y
+    load_row<V>(qa, q, i0, N, j0);
+    if (i0 > 0) {
+      float qp[V + 2];
+      load_row<V>(qp, q, i0 - 1, N, j0);
+      const size_t ro = (size_t)(i0 - 1) * N;
+      float sxv[V], syv[V], pxv[V], pyv[V];
+      ldv<V>(sxv, sx + ro + j0);
+      ldv<V>(syv, sy + ro + j0);
+      ldv<V>(pxv, px + ro + j0);
+      ldv<V>(pyv, py + ro + j0);
+#pragma unroll
+      for (int c = 0; c < V; ++c) {
+        const int j = j0 + c;
+        const float gx = (j < N - 1) ? (qp[c + 2] - qp[c + 1]) * P.invh : 0.f;
+        const float gy = (qa[c + 1] - qp[c + 1]) * P.invh;
+        const float mx = sxv[c] + gx, my = syv[c] + gy;
+        float p1x, p1y;
+        proj2(pxv[c] + P.sigma * mx, pyv[c] + P.sigma * my, p1x, p1y);
+        sy_up[c] = my - P.tau * (2.f * p1y - pyv[c]);
+        p1y_up[c] = p1y;
+        my_up[c] = my;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < V; ++c) { sy_up[c] = 0.f; p1y_up[c] = 0.f; my_up[c] = 0.f; }
+    }
+    const int iend = min(i0 + RB, N);
+    for (int i = i0; i < iend; ++i) {
+      const size_t ro = (size_t)i * N;
+      load_row<V>(qb, q, i + 1, N, j0);
+      float sxv[V + 1], syv[V + 1], pxv[V + 1], pyv[V + 1];
+      ldv<V>(&sxv[1], sx + ro + j0);
+      ldv<V>(&syv[1], sy + ro + j0);
+      ldv<V>(&pxv[1], px + ro + j0);
+      ldv<V>(&pyv[1], py + ro + j0);
+      if (j0 > 0) {
+        sxv[0] = sx[ro + j0 - 1]; syv[0] = sy[ro + j0 - 1];
+        pxv[0] = px[ro + j0 - 1]; pyv[0] = py[ro + j0 - 1];
+      } else {
+        sxv[0] = syv[0] = pxv[0] = pyv[0] = 0.f;
+      }
+      float gv[V];
+      ldv<V>(gv, g + ro + j0);
+      float mxv[V + 1], myv[V + 1], p1x[V + 1], p1y[V + 1], snx[V + 1], sny[V + 1];
+#pragma unroll
+      for (int c = 0; c <= V; ++c) {
+        const int j = j0 - 1 + c;
+        const bool xr = j < N - 1, yd = i < N - 1;
+        const float gx = xr ? (qa[c + 1] - qa[c]) * P.invh : 0.f;
+        const float gy = yd ? (qb[c] - qa[c]) * P.invh : 0.f;
+        mxv[c] = xr ? sxv[c] + gx : 0.f;
+        myv[c] = yd ? syv[c] + gy : 0.f;
+        proj2(pxv[c] + P.sigma * mxv[c], pyv[c] + P.sigma * myv[c], p1x[c], p1y[c]);
+        if (!xr) p1x[c] = 0.f;
+        if (!yd) p1y[c] = 0.f;
+        snx[c] = mxv[c] - P.tau * (2.f * p1x[c] - pxv[c]);
+        sny[c] = myv[c] - P.tau * (2.f * p1y[c] - pyv[c]);
+        if (!xr) snx[c] = 0.f;
+        if (!yd) sny[c] = 0.f;
+      }
+      float od[V], omx[V], omy[V], oe[V];
+#pragma unroll
+      for (int c = 1; c <= V; ++c) {
+        const int j = j0 + c - 1;
+        const bool xl = j > 0, yu = i > 0;
+        const float divs = (snx[c] - (xl ? snx[c - 1] : 0.f) + sny[c] - (yu ? sy_up[c - 1] : 0.f)) * P.invh;
+        od[c - 1] = gv[c - 1] - divs;
+        if constexpr (GAP) {
+          const float mx = mxv[c], my = myv[c];
+          omx[c - 1] = mx;
+          omy[c - 1] = my;
+          oe[c - 1] = -(p1x[c] - (xl ? p1x[c - 1] : 0.f) + p1y[c] - (yu ? p1y_up[c - 1] : 0.f)) * P.invh;
+          s_m.add(sqrtf(mx * mx + my * my));
+          const float dm = (mx - (xl ? mxv[c - 1] : 0.f) + my - (yu ? my_up[c - 1] : 0.f)) * P.invh;
+          s_mass.add(fabsf(dm - gv[c - 1]));
+        }
+      }
+      stv<V>(sout + ro + j0, &snx[1]);
+      stv<V>(sout + NN + ro + j0, &sny[1]);
+      stv<V>(pout + ro + j0, &p1x[1]);
+      stv<V>(pout + NN + ro + j0, &p1y[1]);
+      stv<V>(d + ro + j0, od);
+      if constexpr (GAP) {
+        stv<V>(m + ro + j0, omx);
+        stv<V>(m + NN + ro + j0, omy);
+        stv<V>(e + ro + j0, oe);
+      }
+#pragma unroll
+      for (int c = 0; c < V; ++c) {
+        sy_up[c] = sny[c + 1];
+        p1y_up[c] = p1y[c + 1];
+        my_up[c] = myv[c + 1];
+      }
+#pragma unroll
+      for (int c = 0; c < V + 2; ++c) qa[c] = qb[c];
+    }
+  }
+  if constexpr (GAP) {
+    double v[2] = {s_m.value(), s_mass.value()};
+    block_reduce_store<2>(v, 0u, part);
+  }
+}
+
+// EMD dual bound inputs: sum phi (f1 - f0) and max |grad phi|.
+__global__ void __launch_bounds__(256) k_emd_dual(const float* __restrict__ phi, const float* __restrict__ f0,
+                                                  const float* __restrict__ f1, int N, float invh,
+                                                  double* __restrict__ part) {
+  CSum s;
+  float gmax = 0.f;
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const float ph = phi[idx];
+    s.add(ph * (f1[idx] - f0[idx]));
+    const float gx = j < N - 1 ? (phi[idx + 1] - ph) * invh : 0.f;
+    const float gy = i < N - 1 ? (phi[idx + N] - ph) * invh : 0.f;
+    gmax = fmaxf(gmax, sqrtf(gx * gx + gy * gy));
+  }
+  double v[2] = {s.value(), (double)gmax};
+  block_reduce_store<2>(v, 2u, part);
+}
+
+// ROF step-rule statistics: sum |grad I|, sum |grad I|^2, sum I.
+__global__ void __launch_bounds__(256) k_rof_stats(const float* __restrict__ I, int N, float invh,
+                                                   double* __restrict__ part) {
+  CSum a, b, c;
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const float v = I[idx];
+    const float gx = j < N - 1 ? (I[idx + 1] - v) * invh : 0.f;
+    const float gy = i < N - 1 ? (I[idx + N] - v) * invh : 0.f;
+    const float g2 = gx * gx + gy * gy;
+    a.add(sqrtf(g2));
+    b.add(g2);
+    c.add(v);
+  }
+  double v[3] = {a.value(), b.value(), c.value()};
+  block_reduce_store<3>(v, 0u, part);
+}
+
+__global__ void __launch_bounds__(256) k_sq_dev(const float* __restrict__ I, size_t NN, float mean,
+                                                double* __restrict__ part) {
+  CSum a;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const float e = I[idx] - mean;
+    a.add(e * e);
+  }
+  double v[1] = {a.value()};
+  block_reduce_store<1>(v, 0u, part);
+}
+
+// Sum (or max) of per-block partials in a fixed order: deterministic.
+__global__ void __launch_bounds__(256) k_final_reduce(const double* __restrict__ part, int nblk, int nq,
+                                                      unsigned maxmask, double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int q = 0; q < nq; ++q) {
+    const bool mx = (maxmask >> q) & 1u;
+    double acc = mx ? -1e300 : 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+      const double x = part[(size_t)b * nq + q];
+      acc = mx ? fmax(acc, x) : acc + x;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (threadIdx.x < s) sh[threadIdx.x] = mx ? fmax(sh[threadIdx.x], sh[threadIdx.x + s]) : sh[threadIdx.x] + sh[threadIdx.x + s];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[q] = sh[0];
+    __syncthreads();
+  }
+}
+
+// ROF state set-up: r = lambda tau I + tau div pbar - Lap u; zero the p slots.
+__global__ void k_rof_init(const float* __restrict__ I, const float* __restrict__ u, const float* __restrict__ pbar,
+                           float* __restrict__ p, float* __restrict__ r, RofParams P) {
+  const int N = P.N;
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const bool xr = j < N - 1, xl = j > 0, yd = i < N - 1, yu = i > 0;
+    const float dx = (xr ? pbar[idx] : 0.f) - (xl ? pbar[idx - 1] : 0.f);
+    const float dy = (yd ? pbar[NN + idx] : 0.f) - (yu ? pbar[NN + idx - N] : 0.f);
+    const float uo = u[idx];
+    float lap = 0.f;
+    if (xr) lap += u[idx + 1] - uo;
+    if (xl) lap += u[idx - 1] - uo;
+    if (yd) lap += u[idx + N] - uo;
+    if (yu) lap += u[idx - N] - uo;
+    r[idx] = P.lt * I[idx] + P.tau * (dx + dy) * P.invh - lap * P.invh2;
+    if (!xr) p[idx] = 0.f;
+    if (!yd) p[NN + idx] = 0.f;
+  }
+}
+
+// EMD state set-up: s = m0 - tau pbar0 (slots 0); zero the p slots.
+__global__ void k_emd_init(const float* __restrict__ m0, const float* __restrict__ pbar, float* __restrict__ p,
+                           float* __restrict__ s, EmdParams P) {
+  const int N = P.N;
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const bool xr = j < N - 1, yd = i < N - 1;
+    s[idx] = xr ? m0[idx] - P.tau * pbar[idx] : 0.f;
+    s[NN + idx] = yd ? m0[NN + idx] - P.tau * pbar[NN + idx] : 0.f;
+    if (!xr) p[idx] = 0.f;
+    if (!yd) p[NN + idx] = 0.f;
+  }
+}
+
+// d = g - div s (right-hand side of the affine Leray step)
+__global__ void k_affine_rhs(const float* __restrict__ s, const float* __restrict__ g, float* __restrict__ d, int N,
+                             float invh) {
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const bool xr = j < N - 1, xl = j > 0, yd = i < N - 1, yu = i > 0;
+    const float dv = ((xr ? s[idx] : 0.f) - (xl ? s[idx - 1] : 0.f) + (yd ? s[NN + idx] : 0.f) -
+                      (yu ? s[NN + idx - N] : 0.f)) * invh;
+    d[idx] = g[idx] - dv;
+  }
+}
+
+// out = a - b
+__global__ void k_sub(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out, size_t n) {
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
+    out[idx] = a[idx] - b[idx];
+}
+
+// g = grad x (two planes, zero slots)
+__global__ void k_grad(const float* __restrict__ x, float* __restrict__ g, int N, float invh) {
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    g[idx] = j < N - 1 ? (x[idx + 1] - x[idx]) * invh : 0.f;
+    g[NN + idx] = i < N - 1 ? (x[idx + N] - x[idx]) * invh : 0.f;
+  }
+}
+
+// Copy a vector field (x plane, y plane), zeroing its structural slots.
+__global__ void k_copy_field(const float* __restrict__ a, float* __restrict__ b, int N) {
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    b[idx] = j < N - 1 ? a[idx] : 0.f;
+    b[NN + idx] = i < N - 1 ? a[NN + idx] : 0.f;
+  }
+}
+
+// Generic (unfused) ROF gap terms of (u, p): sum |grad u|, sum (u - I)^2,
+// sum I div p, sum (div p)^2.
+__global__ void __launch_bounds__(256) k_rof_gap(const float* __restrict__ u, const float* __restrict__ p,
+                                                 const float* __restrict__ I, int N, float invh,
+                                                 double* __restrict__ part) {
+  CSum a, b, c, e;
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const bool xr = j < N - 1, xl = j > 0, yd = i < N - 1, yu = i > 0;
+    const float uo = u[idx];
+    const float gx = xr ? (u[idx + 1] - uo) * invh : 0.f;
+    const float gy = yd ? (u[idx + N] - uo) * invh : 0.f;
+    a.add(sqrtf(gx * gx + gy * gy));
+    const float r = uo - I[idx];
+    b.add(r * r);
+    const float dv = ((xr ? p[idx] : 0.f) - (xl ? p[idx - 1] : 0.f) + (yd ? p[NN + idx] : 0.f) -
+                      (yu ? p[NN + idx - N] : 0.f)) * invh;
+    c.add(I[idx] * dv);
+    e.add(dv * dv);
+  }
+  double v[4] = {a.value(), b.value(), c.value(), e.value()};
+  block_reduce_store<4>(v, 0u, part);
+}
+
+// Generic EMD primal terms of m: sum |m|, sum |div m - (f0 - f1)|; and
+// e = -div p for the dual potential.
+__global__ void __launch_bounds__(256) k_emd_primal(const float* __restrict__ m, const float* __restrict__ p,
+                                                    const float* __restrict__ f0, const float* __restrict__ f1,
+                                                    float* __restrict__ e, int N, float invh,
+                                                    double* __restrict__ part) {
+  CSum a, b;
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const bool xr = j < N - 1, xl = j > 0, yd = i < N - 1, yu = i > 0;
+    const float mx = xr ? m[idx] : 0.f, my = yd ? m[NN + idx] : 0.f;
+    a.add(sqrtf(mx * mx + my * my));
+    const float dm = (mx - (xl ? m[idx - 1] : 0.f) + my - (yu ? m[NN + idx - N] : 0.f)) * invh;
+    b.add(fabsf(dm - (f0[idx] - f1[idx])));
+    e[idx] = -((xr ? p[idx] : 0.f) - (xl ? p[idx - 1] : 0.f) + (yd ? p[NN + idx] : 0.f) -
+               (yu ? p[NN + idx - N] : 0.f)) * invh;
+  }
+  double v[2] = {a.value(), b.value()};
+  block_reduce_store<2>(v, 0u, part);
+}
+
+// sum f0, sum f1, sum |f0 - f1|
+__global__ void __launch_bounds__(256) k_mass_stats(const float* __restrict__ f0, const float* __restrict__ f1,
+                                                    size_t NN, double* __restrict__ part) {
+  CSum a, b, c;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const float x = f0[idx], y = f1[idx];
+    a.add(x);
+    b.add(y);
+    c.add(fabsf(x - y));
+  }
+  double v[3] = {a.value(), b.value(), c.value()};
+  block_reduce_store<3>(v, 0u, part);
+}
+
+constexpr int kRB = 16;
+
+inline int grid_1d(size_t n, int threads) {
+  const size_t b = (n + threads - 1) / threads;
+  return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+dim3 fused_grid(int N, int V) { return dim3(ceil_div(ceil_div(N, V), 128), ceil_div(N, kRB)); }
+
+cudaError_t launch_rof_fused(const float* u, const float* pin, const float* I, float* pout, float* r, double* part,
+                             const RofParams& P, bool vec, bool gap, cudaStream_t st) {
+  const int V = vec ? 4 : 1;
+  dim3 g = fused_grid(P.N, V);
+  if (vec) {
+    if (gap) k_rof_fused<4, kRB, true><<<g, 128, 0, st>>>(u, pin, I, pout, r, part, P);
+    else k_rof_fused<4, kRB, false><<<g, 128, 0, st>>>(u, pin, I, pout, r, part, P);
+  } else {
+    if (gap) k_rof_fused<1, kRB, true><<<g, 128, 0, st>>>(u, pin, I, pout, r, part, P);
+    else k_rof_fused<1, kRB, false><<<g, 128, 0, st>>>(u, pin, I, pout, r, part, P);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emd_fused(const float* q, const float* sin_, const float* pin, const float* g, float* sout,
+                             float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
+                             bool gap, cudaStream_t st) {
+  const int V = vec ? 4 : 1;
+  dim3 gr = fused_grid(P.N, V);
+  if (vec) {
+    if (gap) k_emd_fused<4, kRB, true><<<gr, 128, 0, st>>>(q, sin_, pin, g, sout, pout, d, m, e, part, P);
+    else k_emd_fused<4, kRB, false><<<gr, 128, 0, st>>>(q, sin_, pin, g, sout, pout, d, m, e, part, P);
+  } else {
+    if (gap) k_emd_fused<1, kRB, true><<<gr, 128, 0, st>>>(q, sin_, pin, g, sout, pout, d, m, e, part, P);
+    else k_emd_fused<1, kRB, false><<<gr, 128, 0, st>>>(q, sin_, pin, g, sout, pout, d, m, e, part, P);
+  }
+  return cudaGetLastError();
+}
+
+int reduce_blocks_1d(size_t n) { return grid_1d(n, 256) < 1024 ? grid_1d(n, 256) : 1024; }
+
+cudaError_t launch_emd_dual(const float* phi, const float* f0, const float* f1, int N, double* part, int nblk,
+                            cudaStream_t st) {
+  k_emd_dual<<<nblk, 256, 0, st>>>(phi, f0, f1, N, (float)N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rof_stats(const float* I, int N, double* part, int nblk, cudaStream_t st) {
+  k_rof_stats<<<nblk, 256, 0, st>>>(I, N, (float)N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sq_dev(const float* I, size_t NN, float mean, double* part, int nblk, cudaStream_t st) {
+  k_sq_dev<<<nblk, 256, 0, st>>>(I, NN, mean, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rof_gap(const float* u, const float* p, const float* I, int N, double* part, int nblk,
+                           cudaStream_t st) {
+  k_rof_gap<<<nblk, 256, 0, st>>>(u, p, I, N, (float)N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emd_primal(const float* m, const float* p, const float* f0, const float* f1, float* e, int N,
+                              double* part, int nblk, cudaStream_t st) {
+  k_emd_primal<<<nblk, 256, 0, st>>>(m, p, f0, f1, e, N, (float)N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_stats(const float* f0, const float* f1, size_t NN, double* part, int nblk, cudaStream_t st) {
+  k_mass_stats<<<nblk, 256, 0, st>>>(f0, f1, NN, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_final_reduce(const double* part, int nblk, int nq, unsigned maxmask, double* out, cudaStream_t st) {
+  k_final_reduce<<<1, 256, 0, st>>>(part, nblk, nq, maxmask, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rof_init(const float* I, const float* u, const float* pbar, float* p, float* r, const RofParams& P,
+                            cudaStream_t st) {
+  const size_t NN = (size_t)P.N * P.N;
+  k_rof_init<<<grid_1d(NN, 256), 256, 0, st>>>(I, u, pbar, p, r, P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emd_init(const float* m0, const float* pbar, float* p, float* s, const float* g, float* d,
+                            const EmdParams& P, cudaStream_t st) {
+  const size_t NN = (size_t)P.N * P.N;
+  k_emd_init<<<grid_1d(NN, 256), 256, 0, st>>>(m0, pbar, p, s, P);
+  k_affine_rhs<<<grid_1d(NN, 256), 256, 0, st>>>(s, g, d, P.N, P.invh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub(const float* a, const float* b, float* out, size_t n, cudaStream_t st) {
+  k_sub<<<grid_1d(n, 256), 256, 0, st>>>(a, b, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const float* x, float* g, int N, cudaStream_t st) {
+  k_grad<<<grid_1d((size_t)N * N, 256), 256, 0, st>>>(x, g, N, (float)N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_field(const float* a, float* b, int N, cudaStream_t st) {
+  k_copy_field<<<grid_1d((size_t)N * N, 256), 256, 0, st>>>(a, b, N);
+  return cudaGetLastError();
+}
+
+}  // namespace gp

@@ -1,0 +1,48 @@
+// Launchers of the fused stencil kernels and reductions (stencil.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace gp {
+
+struct RofParams {
+  int N;
+  float invh, invh2;  // 1/h, 1/h^2
+  float lt;           // lambda * tau
+  float tau, sigma;
+};
+
+struct EmdParams {
+  int N;
+  float invh;
+  float tau, sigma;
+};
+
+dim3 fused_grid(int N, int V);
+int reduce_blocks_1d(size_t n);
+
+cudaError_t launch_rof_fused(const float* u, const float* pin, const float* I, float* pout, float* r, double* part,
+                             const RofParams& P, bool vec, bool gap, cudaStream_t st);
+cudaError_t launch_emd_fused(const float* q, const float* sin_, const float* pin, const float* g, float* sout,
+                             float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
+                             bool gap, cudaStream_t st);
+cudaError_t launch_emd_dual(const float* phi, const float* f0, const float* f1, int N, double* part, int nblk,
+                            cudaStream_t st);
+cudaError_t launch_rof_stats(const float* I, int N, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_sq_dev(const float* I, size_t NN, float mean, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_rof_gap(const float* u, const float* p, const float* I, int N, double* part, int nblk,
+                           cudaStream_t st);
+cudaError_t launch_emd_primal(const float* m, const float* p, const float* f0, const float* f1, float* e, int N,
+                              double* part, int nblk, cudaStream_t st);
+cudaError_t launch_mass_stats(const float* f0, const float* f1, size_t NN, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_final_reduce(const double* part, int nblk, int nq, unsigned maxmask, double* out, cudaStream_t st);
+cudaError_t launch_rof_init(const float* I, const float* u, const float* pbar, float* p, float* r, const RofParams& P,
+                            cudaStream_t st);
+cudaError_t launch_emd_init(const float* m0, const float* pbar, float* p, float* s, const float* g, float* d,
+                            const EmdParams& P, cudaStream_t st);
+cudaError_t launch_sub(const float* a, const float* b, float* out, size_t n, cudaStream_t st);
+cudaError_t launch_grad(const float* x, float* g, int N, cudaStream_t st);
+cudaError_t launch_copy_field(const float* a, float* b, int N, cudaStream_t st);
+
+}  // namespace gp

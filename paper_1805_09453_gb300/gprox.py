@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI in ``include/gprox.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_lib/libgprox.so``.  Arrays are torch CUDA tensors (float32, contiguous);
+their device pointers and the current torch stream are passed through.  If the
+library is missing, loading fails loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libgprox.so")
+_lib = None
+
+GP_OK, GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_MAXITER, GP_ERR_NONFINITE, GP_ERR_DIVERGED, GP_ERR_MASS, GP_ERR_UNSUPPORTED = range(8)
+STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_CUDA", 3: "GP_ERR_MAXITER", 4: "GP_ERR_NONFINITE",
+                5: "GP_ERR_DIVERGED", 6: "GP_ERR_MASS", 7: "GP_ERR_UNSUPPORTED"}
+PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
+
+EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_last_error", "dct2_poisson",
+           "rof_solve", "emd_solve", "gp_state_create_rof", "gp_state_create_emd", "pd_step", "gp_state_read",
+           "gp_state_gap", "gp_state_destroy", "gp_profile", "gp_profile_kernels", "gp_profile_query"]
+
+
+class Opts(C.Structure):
+    _fields_ = [("max_iters", C.c_int), ("gap_every", C.c_int), ("tol_rel_gap", C.c_double),
+                ("tau", C.c_double), ("sigma", C.c_double), ("tau_scale", C.c_double), ("eps", C.c_double),
+                ("prec", C.c_int), ("use_graph", C.c_int), ("warm_start", C.c_int)]
+
+
+class Report(C.Structure):
+    _fields_ = [("iters", C.c_int), ("status", C.c_int), ("primal", C.c_double), ("dual", C.c_double),
+                ("rel_gap", C.c_double), ("mass_residual", C.c_double), ("tau", C.c_double),
+                ("sigma", C.c_double), ("seconds", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        return d
+
+
+class GproxError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libgprox.so (built by ``paper_1805_09453_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"{_LIB_PATH} is missing: build it with `python -m paper_1805_09453_gb300.build`")
+    L = C.CDLL(_LIB_PATH)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    L.gp_abi_version.restype = i
+    L.gp_default_opts.argtypes = [C.POINTER(Opts)]
+    L.gp_create.argtypes = [C.POINTER(vp), i]
+    L.gp_destroy.argtypes = [vp]
+    L.gp_last_error.argtypes = [vp]
+    L.gp_last_error.restype = C.c_char_p
+    L.dct2_poisson.argtypes = [vp, vp, vp, i, d, i, vp]
+    L.rof_solve.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(Opts), C.POINTER(Report), vp]
+    L.emd_solve.argtypes = [vp, vp, vp, vp, vp, vp, i, C.POINTER(Opts), C.POINTER(Report), vp]
+    L.gp_state_create_rof.argtypes = [vp, C.POINTER(vp), vp, i, d, d, d, vp, vp, vp, vp]
+    L.gp_state_create_emd.argtypes = [vp, C.POINTER(vp), vp, vp, i, d, d, vp, vp, vp, vp]
+    L.pd_step.argtypes = [vp, vp, i, i, vp]
+    L.gp_state_read.argtypes = [vp, vp, vp, vp, vp]
+    L.gp_state_gap.argtypes = [vp, vp, C.POINTER(Report), vp]
+    L.gp_state_destroy.argtypes = [vp]
+    L.gp_profile.argtypes = [vp, i]
+    L.gp_profile_kernels.restype = i
+    L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
+    for name in EXPORTS:
+        if name not in ("gp_abi_version", "gp_default_opts", "gp_last_error", "gp_profile_kernels"):
+            getattr(L, name).restype = i
+    _lib = L
+    return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float32 tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().gp_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = PREC[v]
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """Owns a gp_handle (workspace, cosine-transform tables, scratch)."""
+
+    def __init__(self, device: int | None = None):
+        if device is None:
+            device = torch.cuda.current_device()
+        self._h = C.c_void_p()
+        st = lib().gp_create(C.byref(self._h), int(device))
+        if st != GP_OK:
+            raise GproxError(st, "gp_create failed")
+        self.device = device
+
+    @property
+    def ptr(self):
+        return self._h
+
+    def last_error(self) -> str:
+        return lib().gp_last_error(self._h).decode()
+
+    def check(self, st, allow=(GP_OK,)):
+        if st not in allow:
+            raise GproxError(st, self.last_error())
+        return st
+
+    def close(self):
+        if self._h:
+            lib().gp_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dct2_poisson(h: Handle, b, x, alpha: float, prec="fp32", stream=None) -> int:
+    """x = (alpha - Lap)^{-1} b (Neumann) -- see include/gprox.h."""
+    N = b.shape[-1]
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    return lib().dct2_poisson(h.ptr, _ptr(b), _ptr(x), int(N), float(alpha), p, _stream(stream))
+
+
+def rof_solve(h: Handle, I, u, p=None, lam: float = 8.0, opts: Opts | None = None, stream=None):
+    """ROF G-prox PDHG solve; returns (status, report dict)."""
+    rep = Report()
+    st = lib().rof_solve(h.ptr, _ptr(I), _ptr(u), _ptr(p), int(I.shape[-1]), float(lam),
+                         C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
+    return st, rep.as_dict()
+
+
+def emd_solve(h: Handle, f0, f1, m, p=None, phi=None, opts: Opts | None = None, stream=None):
+    """L1 EMD G-prox PDHG solve; returns (status, report dict)."""
+    rep = Report()
+    st = lib().emd_solve(h.ptr, _ptr(f0), _ptr(f1), _ptr(m), _ptr(p), _ptr(phi), int(f0.shape[-1]),
+                         C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
+    return st, rep.as_dict()
+
+
+class State:
+    """An explicit G-prox PDHG state (gp_state) for step-by-step driving."""
+
+    def __init__(self, h: Handle, kind: str, N: int, *, I=None, lam=None, f0=None, f1=None, tau=1.0, sigma=None,
+                 primal0=None, p0=None, pbar0=None, stream=None):
+        self.h = h
+        self.kind = kind
+        self.N = N
+        self._s = C.c_void_p()
+        sigma = 1.0 / tau if sigma is None else sigma
+        self._keep = (I, f0, f1)  # inputs must outlive the state
+        if kind == "rof":
+            st = lib().gp_state_create_rof(h.ptr, C.byref(self._s), _ptr(I), int(N), float(lam), float(tau),
+                                           float(sigma), _ptr(primal0), _ptr(p0), _ptr(pbar0), _stream(stream))
+        elif kind == "emd":
+            st = lib().gp_state_create_emd(h.ptr, C.byref(self._s), _ptr(f0), _ptr(f1), int(N), float(tau),
+                                           float(sigma), _ptr(primal0), _ptr(p0), _ptr(pbar0), _stream(stream))
+        else:
+            raise ValueError(kind)
+        h.check(st)
+
+    def step(self, n: int, prec="fp32", stream=None) -> int:
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        return self.h.check(lib().pd_step(self.h.ptr, self._s, int(n), p, _stream(stream)))
+
+    def read(self, stream=None):
+        N = self.N
+        dev = torch.device("cuda", self.h.device)
+        prim = torch.empty((N, N) if self.kind == "rof" else (2, N, N), device=dev, dtype=torch.float32)
+        p = torch.empty((2, N, N), device=dev, dtype=torch.float32)
+        self.h.check(lib().gp_state_read(self.h.ptr, self._s, _ptr(prim), _ptr(p), _stream(stream)))
+        return prim, p
+
+    def gap(self, stream=None):
+        rep = Report()
+        self.h.check(lib().gp_state_gap(self.h.ptr, self._s, C.byref(rep), _stream(stream)))
+        return rep.as_dict()
+
+    def close(self):
+        if self._s:
+            lib().gp_state_destroy(self._s)
+            self._s = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def profile(h: Handle, enable: bool) -> int:
+    """Start (clearing the counters) or stop the library's launch profiler."""
+    return lib().gp_profile(h.ptr, 1 if enable else 0)
+
+
+def profile_read(h: Handle):
+    """{kernel class: (total device ms, launches)} recorded by the profiler."""
+    out = {}
+    for k in range(lib().gp_profile_kernels()):
+        name, ms, n = C.c_char_p(), C.c_double(), C.c_longlong()
+        h.check(lib().gp_profile_query(h.ptr, k, C.byref(name), C.byref(ms), C.byref(n)))
+        out[name.value.decode()] = (ms.value, n.value)
+    return out
+
+
+def pd_step(state: State, n_steps: int, prec="fp32", stream=None) -> int:
+    """Run n_steps G-prox PDHG iterations on an explicit state."""
+    return state.step(n_steps, prec, stream)

@@ -1,0 +1,148 @@
+"""L1 EMD G-prox PDHG (section 3.2) on the GPU through the C ABI vs the FP64
+oracle.
+
+EMD minimisers are not unique (section 3.2), so converged runs are compared on
+values (P, D, gap) and invariants; fixed-length runs from a common start are
+deterministic and compared element by element.  FP32 bars: single steps from
+random (infeasible, non-smooth) states 1e-4 relative L2 on m and 3e-4
+absolute on p; P within 1e-5 relative after a fixed number of iterations;
+mass residual below 5e-4 at 64^2 (FP32 rounding of m alone gives ~3e-5: the
+divergence multiplies it by 1/h).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import gprox_oracle as O
+from paper_1805_09453_gb300 import synth
+from tests.gpu_common import random_unit_field, rel_l2, zero_slots
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_1805_09453_gb300 import build, gprox
+
+    build.build()
+    hh = gprox.Handle(0)
+    yield hh
+    hh.close()
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def _pair(N, seed):
+    f0, f1 = synth.gaussian_mixture_pair(N, seed)
+    return f0, f1
+
+
+@pytest.mark.parametrize("N", [2, 5, 16, 33, 64, 128, 129])
+@pytest.mark.parametrize("n_steps", [1, 3])
+def test_emd_steps_from_random_state(h, N, n_steps):
+    from paper_1805_09453_gb300 import gprox
+
+    f0, f1 = _pair(N, N)
+    rng = np.random.default_rng(N)
+    m0 = zero_slots(rng.normal(size=(N, N)), rng.normal(size=(N, N)))
+    p0 = random_unit_field(N, N + 1)
+    pb0 = random_unit_field(N, N + 2, scale=2.0)
+    tau, sigma = 1.3, 0.7
+    s = gprox.State(h, "emd", N, f0=_t(f0), f1=_t(f1), tau=tau, sigma=sigma, primal0=_t(np.stack(m0)),
+                    p0=_t(np.stack(p0)), pbar0=_t(np.stack(pb0)))
+    s.step(n_steps)
+    m, p = s.read()
+    # the library's steps keep m on {div m = f0 - f1}: start the oracle from the
+    # projection of m0 onto that set (identical to the library's first step)
+    hh = 1.0 / N
+    c = O.helmholtz_solve(-(f0.astype(np.float64) - f1 - O.div(m0[0].astype(np.float64), m0[1].astype(np.float64), hh)), 0.0, hh)
+    gx, gy = O.grad(c, hh)
+    m0p = (m0[0] + gx, m0[1] + gy)
+    ref = O.emd_init(f0, f1, m0p, p0, pb0)
+    O.emd_iterate(ref, tau, sigma, n_steps)
+    mc, pc = m.cpu().numpy(), p.cpu().numpy()
+    assert rel_l2(mc, np.stack([ref["mx"], ref["my"]])) < 1e-4
+    assert np.abs(pc[0] - ref["px"]).max() < 3e-4 and np.abs(pc[1] - ref["py"]).max() < 3e-4
+    s.close()
+
+
+def test_emd_zero_start_fixed_iterations(h):
+    from paper_1805_09453_gb300 import gprox
+
+    N, iters = 64, 300
+    f0, f1 = _pair(N, 1)
+    m = torch.empty((2, N, N), device="cuda")
+    p = torch.empty((2, N, N), device="cuda")
+    phi = torch.empty((N, N), device="cuda")
+    st, rep = gprox.emd_solve(h, _t(f0), _t(f1), m, p, phi, gprox.default_opts(max_iters=iters, tol_rel_gap=0.0))
+    h.check(st)
+    ref = O.emd_solve(f0, f1, n_iters=iters)
+    assert abs(rep["primal"] - ref["primal"]) < 1e-5 * ref["primal"]
+    assert abs(rep["dual"] - ref["dual"]) < 1e-4 * abs(ref["dual"])
+    assert rel_l2(m.cpu().numpy(), np.stack([ref["mx"], ref["my"]])) < 1e-3
+    assert rep["mass_residual"] < 5e-4
+    D, phi_ref, _ = O.emd_dual(ref["px"], ref["py"], f0, f1)
+    assert rel_l2(phi.cpu().numpy() - phi.cpu().numpy().mean(), phi_ref - phi_ref.mean()) < 1e-3
+
+
+def test_emd_to_tolerance_matches_oracle_value(h):
+    from paper_1805_09453_gb300 import gprox
+
+    N = 64
+    f0, f1 = _pair(N, 1)
+    m = torch.empty((2, N, N), device="cuda")
+    st, rep = gprox.emd_solve(h, _t(f0), _t(f1), m, opts=gprox.default_opts(max_iters=20000, tol_rel_gap=1e-5))
+    assert st == gprox.GP_OK and rep["rel_gap"] <= 1e-5
+    ref = O.emd_solve(f0, f1, tol=1e-7, max_iters=100000)
+    assert abs(rep["primal"] - ref["primal"]) <= 2e-5 * ref["primal"]
+    assert rep["dual"] <= ref["primal"] * (1 + 1e-6)
+
+
+def test_emd_exact_1d_identity(h):
+    """Densities varying along x only: the optimum is sum_j h |F0_j - F1_j|."""
+    from paper_1805_09453_gb300 import gprox
+
+    N = 64
+    hx = 1.0 / N
+    rng = np.random.default_rng(0)
+    g0, g1 = rng.uniform(0.2, 1, N), rng.uniform(0.2, 1, N)
+    g0 /= g0.sum() * hx
+    g1 /= g1.sum() * hx
+    exact = hx * np.sum(np.abs(hx * np.cumsum(g0) - hx * np.cumsum(g1)))
+    f0, f1 = np.tile(g0, (N, 1)).astype(np.float32), np.tile(g1, (N, 1)).astype(np.float32)
+    m = torch.empty((2, N, N), device="cuda")
+    st, rep = gprox.emd_solve(h, _t(f0), _t(f1), m, opts=gprox.default_opts(max_iters=50000, tol_rel_gap=1e-6))
+    assert st == gprox.GP_OK
+    assert abs(rep["primal"] - exact) < 2e-6 * exact + 1e-7
+
+
+def test_emd_identical_and_errors(h):
+    from paper_1805_09453_gb300 import gprox
+
+    N = 32
+    f0, _ = _pair(N, 3)
+    m = torch.empty((2, N, N), device="cuda")
+    st, rep = gprox.emd_solve(h, _t(f0), _t(f0), m, opts=gprox.default_opts(max_iters=20, tol_rel_gap=0.0))
+    h.check(st)
+    assert rep["primal"] == 0.0 and torch.count_nonzero(m).item() == 0
+    f1 = 2.0 * f0
+    st, _ = gprox.emd_solve(h, _t(f0), _t(f1), m)
+    assert st == gprox.GP_ERR_MASS
+
+
+def test_emd_full_size_two_iterations(h):
+    """4096 x 4096 (the benchmark size): two iterations, element by element,
+    and mass balance div m = f0 - f1."""
+    from paper_1805_09453_gb300 import gprox
+
+    N = 4096
+    f0, f1 = _pair(N, 1)
+    m = torch.empty((2, N, N), device="cuda")
+    st, rep = gprox.emd_solve(h, _t(f0), _t(f1), m, opts=gprox.default_opts(max_iters=2, gap_every=2, tol_rel_gap=0.0))
+    h.check(st)
+    ref = O.emd_solve(f0, f1, n_iters=2)
+    assert rel_l2(m.cpu().numpy(), np.stack([ref["mx"], ref["my"]])) < 2e-5
+    assert abs(rep["primal"] - ref["primal"]) < 1e-5 * ref["primal"]
+    assert rep["mass_residual"] < 1e-4
