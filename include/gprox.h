@@ -111,7 +111,9 @@ GP_API gp_status gp_create(gp_handle* out, int device);
 /* Release a handle and all memory it owns (synchronises the device). NULL is a no-op. */
 GP_API gp_status gp_destroy(gp_handle h);
 
-/* Text of the last error on this handle ("" if none).  Valid until the next call on `h`. */
+/* Text of the last error on this handle ("" if none).  Valid until the next call on `h`.
+ * gp_last_error(NULL) describes the last failed handle-free call
+ * (dct2_poisson_static) of the calling thread. */
 GP_API const char* gp_last_error(gp_handle h);
 
 /*
@@ -202,6 +204,30 @@ GP_API gp_status pd_step(gp_handle h, gp_state s, int n_steps, int prec, void* s
 GP_API gp_status gp_state_read(gp_handle h, gp_state s, float* primal, float* p, void* stream);
 GP_API gp_status gp_state_gap(gp_handle h, gp_state s, gp_report* report, void* stream);
 GP_API gp_status gp_state_destroy(gp_state s);
+
+/*
+ * dct2_poisson_static: dct2_poisson without any device allocation.  The paper
+ * has no counterpart; this entry point serves callers that may not call
+ * cudaMalloc -- a host framework that owns all device memory through its own
+ * pool and budget, or a real-time loop in which an allocation (and the device
+ * synchronisation it can cause) is not allowed.  The caller passes only b and
+ * x; the scratch (one N x N plane) and the transform tables live in
+ * file-scope static device arrays of a fixed size, which every GPU that loads
+ * the library holds until the process exits (4 MiB + ~16 KiB).
+ *   b, x    device pointers of the current device, N*N float32, 16-byte
+ *           aligned; x may equal b.  Same result as dct2_poisson(GP_PREC_FP32).
+ *   N       power of two in [16, 1024]; anything else returns GP_ERR_ARG
+ *           (text in gp_last_error(NULL)).
+ *   alpha   >= 0, as in dct2_poisson.
+ *   stream  cudaStream_t as void*.
+ * All calls share the static arrays: calls that overlap on the GPU (other
+ * streams, other host threads) race and give wrong results.  Nothing in the
+ * arrays needs to start at zero (each pass writes what the next one reads;
+ * the tables are rewritten when N changes).  The first call on a device looks
+ * up the arrays' device addresses with that device current and caches them;
+ * make that first call before any stream capture.
+ */
+GP_API gp_status dct2_poisson_static(const float* b, float* x, int N, double alpha, void* stream);
 
 /*
  * Launch profiler (tracing).  gp_profile(h, 1) clears the counters and starts

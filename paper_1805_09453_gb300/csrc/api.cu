@@ -666,7 +666,7 @@ gp_status gp_destroy(gp_handle h) {
   return GP_OK;
 }
 
-const char* gp_last_error(gp_handle h) { return h ? h->err.c_str() : "null handle"; }
+const char* gp_last_error(gp_handle h) { return h ? h->err.c_str() : static_last_error(); }
 
 gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alpha, int prec, void* stream) {
   if (!h) return GP_ERR_ARG;

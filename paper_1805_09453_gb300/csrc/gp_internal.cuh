@@ -52,6 +52,9 @@ cudaError_t dct_fft_pass(const DctPlan& p, int pass, const float* in, float* out
 cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp,
                                  float alpha, float scale, cudaStream_t st);
 
+// Error text of the last failed handle-free call on this thread (static_solve.cu).
+const char* static_last_error();
+
 // Reduction helpers (stencil.cu)
 constexpr int kRedThreads = 256;
 constexpr int kMaxQ = 4;

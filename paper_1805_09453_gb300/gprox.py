@@ -22,7 +22,8 @@ PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
 
 EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_last_error", "dct2_poisson",
            "rof_solve", "emd_solve", "gp_state_create_rof", "gp_state_create_emd", "pd_step", "gp_state_read",
-           "gp_state_gap", "gp_state_destroy", "gp_profile", "gp_profile_kernels", "gp_profile_query"]
+           "gp_state_gap", "gp_state_destroy", "gp_profile", "gp_profile_kernels", "gp_profile_query",
+           "dct2_poisson_static"]
 
 
 class Opts(C.Structure):
@@ -72,6 +73,7 @@ def lib():
     L.gp_state_read.argtypes = [vp, vp, vp, vp, vp]
     L.gp_state_gap.argtypes = [vp, vp, C.POINTER(Report), vp]
     L.gp_state_destroy.argtypes = [vp]
+    L.dct2_poisson_static.argtypes = [vp, vp, i, d, vp]
     L.gp_profile.argtypes = [vp, i]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
@@ -149,6 +151,16 @@ def dct2_poisson(h: Handle, b, x, alpha: float, prec="fp32", stream=None) -> int
     N = b.shape[-1]
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     return lib().dct2_poisson(h.ptr, _ptr(b), _ptr(x), int(N), float(alpha), p, _stream(stream))
+
+
+def dct2_poisson_static(b, x, alpha: float, stream=None) -> int:
+    """dct2_poisson without device allocation (static scratch, N <= 1024) -- see include/gprox.h."""
+    return lib().dct2_poisson_static(_ptr(b), _ptr(x), int(b.shape[-1]), float(alpha), _stream(stream))
+
+
+def static_last_error() -> str:
+    """Error text of the last failed handle-free call on this thread."""
+    return lib().gp_last_error(None).decode()
 
 
 def rof_solve(h: Handle, I, u, p=None, lam: float = 8.0, opts: Opts | None = None, stream=None):
