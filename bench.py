@@ -42,8 +42,10 @@ BYTES_PER_POINT = {
     "dct_rows_fwd": 8,     # read b, write row spectrum
     "dct_cols_solve": 8,   # read + write the plane in place
     "dct_rows_inv": 8,     # read spectrum, write x
+    "dct_cols_grad": 12,   # read row spectrum, write A and B
+    "dct_rows_grad": 16,   # read A, B; write grad x (2)   (gap checks also write phi)
     "rof_fused": 28,       # read u, p(2), I; write p(2), r
-    "emd_fused": 44,       # read q, s(2), p(2), g; write s(2), p(2), d  (gap steps add m(2), e)
+    "emd_fused": 48,       # read grad q(2), s(2), p(2), g; write s(2), p(2), d  (gap steps add m(2), e)
 }
 
 # ncu DRAM traffic (read + write bytes per launch) of the dominant kernel, from
@@ -290,7 +292,7 @@ def run_ours(args):
     launches = int(sum(v[1] for v in prof.values()))
 
     # whole-iteration HBM fraction (algorithmic bytes of all passes / step time)
-    it_bytes = (3 * 8 + 28) * N * N + (3 * 8 + 44) * N * N  # ROF + EMD per iteration
+    it_bytes = (3 * 8 + 28) * N * N + (8 + 12 + 16 + 48) * N * N  # ROF + EMD per iteration
     whole_frac = (it_bytes * ITERS_PER_STEP * args.steps / (ms_max / 1e3) / 1e9) / peak
 
     # end to end through the public solve calls with host (pinned) buffers

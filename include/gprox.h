@@ -136,6 +136,21 @@ GP_API gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, doub
                        int prec, void* stream);
 
 /*
+ * dct2_poisson_grad: g = grad x for x = (alpha - Laplacian)^{-1} b, the
+ * forward-difference gradient of the discretisation (x plane then y plane;
+ * zero slots).  Sections 3.1 / 3.2 use it for the Hodge split m0 = grad psi
+ * and the Leray step (grad Lap^{-1} div).  For power-of-two N in [16, 8192]
+ * the gradient is synthesised from the cosine spectrum of x, so it keeps FP32
+ * relative precision at any N (differencing an FP32 x loses ~log2(N) bits);
+ * other N difference the dense solve's output.
+ *   b      device, N*N, read only.  g: device, 2*N*N, written.
+ *   alpha  >= 0 (alpha == 0: constant mode dropped).
+ * Errors as dct2_poisson.
+ */
+GP_API gp_status dct2_poisson_grad(gp_handle h, const float* b, float* g, int N, double alpha, int prec,
+                                   void* stream);
+
+/*
  * rof_solve: minimise the ROF energy ||u||_TV + lambda/2 ||u - I||^2
  * (section 3.1) with G-prox PDHG:
  *     u_{n+1} = (lambda tau - Lap)^{-1} (lambda tau I + tau div pbar_n - Lap u_n)

@@ -25,6 +25,8 @@ enum {
   PK_DCT_ROWS_FWD = 0,
   PK_DCT_COLS,
   PK_DCT_ROWS_INV,
+  PK_DCT_COLS_GRAD,
+  PK_DCT_ROWS_GRAD,
   PK_DCT_DENSE,
   PK_ROF_FUSED,
   PK_EMD_FUSED,
@@ -32,10 +34,11 @@ enum {
   PK_SETUP,
   PK_COUNT
 };
-static const char* kProfNames[PK_COUNT] = {"dct_rows_fwd", "dct_cols_solve", "dct_rows_inv", "dct_dense",
-                                           "rof_fused",    "emd_fused",      "reduce",       "setup"};
+static const char* kProfNames[PK_COUNT] = {"dct_rows_fwd", "dct_cols_solve", "dct_rows_inv", "dct_cols_grad",
+                                           "dct_rows_grad", "dct_dense",     "rof_fused",    "emd_fused",
+                                           "reduce",        "setup"};
 // Kernel launches behind one recorded launch of a class.
-static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 5, 1, 1, 1, 1};
+static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 1, 1, 1, 1};
 
 struct Profiler {
   bool on = false;
@@ -81,7 +84,7 @@ struct gp_state_s {
   const float* I = nullptr;
   const float* f0 = nullptr;
   const float* f1 = nullptr;
-  float* prim = nullptr;  // ROF: u (N^2); EMD: q (N^2)
+  float* prim = nullptr;  // ROF: u (N^2); EMD: grad q (2 N^2), also grad phi at gap checks
   float* r = nullptr;     // ROF: next right-hand side; EMD: d = g - div s (= tau div pbar)
   float* p[2] = {nullptr, nullptr};
   float* s[2] = {nullptr, nullptr};  // EMD only
@@ -220,6 +223,32 @@ gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double
   return GP_OK;
 }
 
+// g2 (two planes) = forward-difference gradient of x = scale (alpha - Lap)^{-1} b
+// and, when want_phi, phi = x.  Fast sizes take the gradient in the spectral
+// domain; other sizes difference the dense solve's output (phi is then always
+// written).  tmp holds 2 N^2.
+gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, bool want_phi, float* tmp,
+                     double alpha, double scale, int prec, cudaStream_t st) {
+  const DctPlan* p = nullptr;
+  gp_status s = get_plan(h, N, &p);
+  if (s != GP_OK) return s;
+  if (prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
+  const float a = (float)alpha, sc = (float)scale;
+  const size_t NN = (size_t)N * N;
+  if (p->fft) {
+    float* A = tmp;
+    float* B = tmp + NN;
+    GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return dct_fft_pass(*p, 0, b, A, a, sc, st); }));
+    GP_CUDA(h, plaunch(h, PK_DCT_COLS_GRAD, st, [&] { return dct_grad_cols(*p, A, A, B, a, sc, st); }));
+    GP_CUDA(h, plaunch(h, PK_DCT_ROWS_GRAD, st,
+                       [&] { return dct_grad_rows(*p, A, B, g2, g2 + NN, want_phi ? phi : nullptr, st); }));
+    return GP_OK;
+  }
+  if ((s = solve(h, N, b, phi, tmp, alpha, scale, prec, false, st)) != GP_OK) return s;
+  GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_grad(phi, g2, N, st); }));
+  return GP_OK;
+}
+
 size_t fused_blocks(int N, bool vec) {
   dim3 g = fused_grid(N, vec ? 4 : 1);
   return (size_t)g.x * g.y;
@@ -261,7 +290,7 @@ gp_status alloc_state(gp_handle h, int kind, int N, gp_state* out) {
     return e;
   };
   cudaError_t e = cudaSuccess;
-  if (!e) e = A(&s->prim, NN);
+  if (!e) e = A(&s->prim, kind == KIND_EMD ? 2 * NN : NN);
   if (!e) e = A(&s->r, NN);
   if (!e) e = A(&s->p[0], 2 * NN);
   if (!e) e = A(&s->p[1], 2 * NN);
@@ -339,8 +368,8 @@ gp_status emd_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
   const int N = s->N;
   EmdParams P{N, (float)N, (float)s->tau, (float)s->sigma};
   for (int k = 0; k < n_steps; ++k) {
-    // q = Lap^{-1} d  <=>  (0 - Lap) q = -d
-    gp_status r = solve(h, N, s->r, s->prim, s->tmp, 0.0, -1.0, prec, true, st);
+    // grad q, q = Lap^{-1} d  <=>  (0 - Lap) q = -d
+    gp_status r = solve_grad(h, N, s->r, s->prim, s->phi, false, s->tmp, 0.0, -1.0, prec, st);
     if (r != GP_OK) return r;
     const bool g = gap_last && (k == n_steps - 1);
     const int c = s->cur;
@@ -425,9 +454,8 @@ gp_status emd_setup(gp_state s, const float* f0, const float* f1, double tau, do
     GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_copy_field(m0, s->m, N, st); }));
   } else {
     // Hodge split (section 3.2): Lap psi = f0 - f1 = g  <=>  (0 - Lap) psi = -g; m0 = grad psi
-    gp_status r = solve(h, N, s->g, s->phi, s->tmp, 0.0, -1.0, GP_PREC_FP32, true, st);
+    gp_status r = solve_grad(h, N, s->g, s->m, s->phi, false, s->tmp, 0.0, -1.0, GP_PREC_FP32, st);
     if (r != GP_OK) return r;
-    GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_grad(s->phi, s->m, N, st); }));
   }
   if (p0) GP_CUDA(h, cudaMemcpyAsync(s->p[0], p0, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
   else GP_CUDA(h, cudaMemsetAsync(s->p[0], 0, 2 * NN * sizeof(float), st));
@@ -476,11 +504,12 @@ gp_status state_gap(gp_state s, gp_report* rep, int prec, cudaStream_t st) {
               return launch_emd_primal(s->m, s->p[s->cur], s->f0, s->f1, s->e, N, s->part, nb, st);
             }));
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 2, 0u, h->dres, st); }));
-  // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p = e
-  if ((r = solve(h, N, s->e, s->phi, s->tmp, 0.0, 1.0, prec, true, st)) != GP_OK) return r;
+  // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p = e; grad phi into prim (free between steps)
+  if ((r = solve_grad(h, N, s->e, s->prim, s->phi, true, s->tmp, 0.0, 1.0, prec, st)) != GP_OK) return r;
   const int nd = reduce_blocks_1d(NN);
   double* pd = s->part + (size_t)nb * 4;
-  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_emd_dual(s->phi, s->f0, s->f1, N, pd, nd, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st,
+                     [&] { return launch_emd_dual(s->phi, s->prim, s->f0, s->f1, N, pd, nd, st); }));
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(pd, nd, 2, 2u, h->dres + 2, st); }));
   if ((r = fetch(h, 4, st)) != GP_OK) return r;
   finish_report(rep, h2 * h->hres[0], h2 * h->hres[2] / fmax(1.0, h->hres[3]));
@@ -692,6 +721,33 @@ gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alph
     h->ws_floats = need;
   }
   return solve(h, N, b, x, h->ws, alpha, 1.0, prec, true, (cudaStream_t)stream);
+}
+
+gp_status dct2_poisson_grad(gp_handle h, const float* b, float* g, int N, double alpha, int prec, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
+  if (!(alpha >= 0.0) || !isfinite(alpha)) return fail(h, GP_ERR_ARG, "alpha must be finite and >= 0");
+  if (prec < 0 || prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
+  DeviceGuard dg(h->device);
+  if (!dg.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  gp_status r;
+  if ((r = check_ptr(h, b, "b")) != GP_OK) return r;
+  if ((r = check_ptr(h, g, "g")) != GP_OK) return r;
+  const DctPlan* p = nullptr;
+  if ((r = get_plan(h, N, &p)) != GP_OK) return r;
+  if (p->fft && !(aligned16(b) && aligned16(g)))
+    return fail(h, GP_ERR_ARG, "b and g must be 16-byte aligned for power-of-two N");
+  const size_t NN = (size_t)N * N;
+  const size_t need = 3 * NN;  // 2 N^2 transform scratch + N^2 for the potential
+  if (h->ws_floats < need) {
+    if (h->ws) cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_floats = 0;
+    GP_CUDA(h, cudaMalloc(&h->ws, need * sizeof(float)));
+    h->ws_floats = need;
+  }
+  return solve_grad(h, N, b, g, h->ws + 2 * NN, false, h->ws, alpha, 1.0, prec, (cudaStream_t)stream);
 }
 
 gp_status gp_state_create_rof(gp_handle h, gp_state* out, const float* I, int N, double lambda, double tau,

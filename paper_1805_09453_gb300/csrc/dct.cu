@@ -18,6 +18,14 @@
 //     v_n = x_{2n},  v_{N-1-n} = x_{2n+1},   X_k = Re(e^{-i pi k / 2N} V_k).
 // The complex FFT is a self-sorting (Stockham) radix-16 transform in padded
 // shared memory; each thread holds one 16-point butterfly in registers.
+// Between passes the spectra live in a 4-row-interleaved layout so that the
+// row passes (4 rows per CTA) and the column pass (2 columns per CTA) all
+// move contiguous, full-sector blocks.
+//
+// Gradient variant (EMD): the column and last row pass also synthesise the
+// forward differences of the solution directly from its spectrum, so that the
+// gradient keeps FP32 relative precision at any N (differencing an FP32
+// potential loses about log2(N) bits).
 //
 // Dense path (any N): four FP32 GEMMs with the orthonormal DCT-II matrix.
 #include <math.h>
@@ -92,6 +100,32 @@ __device__ __forceinline__ void dft_reg(float2* v) {
   }
 }
 
+// Twiddles w_r = e^{DIR 2 pi i r m / N}, r < R, from at most four table loads
+// (w1, w2, w4, w8); the others are products of two or three of them.
+template <int R, int DIR>
+__device__ __forceinline__ void stage_twiddles(const float2* __restrict__ tw, int m, float2 (&w)[R]) {
+  w[0] = make_float2(1.f, 0.f);
+  if constexpr (R >= 2) w[1] = __ldg(&tw[m]);
+  if constexpr (R >= 4) {
+    w[2] = __ldg(&tw[2 * m]);
+    w[3] = cmul(w[1], w[2]);
+  }
+  if constexpr (R >= 8) {
+    w[4] = __ldg(&tw[4 * m]);
+#pragma unroll
+    for (int r = 5; r < 8; ++r) w[r] = cmul(w[r - 4], w[4]);
+  }
+  if constexpr (R >= 16) {
+    w[8] = __ldg(&tw[8 * m]);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+  }
+  if constexpr (DIR > 0) {
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r].y = -w[r].y;
+  }
+}
+
 // One self-sorting Stockham stage of radix R over a length-N complex array
 // in (padded) shared memory, TPF threads per transform.
 template <int N, int R, int DIR, int TPF>
@@ -113,13 +147,10 @@ __device__ __forceinline__ void fft_stage(float2* buf, const int Ns, const int t
     const int j = t + b * TPF;
     const int k = j & (Ns - 1);
     if (Ns > 1) {
-      const int step = NB / Ns;  // N / (Ns R)
+      float2 w[R];
+      stage_twiddles<R, DIR>(tw, k * (NB / Ns), w);
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = __ldg(&tw[r * k * step]);
-        if (DIR > 0) w.y = -w.y;
-        v[b][r] = cmul(v[b][r], w);
-      }
+      for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], w[r]);
     }
     dft_reg<R, DIR>(v[b]);
     const int base = (j - k) * R + k;
@@ -148,150 +179,246 @@ __device__ __forceinline__ void fft_smem(float2* buf, int t, const float2* __res
 // Makhoul position of sample n inside the reordered sequence v.
 __device__ __forceinline__ int mk_pos(int n, int N) { return (n & 1) ? (N - 1 - (n >> 1)) : (n >> 1); }
 
-// ----------------------------------------------------------------- pass 1
-template <int LOG2N, int TPF, int FPC>
-__global__ void __launch_bounds__(TPF* FPC) k_dct_rows_fwd(const float* __restrict__ in,
-                                                         float* __restrict__ out,
-                                                         const float2* __restrict__ tw,
-                                                         const float2* __restrict__ wq) {
-  constexpr int N = 1 << LOG2N;
-  constexpr int PADN = N + N / 16;
-  extern __shared__ float2 smem[];
-  const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
-  float2* buf = smem + f * PADN;
-  const size_t ra = (size_t)(2 * (blockIdx.x * FPC + f)) * N;
-  const float* __restrict__ xa = in + ra;
-  const float* __restrict__ xb = xa + N;
-  for (int j = 4 * t; j < N; j += 4 * TPF) {
-    const float4 a = *reinterpret_cast<const float4*>(xa + j);
-    const float4 b = *reinterpret_cast<const float4*>(xb + j);
-    const int hj = j >> 1;
-    buf[padi(hj)] = make_float2(a.x, b.x);
-    buf[padi(N - 1 - hj)] = make_float2(a.y, b.y);
-    buf[padi(hj + 1)] = make_float2(a.z, b.z);
-    buf[padi(N - 2 - hj)] = make_float2(a.w, b.w);
-  }
-  __syncthreads();
-  fft_smem<LOG2N, -1, TPF>(buf, t, tw);
-  float* __restrict__ oa = out + ra;
-  float* __restrict__ ob = oa + N;
-  for (int k = t; k <= N / 2; k += TPF) {
-    if (k == 0) {
-      const float2 z = buf[0];
-      oa[0] = z.x;
-      ob[0] = z.y;
-    } else if (k == N / 2) {
-      const float2 z = buf[padi(N / 2)];
-      oa[N / 2] = z.x * kRsqrt2;
-      ob[N / 2] = z.y * kRsqrt2;
-    } else {
-      const float2 A = buf[padi(k)], B = buf[padi(N - k)];
-      const float2 va = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-      const float2 vb = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-      const float2 w = __ldg(&wq[k]);
-      const float2 ya = cmul(w, va), yb = cmul(w, vb);
-      oa[k] = ya.x;
-      oa[N - k] = -ya.y;
-      ob[k] = yb.x;
-      ob[N - k] = -yb.y;
-    }
-  }
+// Offset of element (row i, column l) in the 4-row-interleaved layout of the
+// intermediate spectra: each block of 4 rows is stored column by column, 4
+// values per column.  A row pass (4 rows per CTA) then reads or writes one
+// contiguous 16N-byte block, and a column pass (2 columns per CTA) reads 32
+// contiguous bytes per block: every pass is coalesced.
+__device__ __forceinline__ size_t b4(int i, int l, int N) {
+  return (size_t)(i >> 2) * 4 * N + (size_t)l * 4 + (i & 3);
+}
+
+// Forward post-step of a two-real-sequence FFT for the pair (k, N-k),
+// 0 < k < N/2: spectra of the real part (a) and imaginary part (b).
+__device__ __forceinline__ void fwd_post(float2 zk, float2 zn, float2 w, float& ak, float& an, float& bk, float& bn) {
+  const float2 va = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+  const float2 vb = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+  const float2 ya = cmul(w, va), yb = cmul(w, vb);
+  ak = ya.x;
+  an = -ya.y;
+  bk = yb.x;
+  bn = -yb.y;
+}
+
+// Unnormalised-inverse pre-step for the pair (k, N-k), 0 < k < N/2: the
+// values Z[k], Z[N-k] whose inverse FFT (Makhoul order) is S_c(P) + i S_c(Q),
+// S_c(X)[j] = X_0 + 2 sum_{l>=1} X_l cos(pi l (2j+1) / 2N).
+__device__ __forceinline__ void inv_pre(float pk, float pn, float qk, float qn, float2 w, float2& zk, float2& zn) {
+  const float2 wc = make_float2(w.x, -w.y);
+  const float2 ua = cmul(wc, make_float2(pk, -pn));
+  const float2 ub = cmul(wc, make_float2(qk, -qn));
+  zk = make_float2(ua.x - ub.y, ua.y + ub.x);
+  zn = make_float2(ua.x + ub.y, -ua.y + ub.x);
+}
+
+// ------------------------------------------------- spectral gradients
+// Forward differences of a cosine series, taken in the spectral domain so that
+// no two nearly equal FP32 values are ever subtracted.  For one dimension,
+// with theta_l = pi l / N,
+//     N (S_c(X)[j+1] - S_c(X)[j]) = N (S_c(P)[j] - (-1)^j S_c(Q)[j]),
+//     P_l = -2 sin^2(theta_l / 2) X_l,   Q_l = sin(theta_l) X_{N-l},  Q_0 = 0,
+// and the right side vanishes at j = N-1 (the zero-flux slot).  Both
+// syntheses are one complex Makhoul inverse.  For the pair (k, N-k) with
+// w = e^{-i pi k / 2N} = (c, -s):
+//     P_k = -2 s^2 X_k,  P_{N-k} = -2 c^2 X_{N-k},  Q_k = 2sc X_{N-k},  Q_{N-k} = 2sc X_k;
+// k = N/2: P = -X, Q = X;  k = 0: P = Q = 0.
+__device__ __forceinline__ void deriv_pre(float xk, float xn, float2 w, float2& zk, float2& zn) {
+  const float c = w.x, s = -w.y;
+  const float sc2 = 2.f * s * c;
+  inv_pre(-2.f * s * s * xk, -2.f * c * c * xn, sc2 * xn, sc2 * xk, w, zk, zn);
 }
 
 // Spectral factor of the solve at frequency (k, l): scale / ((alpha + mu_k + mu_l) N^2),
 // 0 for the constant mode when alpha == 0.
-__device__ __forceinline__ float spec_gain(int k, int l, const float* __restrict__ mu, float mul,
-                                           float alpha, float sN2) {
+__device__ __forceinline__ float spec_gain(int k, const float* __restrict__ mu, float mul, float alpha, float sN2) {
   const float den = alpha + __ldg(&mu[k]) + mul;
   return den > 0.f ? sN2 / den : 0.f;
 }
 
-// ----------------------------------------------------------------- pass 2
-template <int LOG2N, int TPF, int FPC>
-__global__ void __launch_bounds__(TPF* FPC) k_dct_cols_solve(float* __restrict__ data,
-                                                           const float2* __restrict__ tw,
-                                                           const float2* __restrict__ wq,
-                                                           const float* __restrict__ mu, float alpha,
-                                                           float sN2) {
-  constexpr int N = 1 << LOG2N;
-  constexpr int PADN = N + N / 16;
+template <int LOG2N>
+struct FftCfg {
+  static constexpr int N = 1 << LOG2N;
+  static constexpr int PADN = N + N / 16;
+  static constexpr int TPF = N / 16;  // threads per transform
+};
+
+// Makhoul scatter of 4 consecutive samples x[j..j+3] (j % 4 == 0) of two real
+// rows into the complex buffer z = a + i b.
+__device__ __forceinline__ void scatter4(float2* buf, int j, int N, float4 a, float4 b) {
+  const int hj = j >> 1;
+  buf[padi(hj)] = make_float2(a.x, b.x);
+  buf[padi(N - 1 - hj)] = make_float2(a.y, b.y);
+  buf[padi(hj + 1)] = make_float2(a.z, b.z);
+  buf[padi(N - 2 - hj)] = make_float2(a.w, b.w);
+}
+
+// ------------------------------------------------------- row pass, forward
+// CTA = one block of 4 rows (two transforms of two rows each); input
+// row-major, output spectra in the 4-row-interleaved layout.
+template <int LOG2N>
+__global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
+    k_dct_rows_fwd(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
+                   const float2* __restrict__ wq) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
   extern __shared__ float2 smem[];
-  const int col0 = blockIdx.x * (2 * FPC);
-  for (int idx = threadIdx.x; idx < N * FPC; idx += TPF * FPC) {
-    const int n = idx / FPC, f = idx % FPC;
-    const float2 v = *reinterpret_cast<const float2*>(data + (size_t)n * N + col0 + 2 * f);
-    smem[f * PADN + padi(mk_pos(n, N))] = v;
-  }
-  __syncthreads();
   const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
   float2* buf = smem + f * PADN;
-  fft_smem<LOG2N, -1, TPF>(buf, t, tw);
-  const int la = col0 + 2 * f, lb = la + 1;
-  const float mua = __ldg(&mu[la]), mub = __ldg(&mu[lb]);
-  for (int k = t; k <= N / 2; k += TPF) {
-    if (k == 0 || k == N / 2) {
-      const int p = padi(k);
-      const float2 z = buf[p];
-      buf[p] = make_float2(z.x * spec_gain(k, la, mu, mua, alpha, sN2),
-                           z.y * spec_gain(k, lb, mu, mub, alpha, sN2));
-    } else {
-      const float2 A = buf[padi(k)], B = buf[padi(N - k)];
-      const float2 va = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-      const float2 vb = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-      const float2 w = __ldg(&wq[k]);
-      const float2 ya = cmul(w, va), yb = cmul(w, vb);
-      // forward spectra X[k] = Re y, X[N-k] = -Im y, then the eigenvalue gain
-      const float gak = spec_gain(k, la, mu, mua, alpha, sN2);
-      const float gan = spec_gain(N - k, la, mu, mua, alpha, sN2);
-      const float gbk = spec_gain(k, lb, mu, mub, alpha, sN2);
-      const float gbn = spec_gain(N - k, lb, mu, mub, alpha, sN2);
-      const float2 wc = make_float2(w.x, -w.y);
-      // inverse pre-step: V = conj(w) (X[k] - i X[N-k])
-      const float2 ua = cmul(wc, make_float2(ya.x * gak, ya.y * gan));
-      const float2 ub = cmul(wc, make_float2(yb.x * gbk, yb.y * gbn));
-      buf[padi(k)] = make_float2(ua.x - ub.y, ua.y + ub.x);
-      buf[padi(N - k)] = make_float2(ua.x + ub.y, -ua.y + ub.x);
-    }
-  }
+  const int rb = blockIdx.x;
+  const float* __restrict__ xa = in + (size_t)(4 * rb + 2 * f) * N;
+  const float* __restrict__ xb = xa + N;
+  for (int j = 4 * t; j < N; j += 4 * TPF)
+    scatter4(buf, j, N, *reinterpret_cast<const float4*>(xa + j), *reinterpret_cast<const float4*>(xb + j));
   __syncthreads();
-  fft_smem<LOG2N, +1, TPF>(buf, t, tw);
-  for (int idx = threadIdx.x; idx < N * FPC; idx += TPF * FPC) {
-    const int n = idx / FPC, ff = idx % FPC;
-    *reinterpret_cast<float2*>(data + (size_t)n * N + col0 + 2 * ff) = smem[ff * PADN + padi(mk_pos(n, N))];
+  fft_smem<LOG2N, -1, TPF>(buf, t, tw);
+  float* __restrict__ o = out + (size_t)rb * 4 * N;
+  const float2* b0 = smem;
+  const float2* b1 = smem + PADN;
+  for (int k = threadIdx.x; k <= N / 2; k += 2 * TPF) {
+    if (k == 0 || k == N / 2) {
+      const float sc = k == 0 ? 1.f : kRsqrt2;
+      const float2 z0 = b0[padi(k)], z1 = b1[padi(k)];
+      *reinterpret_cast<float4*>(o + 4 * k) = make_float4(sc * z0.x, sc * z0.y, sc * z1.x, sc * z1.y);
+    } else {
+      const float2 w = __ldg(&wq[k]);
+      float4 vk, vn;
+      fwd_post(b0[padi(k)], b0[padi(N - k)], w, vk.x, vn.x, vk.y, vn.y);
+      fwd_post(b1[padi(k)], b1[padi(N - k)], w, vk.z, vn.z, vk.w, vn.w);
+      *reinterpret_cast<float4*>(o + 4 * k) = vk;
+      *reinterpret_cast<float4*>(o + 4 * (N - k)) = vn;
+    }
   }
 }
 
-// ----------------------------------------------------------------- pass 3
-template <int LOG2N, int TPF, int FPC>
-__global__ void __launch_bounds__(TPF* FPC) k_dct_rows_inv(const float* __restrict__ in,
-                                                         float* __restrict__ out,
-                                                         const float2* __restrict__ tw,
-                                                         const float2* __restrict__ wq) {
-  constexpr int N = 1 << LOG2N;
-  constexpr int PADN = N + N / 16;
-  extern __shared__ float2 smem[];
-  const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
-  float2* buf = smem + f * PADN;
-  const size_t ra = (size_t)(2 * (blockIdx.x * FPC + f)) * N;
-  const float* __restrict__ xa = in + ra;
-  const float* __restrict__ xb = xa + N;
+// Load the two columns (2cp, 2cp+1) of the interleaved layout into one
+// Makhoul-ordered complex buffer (column 2cp real, 2cp+1 imaginary).
+template <int N, int TPF>
+__device__ __forceinline__ void load_cols(float2* buf, const float* __restrict__ src, int cp, int t) {
+  float* fb = reinterpret_cast<float*>(buf);
+  for (int idx = t; idx < N / 2; idx += TPF) {
+    const int rb = idx >> 1, c = idx & 1;
+    const float4 v = *reinterpret_cast<const float4*>(src + (size_t)rb * 4 * N + (size_t)(2 * cp + c) * 4);
+    const int n = 4 * rb;
+    fb[2 * padi(mk_pos(n, N)) + c] = v.x;
+    fb[2 * padi(mk_pos(n + 1, N)) + c] = v.y;
+    fb[2 * padi(mk_pos(n + 2, N)) + c] = v.z;
+    fb[2 * padi(mk_pos(n + 3, N)) + c] = v.w;
+  }
+}
+
+// Store the synthesised columns (real part -> column 2cp, imaginary -> 2cp+1).
+template <int N, int TPF>
+__device__ __forceinline__ void store_cols(const float2* buf, float* __restrict__ dst, int cp, int t) {
+  const float* fb = reinterpret_cast<const float*>(buf);
+  for (int idx = t; idx < N / 2; idx += TPF) {
+    const int rb = idx >> 1, c = idx & 1;
+    const int n = 4 * rb;
+    const float4 v = make_float4(fb[2 * padi(mk_pos(n, N)) + c], fb[2 * padi(mk_pos(n + 1, N)) + c],
+                                 fb[2 * padi(mk_pos(n + 2, N)) + c], fb[2 * padi(mk_pos(n + 3, N)) + c]);
+    *reinterpret_cast<float4*>(dst + (size_t)rb * 4 * N + (size_t)(2 * cp + c) * 4) = v;
+  }
+}
+
+// Forward column transform + gain: leaves the gained spectra of both columns
+// in `buf` as the inverse pre-step values (plain synthesis) when X == nullptr,
+// or stores them in X[k] = (X_a[k], X_b[k]) when X != nullptr.
+template <int N, int TPF>
+__device__ __forceinline__ void col_spectrum(float2* buf, float2* X, int cp, int t, const float2* __restrict__ wq,
+                                             const float* __restrict__ mu, float alpha, float sN2) {
+  const int la = 2 * cp, lb = la + 1;
+  const float mua = __ldg(&mu[la]), mub = __ldg(&mu[lb]);
   for (int k = t; k <= N / 2; k += TPF) {
-    if (k == 0) {
-      buf[0] = make_float2(xa[0], xb[0]);
-    } else if (k == N / 2) {
-      buf[padi(N / 2)] = make_float2(kSqrt2 * xa[N / 2], kSqrt2 * xb[N / 2]);
+    if (k == 0 || k == N / 2) {
+      const int pk = padi(k);
+      const float2 z = buf[pk];
+      const float ga = spec_gain(k, mu, mua, alpha, sN2), gb = spec_gain(k, mu, mub, alpha, sN2);
+      if (X) {
+        const float sc = k == 0 ? 1.f : kRsqrt2;
+        X[k] = make_float2(sc * z.x * ga, sc * z.y * gb);
+      } else {
+        buf[pk] = make_float2(z.x * ga, z.y * gb);  // k = N/2: the 1/sqrt2 and sqrt2 cancel
+      }
     } else {
       const float2 w = __ldg(&wq[k]);
-      const float2 wc = make_float2(w.x, -w.y);
-      const float2 ua = cmul(wc, make_float2(xa[k], -xa[N - k]));
-      const float2 ub = cmul(wc, make_float2(xb[k], -xb[N - k]));
-      buf[padi(k)] = make_float2(ua.x - ub.y, ua.y + ub.x);
-      buf[padi(N - k)] = make_float2(ua.x + ub.y, -ua.y + ub.x);
+      float ak, an, bk, bn;
+      fwd_post(buf[padi(k)], buf[padi(N - k)], w, ak, an, bk, bn);
+      ak *= spec_gain(k, mu, mua, alpha, sN2);
+      an *= spec_gain(N - k, mu, mua, alpha, sN2);
+      bk *= spec_gain(k, mu, mub, alpha, sN2);
+      bn *= spec_gain(N - k, mu, mub, alpha, sN2);
+      if (X) {
+        X[k] = make_float2(ak, bk);
+        X[N - k] = make_float2(an, bn);
+      } else {
+        float2 zk, zn;
+        inv_pre(ak, an, bk, bn, w, zk, zn);
+        buf[padi(k)] = zk;
+        buf[padi(N - k)] = zn;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------ column pass, solve
+// CTA = one column pair; in place on the interleaved spectra: forward DCT-II
+// along the column, divide by the eigenvalue, inverse.
+template <int LOG2N>
+__global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 4 : 1)) k_dct_cols_solve(float* __restrict__ data,
+                                                                      const float2* __restrict__ tw,
+                                                                      const float2* __restrict__ wq,
+                                                                      const float* __restrict__ mu, float alpha,
+                                                                      float sN2) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, TPF = C::TPF;
+  extern __shared__ float2 smem[];
+  const int cp = blockIdx.x, t = threadIdx.x;
+  load_cols<N, TPF>(smem, data, cp, t);
+  __syncthreads();
+  fft_smem<LOG2N, -1, TPF>(smem, t, tw);
+  col_spectrum<N, TPF>(smem, nullptr, cp, t, wq, mu, alpha, sN2);
+  __syncthreads();
+  fft_smem<LOG2N, +1, TPF>(smem, t, tw);
+  store_cols<N, TPF>(smem, data, cp, t);
+}
+
+// ------------------------------------------------------- row pass, inverse
+// CTA = one block of 4 rows: interleaved spectra in, row-major x out.
+template <int LOG2N>
+__global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
+    k_dct_rows_inv(const float* __restrict__ in, float* __restrict__ out, const float2* __restrict__ tw,
+                   const float2* __restrict__ wq) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  extern __shared__ float2 smem[];
+  const int rb = blockIdx.x;
+  const float* __restrict__ src = in + (size_t)rb * 4 * N;
+  float2* b0 = smem;
+  float2* b1 = smem + PADN;
+  for (int k = threadIdx.x; k <= N / 2; k += 2 * TPF) {
+    const float4 vk = *reinterpret_cast<const float4*>(src + 4 * k);
+    if (k == 0) {
+      b0[0] = make_float2(vk.x, vk.y);
+      b1[0] = make_float2(vk.z, vk.w);
+    } else if (k == N / 2) {
+      b0[padi(k)] = make_float2(kSqrt2 * vk.x, kSqrt2 * vk.y);
+      b1[padi(k)] = make_float2(kSqrt2 * vk.z, kSqrt2 * vk.w);
+    } else {
+      const float4 vn = *reinterpret_cast<const float4*>(src + 4 * (N - k));
+      const float2 w = __ldg(&wq[k]);
+      float2 zk, zn;
+      inv_pre(vk.x, vn.x, vk.y, vn.y, w, zk, zn);
+      b0[padi(k)] = zk;
+      b0[padi(N - k)] = zn;
+      inv_pre(vk.z, vn.z, vk.w, vn.w, w, zk, zn);
+      b1[padi(k)] = zk;
+      b1[padi(N - k)] = zn;
     }
   }
   __syncthreads();
+  const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
+  float2* buf = smem + f * PADN;
   fft_smem<LOG2N, +1, TPF>(buf, t, tw);
-  float* __restrict__ oa = out + ra;
+  float* __restrict__ oa = out + (size_t)(4 * rb + 2 * f) * N;
   float* __restrict__ ob = oa + N;
   for (int j = 4 * t; j < N; j += 4 * TPF) {
     const int hj = j >> 1;
@@ -302,39 +429,219 @@ __global__ void __launch_bounds__(TPF* FPC) k_dct_rows_inv(const float* __restri
   }
 }
 
-// Launch configuration per size: threads per transform (TPF = N/16 / split)
-// and transforms per CTA for the row passes (FPR) and the column pass (FPCc).
+// --------------------------------------------------- column pass, gradient
+// CTA = one column pair.  After the forward transform and the gain, three
+// syntheses along the column:
+//   A[:, pair] = S_c(X)                      (plain; feeds the x-derivative and phi)
+//   B[:, a]    = D_y S_c(X_a),  B[:, b] = D_y S_c(X_b)
+// `in` may alias A.  Shared memory: transform buffer, gained spectra, D_y of a.
 template <int LOG2N>
-struct FftCfg {
-  static constexpr int N = 1 << LOG2N;
-  static constexpr int TPF = N / 16;
-  static constexpr int FPR = (TPF >= 256) ? 1 : (256 / TPF < N / 2 ? 256 / TPF : N / 2);
-  static constexpr int FPC = (N >= 4096) ? 2 : (TPF >= 128 ? 2 : (256 / TPF < 8 ? 256 / TPF : 8));
-};
+__global__ void __launch_bounds__(FftCfg<LOG2N>::TPF) k_dct_cols_grad(const float* __restrict__ in, float* A, float* B,
+                                                                     const float2* __restrict__ tw,
+                                                                     const float2* __restrict__ wq,
+                                                                     const float* __restrict__ mu, float alpha,
+                                                                     float sN2) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  extern __shared__ float2 smem[];
+  float2* buf = smem;
+  float2* X = smem + PADN;                               // N complex
+  float* Da = reinterpret_cast<float*>(smem + PADN + N);  // N floats
+  const int cp = blockIdx.x, t = threadIdx.x;
+  const float fN = (float)N;
+  load_cols<N, TPF>(buf, in, cp, t);
+  __syncthreads();
+  fft_smem<LOG2N, -1, TPF>(buf, t, tw);
+  col_spectrum<N, TPF>(buf, X, cp, t, wq, mu, alpha, sN2);
+  __syncthreads();
+  for (int pass = 0; pass < 3; ++pass) {
+    for (int k = t; k <= N / 2; k += TPF) {
+      const float2 xk = X[k];
+      if (pass == 0) {
+        if (k == 0) {
+          buf[0] = xk;
+        } else if (k == N / 2) {
+          buf[padi(k)] = make_float2(kSqrt2 * xk.x, kSqrt2 * xk.y);
+        } else {
+          const float2 xn = X[N - k];
+          float2 zk, zn;
+          inv_pre(xk.x, xn.x, xk.y, xn.y, __ldg(&wq[k]), zk, zn);
+          buf[padi(k)] = zk;
+          buf[padi(N - k)] = zn;
+        }
+      } else {
+        const float x0 = pass == 1 ? xk.x : xk.y;
+        if (k == 0) {
+          buf[0] = make_float2(0.f, 0.f);
+        } else if (k == N / 2) {
+          buf[padi(k)] = make_float2(-kSqrt2 * x0, kSqrt2 * x0);
+        } else {
+          const float2 xn2 = X[N - k];
+          float2 zk, zn;
+          deriv_pre(x0, pass == 1 ? xn2.x : xn2.y, __ldg(&wq[k]), zk, zn);
+          buf[padi(k)] = zk;
+          buf[padi(N - k)] = zn;
+        }
+      }
+    }
+    __syncthreads();
+    fft_smem<LOG2N, +1, TPF>(buf, t, tw);
+    if (pass == 0) {
+      store_cols<N, TPF>(buf, A, cp, t);
+    } else if (pass == 1) {
+      for (int n = t; n < N; n += TPF) {
+        const float2 z = buf[padi(mk_pos(n, N))];
+        Da[n] = (n == N - 1) ? 0.f : fN * (z.x - ((n & 1) ? -z.y : z.y));
+      }
+    } else {
+      for (int idx = t; idx < N / 2; idx += TPF) {
+        const int rb = idx >> 1, c = idx & 1;
+        float v[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int n = 4 * rb + r;
+          if (c == 0) {
+            v[r] = Da[n];
+          } else {
+            const float2 z = buf[padi(mk_pos(n, N))];
+            v[r] = (n == N - 1) ? 0.f : fN * (z.x - ((n & 1) ? -z.y : z.y));
+          }
+        }
+        *reinterpret_cast<float4*>(B + (size_t)rb * 4 * N + (size_t)(2 * cp + c) * 4) =
+            make_float4(v[0], v[1], v[2], v[3]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ row pass, gradient
+// CTA = one block of 4 rows (two transforms).  Per transform slot f (rows
+// r0 = 4 rb + 2f and r0 + 1):
+//   gx[r0] = D_x S_c(A[r0]),  gx[r0+1] = D_x S_c(A[r0+1]),  gy[r0, r0+1] = S_c(B[r0, r0+1]),
+//   and phi[r0, r0+1] = S_c(A[r0, r0+1]) when phi != nullptr.
+// A, B interleaved; gx, gy, phi row-major; gx has its zero slot at j = N-1.
+template <int LOG2N>
+__global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
+    k_dct_rows_grad(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ gx,
+                    float* __restrict__ gy, float* __restrict__ phi, const float2* __restrict__ tw,
+                    const float2* __restrict__ wq) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  extern __shared__ float2 smem[];
+  const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
+  float2* buf = smem + f * PADN;
+  const int rb = blockIdx.x;
+  const int r0 = 4 * rb + 2 * f;
+  const float fN = (float)N;
+  const int npass = phi ? 4 : 3;
+  for (int pass = 0; pass < npass; ++pass) {
+    // pass 0: D_x of A row r0; 1: D_x of A row r0+1; 2: plain of B rows r0, r0+1; 3: plain of A rows
+    const float* __restrict__ src = (pass == 2 ? B : A) + (size_t)rb * 4 * N;
+    for (int k = t; k <= N / 2; k += TPF) {
+      const float2 xk2 = *reinterpret_cast<const float2*>(src + 4 * k + 2 * f);
+      if (pass < 2) {
+        const float xk = pass == 0 ? xk2.x : xk2.y;
+        if (k == 0) {
+          buf[0] = make_float2(0.f, 0.f);
+        } else if (k == N / 2) {
+          buf[padi(k)] = make_float2(-kSqrt2 * xk, kSqrt2 * xk);
+        } else {
+          const float2 xn2 = *reinterpret_cast<const float2*>(src + 4 * (N - k) + 2 * f);
+          float2 zk, zn;
+          deriv_pre(xk, pass == 0 ? xn2.x : xn2.y, __ldg(&wq[k]), zk, zn);
+          buf[padi(k)] = zk;
+          buf[padi(N - k)] = zn;
+        }
+      } else {
+        if (k == 0) {
+          buf[0] = xk2;
+        } else if (k == N / 2) {
+          buf[padi(k)] = make_float2(kSqrt2 * xk2.x, kSqrt2 * xk2.y);
+        } else {
+          const float2 xn2 = *reinterpret_cast<const float2*>(src + 4 * (N - k) + 2 * f);
+          float2 zk, zn;
+          inv_pre(xk2.x, xn2.x, xk2.y, xn2.y, __ldg(&wq[k]), zk, zn);
+          buf[padi(k)] = zk;
+          buf[padi(N - k)] = zn;
+        }
+      }
+    }
+    __syncthreads();
+    fft_smem<LOG2N, +1, TPF>(buf, t, tw);
+    if (pass < 2) {
+      float* __restrict__ o = gx + (size_t)(r0 + pass) * N;
+      for (int j = 4 * t; j < N; j += 4 * TPF) {
+        const int hj = j >> 1;
+        const float2 z0 = buf[padi(hj)], z1 = buf[padi(N - 1 - hj)];
+        const float2 z2 = buf[padi(hj + 1)], z3 = buf[padi(N - 2 - hj)];
+        float4 v = make_float4(fN * (z0.x - z0.y), fN * (z1.x + z1.y), fN * (z2.x - z2.y), fN * (z3.x + z3.y));
+        if (j + 4 == N) v.w = 0.f;  // zero-flux slot
+        *reinterpret_cast<float4*>(o + j) = v;
+      }
+    } else {
+      float* __restrict__ oa = (pass == 2 ? gy : phi) + (size_t)r0 * N;
+      float* __restrict__ ob = oa + N;
+      for (int j = 4 * t; j < N; j += 4 * TPF) {
+        const int hj = j >> 1;
+        const float2 z0 = buf[padi(hj)], z1 = buf[padi(N - 1 - hj)];
+        const float2 z2 = buf[padi(hj + 1)], z3 = buf[padi(N - 2 - hj)];
+        *reinterpret_cast<float4*>(oa + j) = make_float4(z0.x, z1.x, z2.x, z3.x);
+        *reinterpret_cast<float4*>(ob + j) = make_float4(z0.y, z1.y, z2.y, z3.y);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K>
+cudaError_t set_smem(K k, size_t bytes) {
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
 
 template <int LOG2N>
 cudaError_t launch_fft_pass(const DctPlan& p, int pass, const float* in, float* out, float alpha, float scale,
                             cudaStream_t st) {
-  using Cfg = FftCfg<LOG2N>;
-  constexpr int N = Cfg::N;
-  constexpr int PADN = N + N / 16;
-  const size_t smR = (size_t)Cfg::FPR * PADN * sizeof(float2);
-  const size_t smC = (size_t)Cfg::FPC * PADN * sizeof(float2);
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  const size_t sm1 = (size_t)PADN * sizeof(float2), sm2 = 2 * sm1;
   cudaError_t e;
   if (pass == 0) {
-    auto k = k_dct_rows_fwd<LOG2N, Cfg::TPF, Cfg::FPR>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smR))) return e;
-    k<<<N / 2 / Cfg::FPR, Cfg::TPF * Cfg::FPR, smR, st>>>(in, out, p.tw, p.wq);
+    if ((e = set_smem(k_dct_rows_fwd<LOG2N>, sm2))) return e;
+    k_dct_rows_fwd<LOG2N><<<N / 4, 2 * TPF, sm2, st>>>(in, out, p.tw, p.wq);
   } else if (pass == 1) {
-    auto k = k_dct_cols_solve<LOG2N, Cfg::TPF, Cfg::FPC>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smC))) return e;
+    if ((e = set_smem(k_dct_cols_solve<LOG2N>, sm1))) return e;
     const float sN2 = (float)((double)scale / ((double)N * (double)N));
-    k<<<N / 2 / Cfg::FPC, Cfg::TPF * Cfg::FPC, smC, st>>>(out, p.tw, p.wq, p.mu, alpha, sN2);
+    k_dct_cols_solve<LOG2N><<<N / 2, TPF, sm1, st>>>(out, p.tw, p.wq, p.mu, alpha, sN2);
   } else {
-    auto k = k_dct_rows_inv<LOG2N, Cfg::TPF, Cfg::FPR>;
-    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smR))) return e;
-    k<<<N / 2 / Cfg::FPR, Cfg::TPF * Cfg::FPR, smR, st>>>(in, out, p.tw, p.wq);
+    if ((e = set_smem(k_dct_rows_inv<LOG2N>, sm2))) return e;
+    k_dct_rows_inv<LOG2N><<<N / 4, 2 * TPF, sm2, st>>>(in, out, p.tw, p.wq);
   }
+  return cudaGetLastError();
+}
+
+template <int LOG2N>
+cudaError_t launch_grad_cols(const DctPlan& p, const float* in, float* A, float* B, float alpha, float scale,
+                             cudaStream_t st) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  const size_t sm = (size_t)PADN * sizeof(float2) + (size_t)N * sizeof(float2) + (size_t)N * sizeof(float);
+  cudaError_t e;
+  if ((e = set_smem(k_dct_cols_grad<LOG2N>, sm))) return e;
+  const float sN2 = (float)((double)scale / ((double)N * (double)N));
+  k_dct_cols_grad<LOG2N><<<N / 2, TPF, sm, st>>>(in, A, B, p.tw, p.wq, p.mu, alpha, sN2);
+  return cudaGetLastError();
+}
+
+template <int LOG2N>
+cudaError_t launch_grad_rows(const DctPlan& p, const float* A, const float* B, float* gx, float* gy, float* phi,
+                             cudaStream_t st) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  const size_t sm = 2 * (size_t)PADN * sizeof(float2);
+  cudaError_t e;
+  if ((e = set_smem(k_dct_rows_grad<LOG2N>, sm))) return e;
+  k_dct_rows_grad<LOG2N><<<N / 4, 2 * TPF, sm, st>>>(A, B, gx, gy, phi, p.tw, p.wq);
   return cudaGetLastError();
 }
 
@@ -409,22 +716,43 @@ cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, flo
   return cudaGetLastError();
 }
 
+#define GP_FFT_DISPATCH(N, CALL)   \
+  switch (N) {                     \
+    case 16: return CALL(4);       \
+    case 32: return CALL(5);       \
+    case 64: return CALL(6);       \
+    case 128: return CALL(7);      \
+    case 256: return CALL(8);      \
+    case 512: return CALL(9);      \
+    case 1024: return CALL(10);    \
+    case 2048: return CALL(11);    \
+    case 4096: return CALL(12);    \
+    case 8192: return CALL(13);    \
+    default: return cudaErrorInvalidValue; \
+  }
+
 cudaError_t dct_fft_pass(const DctPlan& p, int pass, const float* in, float* out, float alpha, float scale,
                          cudaStream_t st) {
   if (!p.fft) return cudaErrorInvalidValue;
-  switch (p.N) {
-    case 16: return launch_fft_pass<4>(p, pass, in, out, alpha, scale, st);
-    case 32: return launch_fft_pass<5>(p, pass, in, out, alpha, scale, st);
-    case 64: return launch_fft_pass<6>(p, pass, in, out, alpha, scale, st);
-    case 128: return launch_fft_pass<7>(p, pass, in, out, alpha, scale, st);
-    case 256: return launch_fft_pass<8>(p, pass, in, out, alpha, scale, st);
-    case 512: return launch_fft_pass<9>(p, pass, in, out, alpha, scale, st);
-    case 1024: return launch_fft_pass<10>(p, pass, in, out, alpha, scale, st);
-    case 2048: return launch_fft_pass<11>(p, pass, in, out, alpha, scale, st);
-    case 4096: return launch_fft_pass<12>(p, pass, in, out, alpha, scale, st);
-    case 8192: return launch_fft_pass<13>(p, pass, in, out, alpha, scale, st);
-    default: return cudaErrorInvalidValue;
-  }
+#define GP_CALL(L) launch_fft_pass<L>(p, pass, in, out, alpha, scale, st)
+  GP_FFT_DISPATCH(p.N, GP_CALL)
+#undef GP_CALL
+}
+
+cudaError_t dct_grad_cols(const DctPlan& p, const float* in, float* A, float* B, float alpha, float scale,
+                          cudaStream_t st) {
+  if (!p.fft) return cudaErrorInvalidValue;
+#define GP_CALL(L) launch_grad_cols<L>(p, in, A, B, alpha, scale, st)
+  GP_FFT_DISPATCH(p.N, GP_CALL)
+#undef GP_CALL
+}
+
+cudaError_t dct_grad_rows(const DctPlan& p, const float* A, const float* B, float* gx, float* gy, float* phi,
+                          cudaStream_t st) {
+  if (!p.fft) return cudaErrorInvalidValue;
+#define GP_CALL(L) launch_grad_rows<L>(p, A, B, gx, gy, phi, st)
+  GP_FFT_DISPATCH(p.N, GP_CALL)
+#undef GP_CALL
 }
 
 cudaError_t dct_plan_init(DctPlan& p, int N) {

@@ -45,9 +45,18 @@ void dct_plan_free(DctPlan& p);
 //   pass 0: tmp = row DCT-II of b          (in = b,   out = tmp)
 //   pass 1: column solve in place on tmp    (out = tmp)
 //   pass 2: x = row inverse DCT-II of tmp   (in = tmp, out = x)
-// b may alias x.
+// tmp (N*N floats) holds spectra in a 4-row-interleaved layout; b may alias x.
 cudaError_t dct_fft_pass(const DctPlan& p, int pass, const float* in, float* out, float alpha, float scale,
                          cudaStream_t st);
+// Gradient solve: after pass 0 (tmp = row spectra of b),
+//   dct_grad_cols(tmp -> A, B)  and  dct_grad_rows(A, B -> gx, gy [, phi])
+// give gx, gy = forward-difference gradient of x = scale (alpha - Lap)^{-1} b,
+// taken in the spectral domain, and optionally x itself (phi).  A may alias
+// tmp; A and B are N*N each.
+cudaError_t dct_grad_cols(const DctPlan& p, const float* in, float* A, float* B, float alpha, float scale,
+                          cudaStream_t st);
+cudaError_t dct_grad_rows(const DctPlan& p, const float* A, const float* B, float* gx, float* gy, float* phi,
+                          cudaStream_t st);
 // Dense-matrix form (any N): tmp must hold 2*N*N floats.
 cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp,
                                  float alpha, float scale, cudaStream_t st);

@@ -234,9 +234,10 @@ __global__ void __launch_bounds__(128) k_rof_fused(const float* __restrict__ u, 
 //     q_n = Lap^{-1} (g - div s_n),   m_{n+1} = s_n + grad q_n.
 // For a feasible m_n (div m_n = g) this is m_n - tau (pbar_n - grad Lap^{-1} div pbar_n),
 // the update of section 3.2; in floating point it re-imposes div m = g at
-// every step instead of carrying each step's solve error forward.
+// every step instead of carrying each step's solve error forward.  grad q_n
+// comes from the spectral gradient of the cosine solve (two planes, zero slots).
 template <int V, int RB, bool GAP>
-__global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ q, const float* __restrict__ sin_,
+__global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ gq, const float* __restrict__ sin_,
                                                    const float* __restrict__ pin, const float* __restrict__ g,
                                                    float* __restrict__ sout, float* __restrict__ pout,
                                                    float* __restrict__ d, float* __restrict__ m,
@@ -247,28 +248,26 @@ __global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ q, 
   const int i0 = blockIdx.y * RB;
   CSum s_m, s_mass;
   if (j0 < N) {
+    const float* __restrict__ gqx = gq;
+    const float* __restrict__ gqy = gq + NN;
     const float* __restrict__ sx = sin_;
     const float* __restrict__ sy = sin_ + NN;
     const float* __restrict__ px = pin;
     const float* __restrict__ py = pin + NN;
-    float qa[V + 2], qb[V + 2];
     float sy_up[V], p1y_up[V], my_up[V];  // row above: new s_y, new p_y, m_y
-    load_row<V>(qa, q, i0, N, j0);
     if (i0 > 0) {
-      float qp[V + 2];
-      load_row<V>(qp, q, i0 - 1, N, j0);
       const size_t ro = (size_t)(i0 - 1) * N;
-      float sxv[V], syv[V], pxv[V], pyv[V];
+      float gxv[V], gyv[V], sxv[V], syv[V], pxv[V], pyv[V];
+      ldv<V>(gxv, gqx + ro + j0);
+      ldv<V>(gyv, gqy + ro + j0);
       ldv<V>(sxv, sx + ro + j0);
       ldv<V>(syv, sy + ro + j0);
       ldv<V>(pxv, px + ro + j0);
       ldv<V>(pyv, py + ro + j0);
 #pragma unroll
       for (int c = 0; c < V; ++c) {
-        const int j = j0 + c;
-        const float gx = (j < N - 1) ? (qp[c + 2] - qp[c + 1]) * P.invh : 0.f;
-        const float gy = (qa[c + 1] - qp[c + 1]) * P.invh;
-        const float mx = sxv[c] + gx, my = syv[c] + gy;
+        const bool xr = j0 + c < N - 1;
+        const float mx = xr ? sxv[c] + gxv[c] : 0.f, my = syv[c] + gyv[c];
         float p1x, p1y;
         proj2(pxv[c] + P.sigma * mx, pyv[c] + P.sigma * my, p1x, p1y);
         sy_up[c] = my - P.tau * (2.f * p1y - pyv[c]);
@@ -282,17 +281,19 @@ __global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ q, 
     const int iend = min(i0 + RB, N);
     for (int i = i0; i < iend; ++i) {
       const size_t ro = (size_t)i * N;
-      load_row<V>(qb, q, i + 1, N, j0);
-      float sxv[V + 1], syv[V + 1], pxv[V + 1], pyv[V + 1];
+      float gxv[V + 1], gyv[V + 1], sxv[V + 1], syv[V + 1], pxv[V + 1], pyv[V + 1];
+      ldv<V>(&gxv[1], gqx + ro + j0);
+      ldv<V>(&gyv[1], gqy + ro + j0);
       ldv<V>(&sxv[1], sx + ro + j0);
       ldv<V>(&syv[1], sy + ro + j0);
       ldv<V>(&pxv[1], px + ro + j0);
       ldv<V>(&pyv[1], py + ro + j0);
       if (j0 > 0) {
+        gxv[0] = gqx[ro + j0 - 1]; gyv[0] = gqy[ro + j0 - 1];
         sxv[0] = sx[ro + j0 - 1]; syv[0] = sy[ro + j0 - 1];
         pxv[0] = px[ro + j0 - 1]; pyv[0] = py[ro + j0 - 1];
       } else {
-        sxv[0] = syv[0] = pxv[0] = pyv[0] = 0.f;
+        gxv[0] = gyv[0] = sxv[0] = syv[0] = pxv[0] = pyv[0] = 0.f;
       }
       float gv[V];
       ldv<V>(gv, g + ro + j0);
@@ -301,17 +302,13 @@ __global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ q, 
       for (int c = 0; c <= V; ++c) {
         const int j = j0 - 1 + c;
         const bool xr = j < N - 1, yd = i < N - 1;
-        const float gx = xr ? (qa[c + 1] - qa[c]) * P.invh : 0.f;
-        const float gy = yd ? (qb[c] - qa[c]) * P.invh : 0.f;
-        mxv[c] = xr ? sxv[c] + gx : 0.f;
-        myv[c] = yd ? syv[c] + gy : 0.f;
+        mxv[c] = xr ? sxv[c] + gxv[c] : 0.f;
+        myv[c] = yd ? syv[c] + gyv[c] : 0.f;
         proj2(pxv[c] + P.sigma * mxv[c], pyv[c] + P.sigma * myv[c], p1x[c], p1y[c]);
         if (!xr) p1x[c] = 0.f;
         if (!yd) p1y[c] = 0.f;
-        snx[c] = mxv[c] - P.tau * (2.f * p1x[c] - pxv[c]);
-        sny[c] = myv[c] - P.tau * (2.f * p1y[c] - pyv[c]);
-        if (!xr) snx[c] = 0.f;
-        if (!yd) sny[c] = 0.f;
+        snx[c] = xr ? mxv[c] - P.tau * (2.f * p1x[c] - pxv[c]) : 0.f;
+        sny[c] = yd ? myv[c] - P.tau * (2.f * p1y[c] - pyv[c]) : 0.f;
       }
       float od[V], omx[V], omy[V], oe[V];
 #pragma unroll
@@ -346,8 +343,6 @@ __global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ q, 
         p1y_up[c] = p1y[c + 1];
         my_up[c] = myv[c + 1];
       }
-#pragma unroll
-      for (int c = 0; c < V + 2; ++c) qa[c] = qb[c];
     }
   }
   if constexpr (GAP) {
@@ -356,19 +351,17 @@ __global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ q, 
   }
 }
 
-// EMD dual bound inputs: sum phi (f1 - f0) and max |grad phi|.
-__global__ void __launch_bounds__(256) k_emd_dual(const float* __restrict__ phi, const float* __restrict__ f0,
-                                                  const float* __restrict__ f1, int N, float invh,
+// EMD dual bound inputs: sum phi (f1 - f0) and max |grad phi| (grad phi from
+// the spectral gradient of the solve: two planes).
+__global__ void __launch_bounds__(256) k_emd_dual(const float* __restrict__ phi, const float* __restrict__ gphi,
+                                                  const float* __restrict__ f0, const float* __restrict__ f1, int N,
                                                   double* __restrict__ part) {
   CSum s;
   float gmax = 0.f;
   const size_t NN = (size_t)N * N;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / N), j = (int)(idx % N);
-    const float ph = phi[idx];
-    s.add(ph * (f1[idx] - f0[idx]));
-    const float gx = j < N - 1 ? (phi[idx + 1] - ph) * invh : 0.f;
-    const float gy = i < N - 1 ? (phi[idx + N] - ph) * invh : 0.f;
+    s.add(phi[idx] * (f1[idx] - f0[idx]));
+    const float gx = gphi[idx], gy = gphi[NN + idx];
     gmax = fmaxf(gmax, sqrtf(gx * gx + gy * gy));
   }
   double v[2] = {s.value(), (double)gmax};
@@ -589,26 +582,26 @@ cudaError_t launch_rof_fused(const float* u, const float* pin, const float* I, f
   return cudaGetLastError();
 }
 
-cudaError_t launch_emd_fused(const float* q, const float* sin_, const float* pin, const float* g, float* sout,
+cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pin, const float* g, float* sout,
                              float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
                              bool gap, cudaStream_t st) {
   const int V = vec ? 4 : 1;
   dim3 gr = fused_grid(P.N, V);
   if (vec) {
-    if (gap) k_emd_fused<4, kRB, true><<<gr, 128, 0, st>>>(q, sin_, pin, g, sout, pout, d, m, e, part, P);
-    else k_emd_fused<4, kRB, false><<<gr, 128, 0, st>>>(q, sin_, pin, g, sout, pout, d, m, e, part, P);
+    if (gap) k_emd_fused<4, kRB, true><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
+    else k_emd_fused<4, kRB, false><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
   } else {
-    if (gap) k_emd_fused<1, kRB, true><<<gr, 128, 0, st>>>(q, sin_, pin, g, sout, pout, d, m, e, part, P);
-    else k_emd_fused<1, kRB, false><<<gr, 128, 0, st>>>(q, sin_, pin, g, sout, pout, d, m, e, part, P);
+    if (gap) k_emd_fused<1, kRB, true><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
+    else k_emd_fused<1, kRB, false><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
   }
   return cudaGetLastError();
 }
 
 int reduce_blocks_1d(size_t n) { return grid_1d(n, 256) < 1024 ? grid_1d(n, 256) : 1024; }
 
-cudaError_t launch_emd_dual(const float* phi, const float* f0, const float* f1, int N, double* part, int nblk,
-                            cudaStream_t st) {
-  k_emd_dual<<<nblk, 256, 0, st>>>(phi, f0, f1, N, (float)N, part);
+cudaError_t launch_emd_dual(const float* phi, const float* gphi, const float* f0, const float* f1, int N, double* part,
+                            int nblk, cudaStream_t st) {
+  k_emd_dual<<<nblk, 256, 0, st>>>(phi, gphi, f0, f1, N, part);
   return cudaGetLastError();
 }
 

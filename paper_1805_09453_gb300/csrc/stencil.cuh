@@ -24,11 +24,11 @@ int reduce_blocks_1d(size_t n);
 
 cudaError_t launch_rof_fused(const float* u, const float* pin, const float* I, float* pout, float* r, double* part,
                              const RofParams& P, bool vec, bool gap, cudaStream_t st);
-cudaError_t launch_emd_fused(const float* q, const float* sin_, const float* pin, const float* g, float* sout,
+cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pin, const float* g, float* sout,
                              float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
                              bool gap, cudaStream_t st);
-cudaError_t launch_emd_dual(const float* phi, const float* f0, const float* f1, int N, double* part, int nblk,
-                            cudaStream_t st);
+cudaError_t launch_emd_dual(const float* phi, const float* gphi, const float* f0, const float* f1, int N, double* part,
+                            int nblk, cudaStream_t st);
 cudaError_t launch_rof_stats(const float* I, int N, double* part, int nblk, cudaStream_t st);
 cudaError_t launch_sq_dev(const float* I, size_t NN, float mean, double* part, int nblk, cudaStream_t st);
 cudaError_t launch_rof_gap(const float* u, const float* p, const float* I, int N, double* part, int nblk,

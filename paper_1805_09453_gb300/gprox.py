@@ -23,7 +23,7 @@ PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
 EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_last_error", "dct2_poisson",
            "rof_solve", "emd_solve", "gp_state_create_rof", "gp_state_create_emd", "pd_step", "gp_state_read",
            "gp_state_gap", "gp_state_destroy", "gp_profile", "gp_profile_kernels", "gp_profile_query",
-           "dct2_poisson_static"]
+           "dct2_poisson_static", "dct2_poisson_grad"]
 
 
 class Opts(C.Structure):
@@ -74,6 +74,7 @@ def lib():
     L.gp_state_gap.argtypes = [vp, vp, C.POINTER(Report), vp]
     L.gp_state_destroy.argtypes = [vp]
     L.dct2_poisson_static.argtypes = [vp, vp, i, d, vp]
+    L.dct2_poisson_grad.argtypes = [vp, vp, vp, i, d, i, vp]
     L.gp_profile.argtypes = [vp, i]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
@@ -151,6 +152,13 @@ def dct2_poisson(h: Handle, b, x, alpha: float, prec="fp32", stream=None) -> int
     N = b.shape[-1]
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     return lib().dct2_poisson(h.ptr, _ptr(b), _ptr(x), int(N), float(alpha), p, _stream(stream))
+
+
+def dct2_poisson_grad(h: Handle, b, g, alpha: float, prec="fp32", stream=None) -> int:
+    """g (2, N, N) = forward-difference gradient of (alpha - Lap)^{-1} b -- see include/gprox.h."""
+    N = b.shape[-1]
+    p = PREC[prec] if isinstance(prec, str) else int(prec)
+    return lib().dct2_poisson_grad(h.ptr, _ptr(b), _ptr(g), int(N), float(alpha), p, _stream(stream))
 
 
 def dct2_poisson_static(b, x, alpha: float, stream=None) -> int:
