@@ -190,6 +190,22 @@ GP_API gp_status emd_solve(gp_handle h, const float* f0, const float* f1, float*
                     int N, const gp_opts* opts, gp_report* report, void* stream);
 
 /*
+ * emd_solve_batched: B independent EMD problems (section 3.2) of possibly
+ * different sizes N[b], solved together.  Every chunk of gap_every
+ * iterations of all unconverged problems runs as one CUDA graph with one
+ * branch per problem (so small problems execute concurrently), the gap
+ * checks included; a problem stops at its own tolerance.  Arrays are host
+ * arrays of B device pointers; reports[B] receives one report per problem.
+ *   B       1..256.  stream must be a non-default stream (graph capture).
+ *   opts    as emd_solve (warm_start unsupported).
+ * Returns GP_OK if every problem met the tolerance, else the first non-OK
+ * per-problem status (each report's `status` holds its own).
+ */
+GP_API gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const float* const* f1,
+                                   float* const* m, const int* N, const gp_opts* opts, gp_report* reports,
+                                   void* stream);
+
+/*
  * Explicit solver states for step-by-step driving (checkpoint / resume, tests,
  * external schedulers).  A state owns its device buffers and keeps pointers
  * to the caller's inputs (I, or f0 / f1), which must outlive it.

@@ -75,6 +75,12 @@ struct gp_handle_s {
   std::map<std::pair<int, int>, gp_state_s*> cache;  // solver workspaces keyed by (kind, N)
   Profiler prof;
   bool capturing = false;
+  // batched solves: per-problem states, branch streams, fork/join events, results
+  std::vector<gp_state_s*> batch;
+  std::vector<cudaStream_t> aux;
+  std::vector<cudaEvent_t> evs;
+  double* bres_d = nullptr;
+  double* bres_h = nullptr;
 };
 
 struct gp_state_s {
@@ -85,6 +91,7 @@ struct gp_state_s {
   const float* f0 = nullptr;
   const float* f1 = nullptr;
   float* prim = nullptr;  // ROF: u (N^2); EMD: grad q (2 N^2), also grad phi at gap checks
+  float* gu = nullptr;    // ROF: grad u (2 N^2)
   float* r = nullptr;     // ROF: next right-hand side; EMD: d = g - div s (= tau div pbar)
   float* p[2] = {nullptr, nullptr};
   float* s[2] = {nullptr, nullptr};  // EMD only
@@ -295,6 +302,7 @@ gp_status alloc_state(gp_handle h, int kind, int N, gp_state* out) {
   if (!e) e = A(&s->p[0], 2 * NN);
   if (!e) e = A(&s->p[1], 2 * NN);
   if (!e) e = A(&s->tmp, 2 * NN);
+  if (kind == KIND_ROF && !e) e = A(&s->gu, 2 * NN);
   if (kind == KIND_EMD) {
     if (!e) e = A(&s->s[0], 2 * NN);
     if (!e) e = A(&s->s[1], 2 * NN);
@@ -350,13 +358,15 @@ gp_status rof_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
   const int N = s->N;
   RofParams P{N, (float)N, (float)((double)N * N), (float)(s->lam * s->tau), (float)s->tau, (float)s->sigma};
   for (int k = 0; k < n_steps; ++k) {
-    gp_status r = solve(h, N, s->r, s->prim, s->tmp, s->lam * s->tau, 1.0, prec, true, st);
-    if (r != GP_OK) return r;
     const bool g = gap_last && (k == n_steps - 1);
+    // grad u_{n+1} from the spectrum; u_{n+1} itself only when the step reports the objective
+    gp_status r = solve_grad(h, N, s->r, s->gu, s->prim, g, s->tmp, s->lam * s->tau, 1.0, prec, st);
+    if (r != GP_OK) return r;
     float* pin = s->p[s->cur];
     float* pout = s->p[1 - s->cur];
-    GP_CUDA(h, plaunch(h, PK_ROF_FUSED, st,
-                       [&] { return launch_rof_fused(s->prim, pin, s->I, pout, s->r, s->part, P, s->vec, g, st); }));
+    GP_CUDA(h, plaunch(h, PK_ROF_FUSED, st, [&] {
+              return launch_rof_fused(s->gu, s->prim, pin, s->I, pout, s->r, s->part, P, s->vec, g, st);
+            }));
     s->cur = 1 - s->cur;
     s->n++;
   }
@@ -477,43 +487,58 @@ void finish_report(gp_report* rep, double P, double D) {
   rep->rel_gap = sc > 0 ? (P - D) / sc : 0.0;
 }
 
-// Gap of the current iterate.  Uses the fused partials when the last step
-// left them, else recomputes the terms with the unfused kernels.
-gp_status state_gap(gp_state s, gp_report* rep, int prec, cudaStream_t st) {
+// Gap of the current iterate, in two halves so that a CUDA graph can hold the
+// device half: state_gap_enqueue writes the four reduced scalars to `dst`
+// (device); state_gap_finish turns their host copy into P, D and the gap.
+// The fused partials are used when the last step left them, else the terms
+// are recomputed with the unfused kernels.
+gp_status state_gap_enqueue(gp_state s, double* dst, int prec, cudaStream_t st) {
   gp_handle h = s->h;
   const int N = s->N;
   const size_t NN = (size_t)N * N;
-  gp_status r = ensure_res(h);
-  if (r != GP_OK) return r;
-  const double h2 = 1.0 / ((double)N * N);
   const bool fused = s->partials_valid;
   const int nb = fused ? (int)fused_blocks(N, s->vec) : reduce_blocks_1d(NN);
   if (s->kind == KIND_ROF) {
     if (!fused)
       GP_CUDA(h, plaunch(h, PK_REDUCE, st,
                          [&] { return launch_rof_gap(s->prim, s->p[s->cur], s->I, N, s->part, nb, st); }));
-    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 4, 0u, h->dres, st); }));
-    if ((r = fetch(h, 4, st)) != GP_OK) return r;
-    finish_report(rep, h2 * (h->hres[0] + 0.5 * s->lam * h->hres[1]),
-                  -h2 * h->hres[2] - h2 * h->hres[3] / (2.0 * s->lam));
-    rep->mass_residual = 0.0;
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 4, 0u, dst, st); }));
     return GP_OK;
   }
   if (!fused)
     GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] {
               return launch_emd_primal(s->m, s->p[s->cur], s->f0, s->f1, s->e, N, s->part, nb, st);
             }));
-  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 2, 0u, h->dres, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 2, 0u, dst, st); }));
   // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p = e; grad phi into prim (free between steps)
-  if ((r = solve_grad(h, N, s->e, s->prim, s->phi, true, s->tmp, 0.0, 1.0, prec, st)) != GP_OK) return r;
+  gp_status r = solve_grad(h, N, s->e, s->prim, s->phi, true, s->tmp, 0.0, 1.0, prec, st);
+  if (r != GP_OK) return r;
   const int nd = reduce_blocks_1d(NN);
   double* pd = s->part + (size_t)nb * 4;
   GP_CUDA(h, plaunch(h, PK_REDUCE, st,
                      [&] { return launch_emd_dual(s->phi, s->prim, s->f0, s->f1, N, pd, nd, st); }));
-  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(pd, nd, 2, 2u, h->dres + 2, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(pd, nd, 2, 2u, dst + 2, st); }));
+  return GP_OK;
+}
+
+void state_gap_finish(gp_state s, const double* v, gp_report* rep) {
+  const double h2 = 1.0 / ((double)s->N * s->N);
+  if (s->kind == KIND_ROF) {
+    finish_report(rep, h2 * (v[0] + 0.5 * s->lam * v[1]), -h2 * v[2] - h2 * v[3] / (2.0 * s->lam));
+    rep->mass_residual = 0.0;
+  } else {
+    finish_report(rep, h2 * v[0], h2 * v[2] / fmax(1.0, v[3]));
+    rep->mass_residual = s->mass_den > 0 ? v[1] / s->mass_den : v[1];
+  }
+}
+
+gp_status state_gap(gp_state s, gp_report* rep, int prec, cudaStream_t st) {
+  gp_handle h = s->h;
+  gp_status r = ensure_res(h);
+  if (r != GP_OK) return r;
+  if ((r = state_gap_enqueue(s, h->dres, prec, st)) != GP_OK) return r;
   if ((r = fetch(h, 4, st)) != GP_OK) return r;
-  finish_report(rep, h2 * h->hres[0], h2 * h->hres[2] / fmax(1.0, h->hres[3]));
-  rep->mass_residual = s->mass_den > 0 ? h->hres[1] / s->mass_den : h->hres[1];
+  state_gap_finish(s, h->hres, rep);
   return GP_OK;
 }
 
@@ -685,6 +710,11 @@ gp_status gp_destroy(gp_handle h) {
   DeviceGuard g(h->device);
   cudaDeviceSynchronize();
   for (auto& kv : h->cache) free_state(kv.second);
+  for (gp_state b : h->batch) free_state(b);
+  for (cudaStream_t a : h->aux) cudaStreamDestroy(a);
+  for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
+  if (h->bres_d) cudaFree(h->bres_d);
+  if (h->bres_h) cudaFreeHost(h->bres_h);
   for (auto& kv : h->plans) dct_plan_free(kv.second);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   if (h->ws) cudaFree(h->ws);
@@ -938,6 +968,194 @@ gp_status emd_solve(gp_handle h, const float* f0, const float* f1, float* m, flo
   rep.seconds = t.s();
   if (report) *report = rep;
   return status;
+}
+
+// ------------------------------------------------------- batched EMD
+// Independent EMD problems of mixed sizes.  Each between-check chunk of all
+// active problems is one CUDA graph with one branch per problem (its k steps
+// and its gap reductions), so small problems run concurrently and the launch
+// cost is paid once per chunk; all gap scalars come back in one copy per
+// chunk.  The graph is re-instantiated when the set of active problems
+// shrinks.
+gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const float* const* f1, float* const* m,
+                            const int* N, const gp_opts* opts, gp_report* reports, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  Timer t;
+  gp_opts o;
+  gp_default_opts(&o);
+  if (opts) o = *opts;
+  gp_status r = check_opts(h, &o);
+  if (r != GP_OK) return r;
+  if (B < 1 || !f0 || !f1 || !m || !N || !reports) return fail(h, GP_ERR_ARG, "bad batch arguments");
+  if (o.warm_start) return fail(h, GP_ERR_ARG, "warm_start is not available for batched solves");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (st == nullptr) return fail(h, GP_ERR_ARG, "batched solves need a non-default stream (graph capture)");
+  for (int b = 0; b < B; ++b) {
+    if (N[b] < 1 || N[b] > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
+    if ((r = check_ptr(h, f0[b], "f0[b]")) != GP_OK || (r = check_ptr(h, f1[b], "f1[b]")) != GP_OK ||
+        (r = check_ptr(h, m[b], "m[b]")) != GP_OK)
+      return r;
+  }
+  const double tau = o.tau > 0 ? o.tau : (o.tau_scale > 0 ? o.tau_scale : 1.0);
+  const double sigma = o.sigma > 0 ? o.sigma : 1.0 / tau;
+  // states (reused across calls with the same sizes) and branch streams
+  while ((int)h->batch.size() < B) h->batch.push_back(nullptr);
+  while ((int)h->aux.size() < B) {
+    cudaStream_t a;
+    GP_CUDA(h, cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    h->aux.push_back(a);
+  }
+  if (!h->evs.size()) {
+    for (int i = 0; i < 2 * 256; ++i) {
+      cudaEvent_t e;
+      GP_CUDA(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      h->evs.push_back(e);
+    }
+  }
+  if (B > 256) return fail(h, GP_ERR_ARG, "at most 256 problems per batch");
+  for (int b = 0; b < B; ++b) {
+    gp_state& s = h->batch[b];
+    if (s && s->N != N[b]) {
+      free_state(s);
+      s = nullptr;
+    }
+    if (!s && (r = alloc_state(h, KIND_EMD, N[b], &s)) != GP_OK) return r;
+    double ms[3];
+    if ((r = mass_stats(h, f0[b], f1[b], N[b], ms, st)) != GP_OK || (r = check_mass(h, ms)) != GP_OK) return r;
+    if ((r = emd_setup(s, f0[b], f1[b], tau, sigma, nullptr, nullptr, nullptr, st)) != GP_OK) return r;
+    s->mass_den = ms[2];
+    memset(&reports[b], 0, sizeof(gp_report));
+    reports[b].status = o.tol_rel_gap > 0 ? GP_ERR_MAXITER : GP_OK;
+  }
+  if (!h->bres_h) {
+    GP_CUDA(h, cudaMallocHost(&h->bres_h, 256 * 4 * sizeof(double)));
+    GP_CUDA(h, cudaMalloc(&h->bres_d, 256 * 4 * sizeof(double)));
+  }
+  // Warm every size once outside capture (plans, kernel attributes).
+  for (int b = 0; b < B; ++b) {
+    const DctPlan* p = nullptr;
+    if ((r = get_plan(h, N[b], &p)) != GP_OK) return r;
+  }
+  std::vector<int> active;
+  for (int b = 0; b < B; ++b) active.push_back(b);
+  std::vector<DivergenceWatch> watch(B);
+  cudaGraphExec_t exec = nullptr;
+  int exec_k = -1;
+  bool first = true;
+  while (!active.empty()) {
+    const int done_iters = h->batch[active[0]]->n;
+    if (done_iters >= o.max_iters) break;
+    const int k = std::min(o.gap_every, o.max_iters - done_iters);
+    if (!exec || exec_k != k || first) {
+      if (exec) cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      if (first) {
+        // one direct chunk: sets kernel attributes before any capture
+        for (int b : active) {
+          gp_state s = h->batch[b];
+          if ((r = run_steps(s, k, o.prec, true, false, st)) != GP_OK) return r;
+          if ((r = state_gap_enqueue(s, h->bres_d + 4 * b, o.prec, st)) != GP_OK) return r;
+        }
+        GP_CUDA(h, cudaMemcpyAsync(h->bres_h, h->bres_d, 4 * B * sizeof(double), cudaMemcpyDeviceToHost, st));
+        GP_CUDA(h, cudaStreamSynchronize(st));
+        first = false;
+      } else {
+        const int n0 = h->batch[active[0]]->n;
+        std::vector<int> cur0;
+        for (int b : active) cur0.push_back(h->batch[b]->cur);
+        cudaGraph_t gr = nullptr;
+        GP_CUDA(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        h->capturing = true;
+        gp_status cr = GP_OK;
+        cudaEventRecord(h->evs[0], st);
+        for (size_t i = 0; i < active.size() && cr == GP_OK; ++i) {
+          const int b = active[i];
+          cudaStream_t a = h->aux[b];
+          cudaStreamWaitEvent(a, h->evs[0], 0);
+          cr = run_steps(h->batch[b], k, o.prec, true, false, a);
+          if (cr == GP_OK) cr = state_gap_enqueue(h->batch[b], h->bres_d + 4 * b, o.prec, a);
+          cudaEventRecord(h->evs[1 + i], a);
+          cudaStreamWaitEvent(st, h->evs[1 + i], 0);
+        }
+        if (cr == GP_OK)
+          cudaMemcpyAsync(h->bres_h, h->bres_d, 4 * B * sizeof(double), cudaMemcpyDeviceToHost, st);
+        h->capturing = false;
+        cudaError_t e = cudaStreamEndCapture(st, &gr);
+        for (size_t i = 0; i < active.size(); ++i) {
+          h->batch[active[i]]->cur = cur0[i];
+          h->batch[active[i]]->n = n0;
+        }
+        if (cr != GP_OK) {
+          if (gr) cudaGraphDestroy(gr);
+          return cr;
+        }
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&exec, gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+        exec_k = k;
+        GP_CUDA(h, cudaGraphLaunch(exec, st));
+        GP_CUDA(h, cudaStreamSynchronize(st));
+        for (int b : active) {
+          gp_state s = h->batch[b];
+          if (k & 1) s->cur = 1 - s->cur;
+          s->n += k;
+          s->partials_valid = true;
+        }
+      }
+    } else {
+      GP_CUDA(h, cudaGraphLaunch(exec, st));
+      GP_CUDA(h, cudaStreamSynchronize(st));
+      for (int b : active) {
+        gp_state s = h->batch[b];
+        if (k & 1) s->cur = 1 - s->cur;
+        s->n += k;
+        s->partials_valid = true;
+      }
+    }
+    std::vector<int> still;
+    for (int b : active) {
+      gp_state s = h->batch[b];
+      gp_report& rep = reports[b];
+      state_gap_finish(s, h->bres_h + 4 * b, &rep);
+      rep.iters = s->n;
+      rep.tau = s->tau;
+      rep.sigma = s->sigma;
+      rep.seconds = t.s();
+      bool stop = false;
+      if (!isfinite(rep.primal) || !isfinite(rep.dual)) {
+        rep.status = GP_ERR_NONFINITE;
+        stop = true;
+      } else if (o.tol_rel_gap > 0 && rep.rel_gap <= o.tol_rel_gap) {
+        rep.status = GP_OK;
+        stop = true;
+      } else if (watch[b].update(rep.rel_gap)) {
+        rep.status = GP_ERR_DIVERGED;
+        stop = true;
+      }
+      if (!stop) still.push_back(b);
+    }
+    if (still.size() != active.size() && exec) {
+      cudaGraphExecDestroy(exec);
+      exec = nullptr;
+      first = false;
+    }
+    active.swap(still);
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  gp_status worst = GP_OK;
+  for (int b = 0; b < B; ++b) {
+    gp_state s = h->batch[b];
+    const size_t NN = (size_t)N[b] * N[b];
+    GP_CUDA(h, cudaMemcpyAsync(m[b], s->m, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (reports[b].status != GP_OK && worst == GP_OK) worst = (gp_status)reports[b].status;
+  }
+  GP_CUDA(h, cudaStreamSynchronize(st));
+  for (int b = 0; b < B; ++b) reports[b].seconds = t.s();
+  return worst;
 }
 
 // ------------------------------------------------------------ profiling

@@ -120,107 +120,99 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[NQ], unsigned max
 }
 
 // ------------------------------------------------------------------ ROF
+// Given grad u_{n+1} (spectral gradient of the solve: two planes, zero slots)
+// and p_n:  p_{n+1} = proj(p_n + sigma grad u_{n+1}), pbar = 2 p_{n+1} - p_n,
+//           r_{n+1} = lambda tau I + tau div pbar - div grad u_{n+1}.
+// GAP steps also read u_{n+1} for the fidelity term of the objective.
 template <int V, int RB, bool GAP>
-__global__ void __launch_bounds__(128) k_rof_fused(const float* __restrict__ u, const float* __restrict__ pin,
-                                                   const float* __restrict__ I, float* __restrict__ pout,
-                                                   float* __restrict__ r, double* __restrict__ part,
-                                                   RofParams P) {
+__global__ void __launch_bounds__(128) k_rof_fused(const float* __restrict__ gu, const float* __restrict__ u,
+                                                   const float* __restrict__ pin, const float* __restrict__ I,
+                                                   float* __restrict__ pout, float* __restrict__ r,
+                                                   double* __restrict__ part, RofParams P) {
   const int N = P.N;
   const size_t NN = (size_t)N * N;
   const int j0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
   const int i0 = blockIdx.y * RB;
   CSum s_tv, s_fid, s_id, s_dd;
   if (j0 < N) {
+    const float* __restrict__ gux = gu;
+    const float* __restrict__ guy = gu + NN;
     const float* __restrict__ pxin = pin;
     const float* __restrict__ pyin = pin + NN;
-    float ua[V + 2], ub[V + 2], uc[V + 2];
-    float pby_up[V], p1y_up[V];
-    load_row<V>(ub, u, i0, N, j0);
-    load_row<V>(uc, u, i0 + 1, N, j0);
+    float pby_up[V], p1y_up[V], gy_up[V];  // row above: pbar_y, p_{n+1,y}, (grad u)_y
     if (i0 > 0) {
-      // recompute p_{n+1} on the row above the strip (only its y part is used)
-      load_row<V>(ua, u, i0 - 1, N, j0);
-      float pnx[V], pny[V];
-      ldv<V>(pnx, pxin + (size_t)(i0 - 1) * N + j0);
-      ldv<V>(pny, pyin + (size_t)(i0 - 1) * N + j0);
+      const size_t ro = (size_t)(i0 - 1) * N;
+      float gxv[V], gyv[V], pnx[V], pny[V];
+      ldv<V>(gxv, gux + ro + j0);
+      ldv<V>(gyv, guy + ro + j0);
+      ldv<V>(pnx, pxin + ro + j0);
+      ldv<V>(pny, pyin + ro + j0);
 #pragma unroll
       for (int c = 0; c < V; ++c) {
-        const int j = j0 + c;
-        const float gx = (j < N - 1) ? (ua[c + 2] - ua[c + 1]) * P.invh : 0.f;
-        const float gy = (ub[c + 1] - ua[c + 1]) * P.invh;
         float px1, py1;
-        proj2(pnx[c] + P.sigma * gx, pny[c] + P.sigma * gy, px1, py1);
+        proj2(pnx[c] + P.sigma * gxv[c], pny[c] + P.sigma * gyv[c], px1, py1);
         pby_up[c] = 2.f * py1 - pny[c];
         p1y_up[c] = py1;
+        gy_up[c] = gyv[c];
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < V + 2; ++c) ua[c] = 0.f;
-#pragma unroll
-      for (int c = 0; c < V; ++c) { pby_up[c] = 0.f; p1y_up[c] = 0.f; }
+      for (int c = 0; c < V; ++c) { pby_up[c] = 0.f; p1y_up[c] = 0.f; gy_up[c] = 0.f; }
     }
     const int iend = min(i0 + RB, N);
     for (int i = i0; i < iend; ++i) {
       const size_t ro = (size_t)i * N;
-      float pnx[V + 1], pny[V + 1];
+      float gxv[V + 1], gyv[V + 1], pnx[V + 1], pny[V + 1];
+      ldv<V>(&gxv[1], gux + ro + j0);
+      ldv<V>(&gyv[1], guy + ro + j0);
       ldv<V>(&pnx[1], pxin + ro + j0);
       ldv<V>(&pny[1], pyin + ro + j0);
-      pnx[0] = j0 > 0 ? pxin[ro + j0 - 1] : 0.f;
-      pny[0] = j0 > 0 ? pyin[ro + j0 - 1] : 0.f;
-      float Iv[V];
+      if (j0 > 0) {
+        gxv[0] = gux[ro + j0 - 1]; gyv[0] = guy[ro + j0 - 1];
+        pnx[0] = pxin[ro + j0 - 1]; pny[0] = pyin[ro + j0 - 1];
+      } else {
+        gxv[0] = gyv[0] = pnx[0] = pny[0] = 0.f;
+      }
+      float Iv[V], uv[V];
       ldv<V>(Iv, I + ro + j0);
-      float p1x[V + 1], p1y[V + 1], pbx[V + 1], pby[V + 1], gxs[V + 1], gys[V + 1];
+      if constexpr (GAP) ldv<V>(uv, u + ro + j0);
+      float p1x[V + 1], p1y[V + 1], pbx[V + 1], pby[V + 1];
 #pragma unroll
       for (int c = 0; c <= V; ++c) {
         const int j = j0 - 1 + c;
-        const float gx = (j < N - 1) ? (ub[c + 1] - ub[c]) * P.invh : 0.f;
-        const float gy = (i < N - 1) ? (uc[c] - ub[c]) * P.invh : 0.f;
-        proj2(pnx[c] + P.sigma * gx, pny[c] + P.sigma * gy, p1x[c], p1y[c]);
-        pbx[c] = 2.f * p1x[c] - pnx[c];
-        pby[c] = 2.f * p1y[c] - pny[c];
-        gxs[c] = gx;
-        gys[c] = gy;
+        const bool xr = j < N - 1, yd = i < N - 1;
+        proj2(pnx[c] + P.sigma * gxv[c], pny[c] + P.sigma * gyv[c], p1x[c], p1y[c]);
+        if (!xr) p1x[c] = 0.f;
+        if (!yd) p1y[c] = 0.f;
+        pbx[c] = 2.f * p1x[c] - (xr ? pnx[c] : 0.f);
+        pby[c] = 2.f * p1y[c] - (yd ? pny[c] : 0.f);
       }
-      float rv[V], ox[V], oy[V];
+      float rv[V];
 #pragma unroll
       for (int c = 1; c <= V; ++c) {
         const int j = j0 + c - 1;
-        const bool xr = j < N - 1, xl = j > 0, yd = i < N - 1, yu = i > 0;
-        ox[c - 1] = xr ? p1x[c] : 0.f;
-        oy[c - 1] = yd ? p1y[c] : 0.f;
-        const float dx = (xr ? pbx[c] : 0.f) - (xl ? pbx[c - 1] : 0.f);
-        const float dy = (yd ? pby[c] : 0.f) - (yu ? pby_up[c - 1] : 0.f);
-        const float uo = ub[c];
-        float lap = 0.f;
-        if (xr) lap += ub[c + 1] - uo;
-        if (xl) lap += ub[c - 1] - uo;
-        if (yd) lap += uc[c] - uo;
-        if (yu) lap += ua[c] - uo;
-        rv[c - 1] = P.lt * Iv[c - 1] + P.tau * (dx + dy) * P.invh - lap * P.invh2;
+        const bool xl = j > 0, yu = i > 0;
+        const float dpb = (pbx[c] - (xl ? pbx[c - 1] : 0.f) + pby[c] - (yu ? pby_up[c - 1] : 0.f)) * P.invh;
+        const float lap = (gxv[c] - (xl ? gxv[c - 1] : 0.f) + gyv[c] - (yu ? gy_up[c - 1] : 0.f)) * P.invh;
+        rv[c - 1] = P.lt * Iv[c - 1] + P.tau * dpb - lap;
         if constexpr (GAP) {
-          s_tv.add(sqrtf(gxs[c] * gxs[c] + gys[c] * gys[c]));
-          const float e = uo - Iv[c - 1];
+          s_tv.add(sqrtf(gxv[c] * gxv[c] + gyv[c] * gyv[c]));
+          const float e = uv[c - 1] - Iv[c - 1];
           s_fid.add(e * e);
-          const float d1 = ((xr ? p1x[c] : 0.f) - (xl ? p1x[c - 1] : 0.f) + (yd ? p1y[c] : 0.f) -
-                            (yu ? p1y_up[c - 1] : 0.f)) * P.invh;
+          const float d1 = (p1x[c] - (xl ? p1x[c - 1] : 0.f) + p1y[c] - (yu ? p1y_up[c - 1] : 0.f)) * P.invh;
           s_id.add(Iv[c - 1] * d1);
           s_dd.add(d1 * d1);
         }
       }
-      stv<V>(pout + ro + j0, ox);
-      stv<V>(pout + NN + ro + j0, oy);
+      stv<V>(pout + ro + j0, &p1x[1]);
+      stv<V>(pout + NN + ro + j0, &p1y[1]);
       stv<V>(r + ro + j0, rv);
 #pragma unroll
       for (int c = 0; c < V; ++c) {
         pby_up[c] = pby[c + 1];
         p1y_up[c] = p1y[c + 1];
+        gy_up[c] = gyv[c + 1];
       }
-#pragma unroll
-      for (int c = 0; c < V + 2; ++c) {
-        ua[c] = ub[c];
-        ub[c] = uc[c];
-      }
-      load_row<V>(uc, u, i + 2, N, j0);
     }
   }
   if constexpr (GAP) {
@@ -568,16 +560,16 @@ inline int grid_1d(size_t n, int threads) {
 
 dim3 fused_grid(int N, int V) { return dim3(ceil_div(ceil_div(N, V), 128), ceil_div(N, kRB)); }
 
-cudaError_t launch_rof_fused(const float* u, const float* pin, const float* I, float* pout, float* r, double* part,
-                             const RofParams& P, bool vec, bool gap, cudaStream_t st) {
+cudaError_t launch_rof_fused(const float* gu, const float* u, const float* pin, const float* I, float* pout, float* r,
+                             double* part, const RofParams& P, bool vec, bool gap, cudaStream_t st) {
   const int V = vec ? 4 : 1;
   dim3 g = fused_grid(P.N, V);
   if (vec) {
-    if (gap) k_rof_fused<4, kRB, true><<<g, 128, 0, st>>>(u, pin, I, pout, r, part, P);
-    else k_rof_fused<4, kRB, false><<<g, 128, 0, st>>>(u, pin, I, pout, r, part, P);
+    if (gap) k_rof_fused<4, kRB, true><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
+    else k_rof_fused<4, kRB, false><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
   } else {
-    if (gap) k_rof_fused<1, kRB, true><<<g, 128, 0, st>>>(u, pin, I, pout, r, part, P);
-    else k_rof_fused<1, kRB, false><<<g, 128, 0, st>>>(u, pin, I, pout, r, part, P);
+    if (gap) k_rof_fused<1, kRB, true><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
+    else k_rof_fused<1, kRB, false><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
   }
   return cudaGetLastError();
 }

@@ -22,8 +22,8 @@ struct EmdParams {
 dim3 fused_grid(int N, int V);
 int reduce_blocks_1d(size_t n);
 
-cudaError_t launch_rof_fused(const float* u, const float* pin, const float* I, float* pout, float* r, double* part,
-                             const RofParams& P, bool vec, bool gap, cudaStream_t st);
+cudaError_t launch_rof_fused(const float* gu, const float* u, const float* pin, const float* I, float* pout, float* r,
+                             double* part, const RofParams& P, bool vec, bool gap, cudaStream_t st);
 cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pin, const float* g, float* sout,
                              float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
                              bool gap, cudaStream_t st);

@@ -23,7 +23,7 @@ PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
 EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_last_error", "dct2_poisson",
            "rof_solve", "emd_solve", "gp_state_create_rof", "gp_state_create_emd", "pd_step", "gp_state_read",
            "gp_state_gap", "gp_state_destroy", "gp_profile", "gp_profile_kernels", "gp_profile_query",
-           "dct2_poisson_static", "dct2_poisson_grad"]
+           "dct2_poisson_static", "dct2_poisson_grad", "emd_solve_batched"]
 
 
 class Opts(C.Structure):
@@ -75,6 +75,8 @@ def lib():
     L.gp_state_destroy.argtypes = [vp]
     L.dct2_poisson_static.argtypes = [vp, vp, i, d, vp]
     L.dct2_poisson_grad.argtypes = [vp, vp, vp, i, d, i, vp]
+    L.emd_solve_batched.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i),
+                                    C.POINTER(Opts), C.POINTER(Report), vp]
     L.gp_profile.argtypes = [vp, i]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
@@ -185,6 +187,20 @@ def emd_solve(h: Handle, f0, f1, m, p=None, phi=None, opts: Opts | None = None, 
     st = lib().emd_solve(h.ptr, _ptr(f0), _ptr(f1), _ptr(m), _ptr(p), _ptr(phi), int(f0.shape[-1]),
                          C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
     return st, rep.as_dict()
+
+
+def emd_solve_batched(h: Handle, f0s, f1s, ms, opts: Opts | None = None, stream=None):
+    """Batched EMD solve of independent problems; returns (status, [report dicts]).
+
+    `stream` (or the current torch stream) must not be the default stream."""
+    B = len(f0s)
+    P = C.c_void_p * B
+    reps = (Report * B)()
+    Ns = (C.c_int * B)(*[int(f.shape[-1]) for f in f0s])
+    st = lib().emd_solve_batched(h.ptr, B, P(*[_ptr(x) for x in f0s]), P(*[_ptr(x) for x in f1s]),
+                                 P(*[_ptr(x) for x in ms]), Ns, C.byref(opts) if opts is not None else None,
+                                 reps, _stream(stream))
+    return st, [r.as_dict() for r in reps]
 
 
 class State:

