@@ -28,6 +28,7 @@ enum {
   PK_DCT_COLS_GRAD,
   PK_DCT_ROWS_GRAD,
   PK_DCT_DENSE,
+  PK_DCT_TC,
   PK_ROF_FUSED,
   PK_EMD_FUSED,
   PK_REDUCE,
@@ -35,10 +36,10 @@ enum {
   PK_COUNT
 };
 static const char* kProfNames[PK_COUNT] = {"dct_rows_fwd", "dct_cols_solve", "dct_rows_inv", "dct_cols_grad",
-                                           "dct_rows_grad", "dct_dense",     "rof_fused",    "emd_fused",
-                                           "reduce",        "setup"};
+                                           "dct_rows_grad", "dct_dense",     "dct_tc_split", "rof_fused",
+                                           "emd_fused",     "reduce",        "setup"};
 // Kernel launches behind one recorded launch of a class.
-static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 1, 1, 1, 1};
+static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 4, 1, 1, 1, 1};
 
 struct Profiler {
   bool on = false;
@@ -75,6 +76,7 @@ struct gp_handle_s {
   std::map<std::pair<int, int>, gp_state_s*> cache;  // solver workspaces keyed by (kind, N)
   Profiler prof;
   bool capturing = false;
+  int* tc_err = nullptr;  // timeout flag of the tensor-core kernels
   // batched solves: per-problem states, branch streams, fork/join events, results
   std::vector<gp_state_s*> batch;
   std::vector<cudaStream_t> aux;
@@ -217,8 +219,19 @@ gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double
   const DctPlan* p = nullptr;
   gp_status s = get_plan(h, N, &p);
   if (s != GP_OK) return s;
-  if (prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
   const float a = (float)alpha, sc = (float)scale;
+  if (prec == GP_PREC_SPLIT_BF16) {
+    if (!tc_solve_supported(N)) return fail(h, GP_ERR_UNSUPPORTED, "split-precision solve needs N a multiple of 128");
+    DctPlan* pm = &h->plans[N];
+    GP_CUDA(h, dct_plan_dense(*pm));
+    if (!h->tc_err) {
+      GP_CUDA(h, cudaMalloc(&h->tc_err, sizeof(int)));
+      GP_CUDA(h, cudaMemset(h->tc_err, 0, sizeof(int)));
+    }
+    GP_CUDA(h, plaunch(h, PK_DCT_TC, st, [&] { return dct_solve_tc(*pm, b, x, tmp, a, sc, h->tc_err, st); }));
+    return GP_OK;
+  }
+  if (prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
   if (p->fft && allow_fast) {
     GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return dct_fft_pass(*p, 0, b, tmp, a, sc, st); }));
     GP_CUDA(h, plaunch(h, PK_DCT_COLS, st, [&] { return dct_fft_pass(*p, 1, tmp, tmp, a, sc, st); }));
@@ -239,10 +252,11 @@ gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, 
   const DctPlan* p = nullptr;
   gp_status s = get_plan(h, N, &p);
   if (s != GP_OK) return s;
-  if (prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
+  if (prec != GP_PREC_FP32 && prec != GP_PREC_SPLIT_BF16)
+    return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
   const float a = (float)alpha, sc = (float)scale;
   const size_t NN = (size_t)N * N;
-  if (p->fft) {
+  if (p->fft && prec == GP_PREC_FP32) {
     float* A = tmp;
     float* B = tmp + NN;
     GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return dct_fft_pass(*p, 0, b, A, a, sc, st); }));
@@ -252,7 +266,7 @@ gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, 
     return GP_OK;
   }
   if ((s = solve(h, N, b, phi, tmp, alpha, scale, prec, false, st)) != GP_OK) return s;
-  GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_grad(phi, g2, N, st); }));
+  GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_grad(phi, g2, N, st); }));  // differences of the solution
   return GP_OK;
 }
 
@@ -718,6 +732,7 @@ gp_status gp_destroy(gp_handle h) {
   for (auto& kv : h->plans) dct_plan_free(kv.second);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   if (h->ws) cudaFree(h->ws);
+  if (h->tc_err) cudaFree(h->tc_err);
   if (h->part) cudaFree(h->part);
   if (h->dres) cudaFree(h->dres);
   if (h->hres) cudaFreeHost(h->hres);
@@ -741,7 +756,8 @@ gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alph
   const DctPlan* p = nullptr;
   if ((r = get_plan(h, N, &p)) != GP_OK) return r;
   const bool aligned = aligned16(b) && aligned16(x);
-  if (p->fft && !aligned) return fail(h, GP_ERR_ARG, "b and x must be 16-byte aligned for power-of-two N");
+  if ((p->fft || prec == GP_PREC_SPLIT_BF16) && !aligned)
+    return fail(h, GP_ERR_ARG, "b and x must be 16-byte aligned for this size / precision");
   const size_t need = 2 * (size_t)N * N;
   if (h->ws_floats < need) {
     if (h->ws) cudaFree(h->ws);
@@ -750,7 +766,15 @@ gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alph
     GP_CUDA(h, cudaMalloc(&h->ws, need * sizeof(float)));
     h->ws_floats = need;
   }
-  return solve(h, N, b, x, h->ws, alpha, 1.0, prec, true, (cudaStream_t)stream);
+  r = solve(h, N, b, x, h->ws, alpha, 1.0, prec, true, (cudaStream_t)stream);
+  if (r == GP_OK && prec == GP_PREC_SPLIT_BF16) {
+    // the tensor-core kernels report a timed-out wait through a flag: check it
+    int flag = 0;
+    GP_CUDA(h, cudaMemcpyAsync(&flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    GP_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+    if (flag) return fail(h, GP_ERR_CUDA, "tensor-core solve: a wait timed out");
+  }
+  return r;
 }
 
 gp_status dct2_poisson_grad(gp_handle h, const float* b, float* g, int N, double alpha, int prec, void* stream) {

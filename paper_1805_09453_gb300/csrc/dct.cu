@@ -127,19 +127,30 @@ __device__ __forceinline__ void stage_twiddles(const float2* __restrict__ tw, in
 }
 
 // One self-sorting Stockham stage of radix R over a length-N complex array
-// in (padded) shared memory, TPF threads per transform.
+// in (padded) shared memory, TPF threads per transform.  Padded addresses
+// are formed once per butterfly and advanced by compile-time strides: with
+// NB and Ns multiples of 16, padi(a + r*S) = padi(a) + r*(S + S/16); for the
+// first stage (Ns = 1) the store index is 16j + r, whose padded form is
+// padi(16j) + r.
 template <int N, int R, int DIR, int TPF>
 __device__ __forceinline__ void fft_stage(float2* buf, const int Ns, const int t,
                                           const float2* __restrict__ tw) {
   constexpr int NB = N / R;
   constexpr int BPT = NB / TPF;
   static_assert(BPT >= 1 && NB % TPF == 0, "threads per transform must divide N/R");
+  constexpr int LD = (NB % 16 == 0) ? NB + NB / 16 : 0;  // padded load stride (0: generic path)
   float2 v[BPT][R];
 #pragma unroll
   for (int b = 0; b < BPT; ++b) {
     const int j = t + b * TPF;
+    if constexpr (LD != 0) {
+      const float2* src = buf + padi(j);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b][r] = buf[padi(j + r * NB)];
+      for (int r = 0; r < R; ++r) v[b][r] = src[r * LD];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = buf[padi(j + r * NB)];
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -154,8 +165,19 @@ __device__ __forceinline__ void fft_stage(float2* buf, const int Ns, const int t
     }
     dft_reg<R, DIR>(v[b]);
     const int base = (j - k) * R + k;
+    if (Ns == 1 && R == 16) {
+      float2* dst = buf + padi(base);
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[padi(base + r * Ns)] = v[b][r];
+      for (int r = 0; r < R; ++r) dst[r] = v[b][r];
+    } else if (Ns % 16 == 0) {
+      float2* dst = buf + padi(base);
+      const int SS = Ns + Ns / 16;
+#pragma unroll
+      for (int r = 0; r < R; ++r) dst[r * SS] = v[b][r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[padi(base + r * Ns)] = v[b][r];
+    }
   }
   __syncthreads();
 }
@@ -232,7 +254,7 @@ __device__ __forceinline__ void deriv_pre(float xk, float xn, float2 w, float2& 
 // 0 for the constant mode when alpha == 0.
 __device__ __forceinline__ float spec_gain(int k, const float* __restrict__ mu, float mul, float alpha, float sN2) {
   const float den = alpha + __ldg(&mu[k]) + mul;
-  return den > 0.f ? sN2 / den : 0.f;
+  return den > 0.f ? __fdividef(sN2, den) : 0.f;  // den >= pi^2 (or alpha) is far from the fast-divide limits
 }
 
 template <int LOG2N>
@@ -291,31 +313,33 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
 }
 
 // Load the two columns (2cp, 2cp+1) of the interleaved layout into one
-// Makhoul-ordered complex buffer (column 2cp real, 2cp+1 imaginary).
+// Makhoul-ordered complex buffer (column 2cp real, 2cp+1 imaginary): one
+// thread per 4-row block reads both columns (32 contiguous bytes) and writes
+// four complex values.
 template <int N, int TPF>
 __device__ __forceinline__ void load_cols(float2* buf, const float* __restrict__ src, int cp, int t) {
-  float* fb = reinterpret_cast<float*>(buf);
-  for (int idx = t; idx < N / 2; idx += TPF) {
-    const int rb = idx >> 1, c = idx & 1;
-    const float4 v = *reinterpret_cast<const float4*>(src + (size_t)rb * 4 * N + (size_t)(2 * cp + c) * 4);
+  for (int rb = t; rb < N / 4; rb += TPF) {
+    const float* p = src + (size_t)rb * 4 * N + (size_t)(2 * cp) * 4;
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    const float4 b = *reinterpret_cast<const float4*>(p + 4);
     const int n = 4 * rb;
-    fb[2 * padi(mk_pos(n, N)) + c] = v.x;
-    fb[2 * padi(mk_pos(n + 1, N)) + c] = v.y;
-    fb[2 * padi(mk_pos(n + 2, N)) + c] = v.z;
-    fb[2 * padi(mk_pos(n + 3, N)) + c] = v.w;
+    buf[padi(mk_pos(n, N))] = make_float2(a.x, b.x);
+    buf[padi(mk_pos(n + 1, N))] = make_float2(a.y, b.y);
+    buf[padi(mk_pos(n + 2, N))] = make_float2(a.z, b.z);
+    buf[padi(mk_pos(n + 3, N))] = make_float2(a.w, b.w);
   }
 }
 
 // Store the synthesised columns (real part -> column 2cp, imaginary -> 2cp+1).
 template <int N, int TPF>
 __device__ __forceinline__ void store_cols(const float2* buf, float* __restrict__ dst, int cp, int t) {
-  const float* fb = reinterpret_cast<const float*>(buf);
-  for (int idx = t; idx < N / 2; idx += TPF) {
-    const int rb = idx >> 1, c = idx & 1;
+  for (int rb = t; rb < N / 4; rb += TPF) {
     const int n = 4 * rb;
-    const float4 v = make_float4(fb[2 * padi(mk_pos(n, N)) + c], fb[2 * padi(mk_pos(n + 1, N)) + c],
-                                 fb[2 * padi(mk_pos(n + 2, N)) + c], fb[2 * padi(mk_pos(n + 3, N)) + c]);
-    *reinterpret_cast<float4*>(dst + (size_t)rb * 4 * N + (size_t)(2 * cp + c) * 4) = v;
+    const float2 z0 = buf[padi(mk_pos(n, N))], z1 = buf[padi(mk_pos(n + 1, N))];
+    const float2 z2 = buf[padi(mk_pos(n + 2, N))], z3 = buf[padi(mk_pos(n + 3, N))];
+    float* p = dst + (size_t)rb * 4 * N + (size_t)(2 * cp) * 4;
+    *reinterpret_cast<float4*>(p) = make_float4(z0.x, z1.x, z2.x, z3.x);
+    *reinterpret_cast<float4*>(p + 4) = make_float4(z0.y, z1.y, z2.y, z3.y);
   }
 }
 
@@ -436,17 +460,14 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
 //   B[:, a]    = D_y S_c(X_a),  B[:, b] = D_y S_c(X_b)
 // `in` may alias A.  Shared memory: transform buffer, gained spectra, D_y of a.
 template <int LOG2N>
-__global__ void __launch_bounds__(FftCfg<LOG2N>::TPF) k_dct_cols_grad(const float* __restrict__ in, float* A, float* B,
-                                                                     const float2* __restrict__ tw,
-                                                                     const float2* __restrict__ wq,
-                                                                     const float* __restrict__ mu, float alpha,
-                                                                     float sN2) {
+__global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
+    k_dct_cols_grad(const float* __restrict__ in, float* A, float* B, const float2* __restrict__ tw,
+                    const float2* __restrict__ wq, const float* __restrict__ mu, float alpha, float sN2) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
   extern __shared__ float2 smem[];
   float2* buf = smem;
-  float2* X = smem + PADN;                               // N complex
-  float* Da = reinterpret_cast<float*>(smem + PADN + N);  // N floats
+  float2* X = smem + PADN;  // gained spectra of the two columns, N complex
   const int cp = blockIdx.x, t = threadIdx.x;
   const float fN = (float)N;
   load_cols<N, TPF>(buf, in, cp, t);
@@ -488,27 +509,18 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF) k_dct_cols_grad(const floa
     fft_smem<LOG2N, +1, TPF>(buf, t, tw);
     if (pass == 0) {
       store_cols<N, TPF>(buf, A, cp, t);
-    } else if (pass == 1) {
-      for (int n = t; n < N; n += TPF) {
-        const float2 z = buf[padi(mk_pos(n, N))];
-        Da[n] = (n == N - 1) ? 0.f : fN * (z.x - ((n & 1) ? -z.y : z.y));
-      }
     } else {
-      for (int idx = t; idx < N / 2; idx += TPF) {
-        const int rb = idx >> 1, c = idx & 1;
+      // D_y of column (2cp + pass - 1): one float4 (4 rows) per row block
+      const int col = 2 * cp + pass - 1;
+      for (int rb = t; rb < N / 4; rb += TPF) {
         float v[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int n = 4 * rb + r;
-          if (c == 0) {
-            v[r] = Da[n];
-          } else {
-            const float2 z = buf[padi(mk_pos(n, N))];
-            v[r] = (n == N - 1) ? 0.f : fN * (z.x - ((n & 1) ? -z.y : z.y));
-          }
+          const float2 z = buf[padi(mk_pos(n, N))];
+          v[r] = (n == N - 1) ? 0.f : fN * (z.x - ((n & 1) ? -z.y : z.y));
         }
-        *reinterpret_cast<float4*>(B + (size_t)rb * 4 * N + (size_t)(2 * cp + c) * 4) =
-            make_float4(v[0], v[1], v[2], v[3]);
+        *reinterpret_cast<float4*>(B + (size_t)rb * 4 * N + (size_t)col * 4) = make_float4(v[0], v[1], v[2], v[3]);
       }
     }
     __syncthreads();
@@ -625,7 +637,7 @@ cudaError_t launch_grad_cols(const DctPlan& p, const float* in, float* A, float*
                              cudaStream_t st) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
-  const size_t sm = (size_t)PADN * sizeof(float2) + (size_t)N * sizeof(float2) + (size_t)N * sizeof(float);
+  const size_t sm = (size_t)PADN * sizeof(float2) + (size_t)N * sizeof(float2);
   cudaError_t e;
   if ((e = set_smem(k_dct_cols_grad<LOG2N>, sm))) return e;
   const float sN2 = (float)((double)scale / ((double)N * (double)N));
@@ -778,14 +790,31 @@ cudaError_t dct_plan_init(DctPlan& p, int N) {
     if ((e = cudaMemcpy(p.wq, wq.data(), sizeof(float2) * (N / 2 + 1), cudaMemcpyHostToDevice))) return e;
   }
   // The dense matrix serves the sizes without a fast transform.
-  if (!p.fft) {
-    std::vector<float> C((size_t)N * N);
-    for (int k = 0; k < N; ++k) {
-      const double s = (k == 0) ? sqrt(1.0 / N) : sqrt(2.0 / N);
-      for (int n = 0; n < N; ++n) C[(size_t)k * N + n] = (float)(s * cos(PI * k * (2.0 * n + 1.0) / (2.0 * N)));
+  if (!p.fft) return dct_plan_dense(p);
+  return cudaSuccess;
+}
+
+cudaError_t dct_plan_dense(DctPlan& p) {
+  if (p.C && p.CT) return cudaSuccess;
+  const int N = p.N;
+  const double PI = 3.14159265358979323846;
+  std::vector<float> C((size_t)N * N), CT((size_t)N * N);
+  for (int k = 0; k < N; ++k) {
+    const double s = (k == 0) ? sqrt(1.0 / N) : sqrt(2.0 / N);
+    for (int n = 0; n < N; ++n) {
+      const float v = (float)(s * cos(PI * k * (2.0 * n + 1.0) / (2.0 * N)));
+      C[(size_t)k * N + n] = v;
+      CT[(size_t)n * N + k] = v;
     }
+  }
+  cudaError_t e;
+  if (!p.C) {
     if ((e = cudaMalloc(&p.C, sizeof(float) * (size_t)N * N))) return e;
     if ((e = cudaMemcpy(p.C, C.data(), sizeof(float) * (size_t)N * N, cudaMemcpyHostToDevice))) return e;
+  }
+  if (!p.CT) {
+    if ((e = cudaMalloc(&p.CT, sizeof(float) * (size_t)N * N))) return e;
+    if ((e = cudaMemcpy(p.CT, CT.data(), sizeof(float) * (size_t)N * N, cudaMemcpyHostToDevice))) return e;
   }
   return cudaSuccess;
 }
@@ -795,6 +824,7 @@ void dct_plan_free(DctPlan& p) {
   if (p.wq) cudaFree(p.wq);
   if (p.mu) cudaFree(p.mu);
   if (p.C) cudaFree(p.C);
+  if (p.CT) cudaFree(p.CT);
   p = DctPlan();
 }
 

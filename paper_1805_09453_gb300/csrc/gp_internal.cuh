@@ -36,6 +36,7 @@ struct DctPlan {
   float2* wq = nullptr;      // e^{-i pi k / (2N)}, k <= N/2       (fft)
   float* mu = nullptr;       // (4/h^2) sin^2(pi k / 2N), k < N
   float* C = nullptr;        // orthonormal DCT-II matrix, N x N   (dense)
+  float* CT = nullptr;       // its transpose (tensor-core path)
 };
 
 // Launchers (dct.cu)
@@ -57,6 +58,13 @@ cudaError_t dct_grad_cols(const DctPlan& p, const float* in, float* A, float* B,
                           cudaStream_t st);
 cudaError_t dct_grad_rows(const DctPlan& p, const float* A, const float* B, float* gx, float* gy, float* phi,
                           cudaStream_t st);
+// Build C (and C^T) for a plan that lacks them (tensor-core path).
+cudaError_t dct_plan_dense(DctPlan& p);
+// Split-precision (hi + lo BF16) tensor-core form, N % 128 == 0: four tcgen05
+// GEMMs; tmp holds 2*N*N floats; *err is set to 1 if a wait timed out.
+bool tc_solve_supported(int N);
+cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
+                         cudaStream_t st);
 // Dense-matrix form (any N): tmp must hold 2*N*N floats.
 cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp,
                                  float alpha, float scale, cudaStream_t st);

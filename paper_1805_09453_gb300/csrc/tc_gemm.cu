@@ -1,0 +1,271 @@
+// Split-precision cosine-transform solve on the 5th-generation tensor cores.
+//
+// The dense form of the Neumann solve (Appendix A cosine basis),
+//     x = C^T [ (C b C^T) / (alpha + mu_k + mu_l) ] C,   C = orthonormal DCT-II,
+// is four N x N x N contractions.  Each runs as a tcgen05 GEMM whose FP32
+// operands are split on the fly into a high and a low 16-bit part,
+// x = x_hi + x_lo (x_hi = bf16(x), x_lo = bf16(x - x_hi)), and
+//     A B^T ~= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+// is accumulated in FP32 in tensor memory (the dropped A_lo B_lo^T term is
+// ~2^-16 relative; BF16 keeps FP32's exponent range, so no operand scaling
+// is needed).  One CTA computes a 128 x 128 tile: all 128 threads load
+// and split a 128 x 64 slab of each operand into shared memory (canonical
+// K-major layout without swizzle), one thread issues the tcgen05.mma
+// instructions, tcgen05.commit signals an mbarrier when they have read shared
+// memory and written the accumulator, and the epilogue moves the accumulator
+// out of tensor memory with tcgen05.ld (thread = tile row), applies the
+// spectral gain when asked, and stores the tile, transposed when asked, so
+// that every operand of the next GEMM is again K-major:
+//     G1: T1^T <- (b C^T)^T      G2: T2^T <- (gain .* (C T1))^T
+//     G3: T3   <- C^T T2         G4: x    <- T3 C
+// Every wait on an mbarrier is bounded; a timeout sets an error flag, waits
+// (bounded) for the tensor core, frees the tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "gp_internal.cuh"
+
+namespace gp {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int TILE_BYTES = BM * BK * 2;  // one 16-bit operand slab, 16 KiB
+constexpr int SMEM_BYTES = 4 * TILE_BYTES + 64;
+constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Canonical K-major layout without swizzle: 8 x 8 core matrices of 16-bit
+// elements (8 rows x 16 bytes); core matrices adjacent along K are LBO = 128 B
+// apart, adjacent along M/N are SBO = 1024 B apart.
+__device__ __forceinline__ uint32_t kmajor_offset(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  const uint64_t lbo = 128, sbo = 1024;
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((lbo >> 4) << 16) | ((sbo >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D = F32, A = B = BF16 (or F16), both K-major, M = 128, N = 128.
+template <bool BF16>
+__device__ __forceinline__ uint32_t instr_desc() {
+  const uint32_t ab = BF16 ? 1u : 0u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t it = 0; it < limit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <bool BF16>
+__device__ __forceinline__ void split4(float4 v, uint2& hi, uint2& lo) {
+  if constexpr (BF16) {
+    const __nv_bfloat162 h01 = __floats2bfloat162_rn(v.x, v.y), h23 = __floats2bfloat162_rn(v.z, v.w);
+    const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+    const __nv_bfloat162 l01 = __floats2bfloat162_rn(v.x - f01.x, v.y - f01.y);
+    const __nv_bfloat162 l23 = __floats2bfloat162_rn(v.z - f23.x, v.w - f23.y);
+    hi = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+    lo = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+  } else {
+    const __half2 h01 = __floats2half2_rn(v.x, v.y), h23 = __floats2half2_rn(v.z, v.w);
+    const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+    const __half2 l01 = __floats2half2_rn(v.x - f01.x, v.y - f01.y);
+    const __half2 l23 = __floats2half2_rn(v.z - f23.x, v.w - f23.y);
+    hi = make_uint2(*reinterpret_cast<const uint32_t*>(&h01), *reinterpret_cast<const uint32_t*>(&h23));
+    lo = make_uint2(*reinterpret_cast<const uint32_t*>(&l01), *reinterpret_cast<const uint32_t*>(&l23));
+  }
+}
+
+// Load a 128 x 64 FP32 slab (rows r0.., columns k0.. of a row-major matrix with
+// leading dimension ld), multiplied by `s`, split into hi / lo 16-bit slabs.
+template <bool BF16>
+__device__ __forceinline__ void load_split(const float* __restrict__ src, int ld, int r0, int k0, float s,
+                                           uint8_t* hi, uint8_t* lo) {
+  // 128 rows x 16 float4 = 2048 float4; 16 per thread, 16 consecutive threads per row
+  for (int idx = threadIdx.x; idx < BM * (BK / 4); idx += blockDim.x) {
+    const int row = idx >> 4, q = idx & 15;
+    float4 v = *reinterpret_cast<const float4*>(src + (size_t)(r0 + row) * ld + k0 + 4 * q);
+    v.x *= s;
+    v.y *= s;
+    v.z *= s;
+    v.w *= s;
+    uint2 h, l;
+    split4<BF16>(v, h, l);
+    const uint32_t off = kmajor_offset(row, 4 * q);
+    *reinterpret_cast<uint2*>(hi + off) = h;
+    *reinterpret_cast<uint2*>(lo + off) = l;
+  }
+}
+
+// D(m0.., n0..) = epi( A(m0.., :) B(n0.., :)^T ), A: M x K, B: Nc x K, both
+// row-major (K-major) FP32.  mode 0: D[m][n] stored; 1: D^T stored (D[n][m]).
+// gain (mu != nullptr): D[m][n] *= gscale / (alpha + mu[m] + mu[n]), 0 when
+// the denominator is 0.  Operand scales sa, sb are undone in the epilogue.
+template <bool BF16>
+__global__ void __launch_bounds__(128) k_tc_gemm_split(const float* __restrict__ A, const float* __restrict__ B,
+                                                       float* __restrict__ D, int Nn, int K, int mode,
+                                                       const float* __restrict__ mu, float alpha, float gscale,
+                                                       float sa, float sb, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* a_hi = smem;
+  uint8_t* a_lo = smem + TILE_BYTES;
+  uint8_t* b_hi = smem + 2 * TILE_BYTES;
+  uint8_t* b_lo = smem + 3 * TILE_BYTES;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4 * TILE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 4 * TILE_BYTES + 16);
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t bar_addr = smem_u32(bar);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_addr), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = instr_desc<BF16>();
+  bool ok = true;
+  uint32_t phase = 0;
+  const int nk = K / BK;
+  for (int kt = 0; kt < nk; ++kt) {
+    if (kt > 0) {  // the previous MMAs must have read the slabs before they are overwritten
+      if (!mbar_wait(bar_addr, phase, kWaitLimit)) ok = false;
+      phase ^= 1u;
+    }
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    load_split<BF16>(A, K, m0, kt * BK, sa, a_hi, a_lo);
+    load_split<BF16>(B, K, n0, kt * BK, sb, b_hi, b_lo);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+#pragma unroll
+      for (int kk = 0; kk < BK / 16; ++kk) {
+        const uint32_t off = (uint32_t)kk * 256;  // 16 elements along K = two core matrices
+        mma_f16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+        mma_f16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
+        mma_f16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_addr)
+                   : "memory");
+    }
+  }
+  if (ok && nk > 0) {
+    if (!mbar_wait(bar_addr, phase, kWaitLimit)) ok = false;
+  }
+  if (!__syncthreads_and(ok)) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+    // let the tensor core finish (bounded) before the memory is released
+    mbar_wait(bar_addr, phase, kWaitLimit);
+    __syncthreads();
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int m = m0 + warp * 32 + lane;  // this thread's accumulator row
+    const float inv = 1.f / (sa * sb);
+    const float mum = mu ? __ldg(&mu[m]) : 0.f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+            "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+            "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+            "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float v[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        float x = __uint_as_float(r[c]) * inv;
+        if (mu) {
+          const float den = alpha + mum + __ldg(&mu[n0 + c0 + c]);
+          x = den > 0.f ? x * (gscale / den) : 0.f;
+        }
+        v[c] = x;
+      }
+      if (mode == 0) {
+        float* row = D + (size_t)m * Nn + n0 + c0;
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4*>(row + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) D[(size_t)(n0 + c0 + c) * Nn + m] = v[c];
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+  }
+}
+
+template <bool BF16>
+cudaError_t gemm(const float* A, const float* B, float* D, int N, int mode, const float* mu, float alpha,
+                 float gscale, float sa, float sb, int* err, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_split<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  if (e != cudaSuccess) return e;
+  dim3 grid(N / BN, N / BM);
+  k_tc_gemm_split<BF16><<<grid, 128, SMEM_BYTES, st>>>(A, B, D, N, N, mode, mu, alpha, gscale, sa, sb, err);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_solve_supported(int N) { return N >= 128 && N <= 8192 && N % 128 == 0; }
+
+cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
+                         cudaStream_t st) {
+  const int N = p.N;
+  if (!p.C || !p.CT || !tc_solve_supported(N)) return cudaErrorInvalidValue;
+  float* t0 = tmp;
+  float* t1 = tmp + (size_t)N * N;
+  cudaError_t e;
+  if ((e = gemm<true>(b, p.C, t0, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;    // T1^T = (b C^T)^T
+  if ((e = gemm<true>(p.C, t0, t1, N, 1, p.mu, alpha, scale, 1.f, 1.f, err, st))) return e;      // T2^T = (gain .* C T1)^T
+  if ((e = gemm<true>(p.CT, t1, t0, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;  // T3 = C^T T2
+  return gemm<true>(t0, p.CT, x, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st);                // x = T3 C
+}
+
+}  // namespace gp
