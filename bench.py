@@ -44,6 +44,7 @@ BYTES_PER_POINT = {
     "dct_rows_inv": 8,     # read spectrum, write x
     "dct_cols_grad": 12,   # read row spectrum, write A and B
     "dct_rows_grad": 16,   # read A, B; write grad x (2)   (gap checks also write phi)
+    "dct_tc_split": 32,    # four GEMMs, each reads two N^2 operands and writes one (contraction-bound)
     "rof_fused": 28,       # read u, p(2), I; write p(2), r
     "emd_fused": 48,       # read grad q(2), s(2), p(2), g; write s(2), p(2), d  (gap steps add m(2), e)
 }
@@ -352,6 +353,38 @@ def run_ours(args):
             ttg["rof"] = {"seconds": time.perf_counter() - t0, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
                           "status": rep["status_name"], "tau": rep["tau"]}
 
+    # split-precision study (FP32 fast transform vs hi+lo BF16 tensor-core GEMMs)
+    prec_study = None
+    if not args.no_prec and rank == 0:
+        from oracle import gprox_oracle as O
+
+        bp = np.ascontiguousarray(I[:, :], dtype=np.float32)
+        ref = O.helmholtz_solve(bp.astype(np.float64), 50.0, 1.0 / N)
+        bd = torch.from_numpy(bp).to(dev)
+        xo = torch.empty_like(bd)
+        prec_study = {"solve": f"(50 - Lap)^-1 I at {N}x{N} vs the FP64 oracle"}
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+            os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+        with torch.cuda.stream(stream):
+            for prec in ("fp32", "split_bf16"):
+                for _ in range(2):
+                    h.check(gprox.dct2_poisson(h, bd, xo, 50.0, prec=prec))
+                stream.synchronize()
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                for _ in range(3):
+                    gprox.dct2_poisson(h, bd, xo, 50.0, prec=prec)
+                a1.record(stream)
+                stream.synchronize()
+                ms_s = a0.elapsed_time(a1) / 3
+                err = float(np.linalg.norm(xo.cpu().numpy() - ref) / np.linalg.norm(ref))
+                row = {"ms": ms_s, "rel_l2_err": err}
+                if prec != "fp32":
+                    tf = 4 * 3 * 2.0 * N ** 3 / (ms_s / 1e3) / 1e12
+                    row.update({"tflops": tf, "bf16_peak_tflops": float(pk.get("bf16_tflops", 1900.0)),
+                                "tensor_frac": tf / float(pk.get("bf16_tflops", 1900.0))})
+                prec_study[prec] = row
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
@@ -360,7 +393,7 @@ def run_ours(args):
                        "N": N, "iters_per_step": ITERS_PER_STEP, "parallelism": f"replicas{ws}",
                        "l2": "no flush: inputs and working set (~1 GB per problem) exceed the 129 MB L2"},
             "roofline": roofline, "whole_iteration_hbm_frac": whole_frac, "kernels": kernels,
-            "gpu_launches": launches, "clocks": cl, "e2e": e2e, "time_to_gap": ttg,
+            "gpu_launches": launches, "clocks": cl, "e2e": e2e, "time_to_gap": ttg, "precision_study": prec_study,
             "last_gap": {"rof": g_rof["rel_gap"], "emd": g_emd["rel_gap"]}}
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle(N, 1)
@@ -385,6 +418,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-prec", action="store_true")
     ap.add_argument("--ttg-cap", type=int, default=60000)
     args = ap.parse_args()
     if args.impl == "reference":

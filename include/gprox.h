@@ -261,6 +261,20 @@ GP_API gp_status gp_state_destroy(gp_state s);
 GP_API gp_status dct2_poisson_static(const float* b, float* x, int N, double alpha, void* stream);
 
 /*
+ * gp_autotune: pick the tile shape of the fused stencil kernels (the height of
+ * the row block each thread walks: 4, 8, 16 or 32 rows) for grids of size N
+ * on this handle's device by timing each on scratch buffers; solves on this
+ * handle use the fastest from then on.  Keyed by (kernel, N, SM version).
+ * cache_path (may be NULL): a JSON file of {"kernel/N=../sm=..": rows} read
+ * before tuning (keys found there are not re-timed) and rewritten after.
+ * N % 4 == 0 required.  Allocates scratch for the duration of the call.
+ * gp_tuned_row_block returns the chosen height for kernel "rof_fused" or
+ * "emd_fused" (0 if not tuned).  The paper has no counterpart.
+ */
+GP_API gp_status gp_autotune(gp_handle h, int N, const char* cache_path, void* stream);
+GP_API int gp_tuned_row_block(gp_handle h, const char* kernel, int N);
+
+/*
  * Launch profiler (tracing).  gp_profile(h, 1) clears the counters and starts
  * recording: every kernel the handle launches is bracketed by CUDA events on
  * its stream (CUDA-graph replay is disabled while recording); gp_profile(h, 0)

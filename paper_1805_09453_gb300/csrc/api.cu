@@ -77,6 +77,7 @@ struct gp_handle_s {
   Profiler prof;
   bool capturing = false;
   int* tc_err = nullptr;  // timeout flag of the tensor-core kernels
+  std::map<std::string, int> tune;  // autotuned row-block heights, "rof_fused/N=.../sm=..." -> rb
   // batched solves: per-problem states, branch streams, fork/join events, results
   std::vector<gp_state_s*> batch;
   std::vector<cudaStream_t> aux;
@@ -104,6 +105,7 @@ struct gp_state_s {
   float* tmp = nullptr;              // solve scratch, 2 N^2
   double* part = nullptr;            // this state's per-block partial sums
   bool vec = false;
+  int rb = 16;                  // row-block height of the fused kernel (autotuned tile shape)
   bool partials_valid = false;  // part holds the fused gap partials of the current iterate
   double mass_den = 0;          // EMD: sum |f0 - f1| (mass-residual normaliser)
   std::vector<void*> allocs;
@@ -270,14 +272,16 @@ gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, 
   return GP_OK;
 }
 
-size_t fused_blocks(int N, bool vec) {
-  dim3 g = fused_grid(N, vec ? 4 : 1);
+size_t fused_blocks(int N, bool vec, int rb) {
+  dim3 g = fused_grid(N, vec ? 4 : 1, rb);
   return (size_t)g.x * g.y;
 }
 
 size_t state_part_size(int N) {
-  // fused partials (<= 4 per block; the scalar layout has the most blocks), then dual partials
-  return fused_blocks(N, false) * 4 + (size_t)reduce_blocks_1d((size_t)N * N) * 4;
+  // fused partials (<= 4 per block; most blocks: vector layout with the smallest row block,
+  // or the scalar layout), then dual partials
+  const size_t nb = std::max(fused_blocks(N, true, 4), fused_blocks(N, false, 16));
+  return nb * 4 + (size_t)reduce_blocks_1d((size_t)N * N) * 4;
 }
 
 // Copy `nq` reduced scalars to the host and wait for them.
@@ -337,6 +341,18 @@ gp_status alloc_state(gp_handle h, int kind, int N, gp_state* out) {
   return GP_OK;
 }
 
+std::string tune_key(gp_handle h, const char* kernel, int N) {
+  int maj = 0, mnr = 0;
+  cudaDeviceGetAttribute(&maj, cudaDevAttrComputeCapabilityMajor, h->device);
+  cudaDeviceGetAttribute(&mnr, cudaDevAttrComputeCapabilityMinor, h->device);
+  return std::string(kernel) + "/N=" + std::to_string(N) + "/sm=" + std::to_string(maj * 10 + mnr);
+}
+
+int tuned_rb(gp_handle h, const char* kernel, int N) {
+  auto it = h->tune.find(tune_key(h, kernel, N));
+  return it == h->tune.end() ? 16 : it->second;
+}
+
 // --------------------------------------------------------------- ROF state
 gp_status rof_setup(gp_state s, const float* I, double lam, double tau, double sigma, const float* u0,
                     const float* p0, const float* pbar0, cudaStream_t st) {
@@ -352,6 +368,7 @@ gp_status rof_setup(gp_state s, const float* I, double lam, double tau, double s
   s->cur = 0;
   s->partials_valid = false;
   s->vec = (N % 4 == 0) && aligned16(I);
+  s->rb = tuned_rb(h, "rof_fused", N);
   if (u0) GP_CUDA(h, cudaMemcpyAsync(s->prim, u0, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
   else GP_CUDA(h, cudaMemsetAsync(s->prim, 0, NN * sizeof(float), st));
   if (p0) GP_CUDA(h, cudaMemcpyAsync(s->p[0], p0, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -379,7 +396,7 @@ gp_status rof_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
     float* pin = s->p[s->cur];
     float* pout = s->p[1 - s->cur];
     GP_CUDA(h, plaunch(h, PK_ROF_FUSED, st, [&] {
-              return launch_rof_fused(s->gu, s->prim, pin, s->I, pout, s->r, s->part, P, s->vec, g, st);
+              return launch_rof_fused(s->gu, s->prim, pin, s->I, pout, s->r, s->part, P, s->vec, g, s->rb, st);
             }));
     s->cur = 1 - s->cur;
     s->n++;
@@ -399,7 +416,7 @@ gp_status emd_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
     const int c = s->cur;
     GP_CUDA(h, plaunch(h, PK_EMD_FUSED, st, [&] {
               return launch_emd_fused(s->prim, s->s[c], s->p[c], s->g, s->s[1 - c], s->p[1 - c], s->r, s->m, s->e,
-                                      s->part, P, s->vec, g, st);
+                                      s->part, P, s->vec, g, s->rb, st);
             }));
     s->cur = 1 - s->cur;
     s->n++;
@@ -473,6 +490,7 @@ gp_status emd_setup(gp_state s, const float* f0, const float* f1, double tau, do
   s->cur = 0;
   s->partials_valid = false;
   s->vec = N % 4 == 0;  // all fused-kernel operands are state buffers
+  s->rb = tuned_rb(h, "emd_fused", N);
   GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_sub(f0, f1, s->g, NN, st); }));
   if (m0) {
     GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_copy_field(m0, s->m, N, st); }));
@@ -511,7 +529,7 @@ gp_status state_gap_enqueue(gp_state s, double* dst, int prec, cudaStream_t st) 
   const int N = s->N;
   const size_t NN = (size_t)N * N;
   const bool fused = s->partials_valid;
-  const int nb = fused ? (int)fused_blocks(N, s->vec) : reduce_blocks_1d(NN);
+  const int nb = fused ? (int)fused_blocks(N, s->vec, s->vec ? s->rb : 16) : reduce_blocks_1d(NN);
   if (s->kind == KIND_ROF) {
     if (!fused)
       GP_CUDA(h, plaunch(h, PK_REDUCE, st,
@@ -1180,6 +1198,111 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
   GP_CUDA(h, cudaStreamSynchronize(st));
   for (int b = 0; b < B; ++b) reports[b].seconds = t.s();
   return worst;
+}
+
+// ------------------------------------------------------------ autotuner
+namespace {
+
+void tune_load(gp_handle h, const char* path) {
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof(line), f)) {
+    char key[256];
+    int rb = 0;
+    if (sscanf(line, " \"%255[^\"]\" : %d", key, &rb) == 2 && rb > 0) h->tune[key] = rb;
+  }
+  fclose(f);
+}
+
+bool tune_save(gp_handle h, const char* path) {
+  if (!path) return true;
+  FILE* f = fopen(path, "w");
+  if (!f) return false;
+  fprintf(f, "{\n");
+  size_t i = 0;
+  for (auto& kv : h->tune) fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++i < h->tune.size() ? "," : "");
+  fprintf(f, "}\n");
+  fclose(f);
+  return true;
+}
+
+}  // namespace
+
+gp_status gp_autotune(gp_handle h, int N, const char* cache_path, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  if (N < 4 || N > 8192 || N % 4 != 0) return fail(h, GP_ERR_ARG, "autotune needs N % 4 == 0 in [4, 8192]");
+  DeviceGuard g(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  tune_load(h, cache_path);
+  const char* names[2] = {"rof_fused", "emd_fused"};
+  const int kinds[2] = {KIND_ROF, KIND_EMD};
+  const int cands[4] = {4, 8, 16, 32};
+  const bool prof = h->prof.on;
+  h->prof.on = false;
+  for (int q = 0; q < 2; ++q) {
+    const std::string key = tune_key(h, names[q], N);
+    if (h->tune.count(key)) continue;
+    gp_state s = nullptr;
+    gp_status r = alloc_state(h, kinds[q], N, &s);
+    if (r != GP_OK) return r;
+    const size_t NN = (size_t)N * N;
+    float* in = nullptr;
+    cudaError_t e = cudaMalloc(&in, 2 * NN * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(in, 0, 2 * NN * sizeof(float), st);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best = 16;
+    float best_ms = 1e30f;
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+      const int rb = cands[c];
+      // the fused kernel on zeroed operands (its cost does not depend on the values)
+      auto launch = [&]() {
+        if (kinds[q] == KIND_ROF) {
+          RofParams P{N, (float)N, (float)((double)N * N), 1.f, 1.f, 1.f};
+          return launch_rof_fused(s->tmp, in, s->p[0], in, s->p[1], s->r, s->part, P, true, false, rb, st);
+        }
+        EmdParams P{N, (float)N, 1.f, 1.f};
+        return launch_emd_fused(s->prim, s->s[0], s->p[0], in, s->s[1], s->p[1], s->r, s->m, s->e, s->part, P, true,
+                                false, rb, st);
+      };
+      for (int w = 0; w < 2 && e == cudaSuccess; ++w) e = launch();
+      if (e != cudaSuccess) break;
+      cudaEventRecord(e0, st);
+      for (int it = 0; it < 5 && e == cudaSuccess; ++it) e = launch();
+      cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best_ms) {
+        best_ms = ms;
+        best = rb;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (in) cudaFree(in);
+    free_state(s);
+    if (e != cudaSuccess) {
+      h->prof.on = prof;
+      return cuda_fail(h, e, "autotune");
+    }
+    h->tune[key] = best;
+  }
+  h->prof.on = prof;
+  // states built before the tuning pick the new shapes up at their next set-up
+  for (auto& kv : h->cache) drop_graphs(kv.second);
+  if (!tune_save(h, cache_path)) return fail(h, GP_ERR_ARG, "cannot write the autotune cache file");
+  return GP_OK;
+}
+
+int gp_tuned_row_block(gp_handle h, const char* kernel, int N) {
+  if (!h || !kernel) return 0;
+  auto it = h->tune.find(tune_key(h, kernel, N));
+  return it == h->tune.end() ? 0 : it->second;
 }
 
 // ------------------------------------------------------------ profiling

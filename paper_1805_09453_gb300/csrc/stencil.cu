@@ -549,8 +549,6 @@ __global__ void __launch_bounds__(256) k_mass_stats(const float* __restrict__ f0
   block_reduce_store<3>(v, 0u, part);
 }
 
-constexpr int kRB = 16;
-
 inline int grid_1d(size_t n, int threads) {
   const size_t b = (n + threads - 1) / threads;
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -558,33 +556,52 @@ inline int grid_1d(size_t n, int threads) {
 
 }  // namespace
 
-dim3 fused_grid(int N, int V) { return dim3(ceil_div(ceil_div(N, V), 128), ceil_div(N, kRB)); }
+// Row-block heights the fused kernels are instantiated for (the autotuned
+// tile shape); 0 selects the default.
+constexpr int kRBDefault = 16;
+inline int norm_rb(int rb) { return (rb == 4 || rb == 8 || rb == 16 || rb == 32) ? rb : kRBDefault; }
+
+dim3 fused_grid(int N, int V, int rb) { return dim3(ceil_div(ceil_div(N, V), 128), ceil_div(N, norm_rb(rb))); }
+
+#define GP_RB_SWITCH(rb, CALL) \
+  switch (norm_rb(rb)) {      \
+    case 4: CALL(4); break;   \
+    case 8: CALL(8); break;   \
+    case 32: CALL(32); break; \
+    default: CALL(16); break; \
+  }
 
 cudaError_t launch_rof_fused(const float* gu, const float* u, const float* pin, const float* I, float* pout, float* r,
-                             double* part, const RofParams& P, bool vec, bool gap, cudaStream_t st) {
+                             double* part, const RofParams& P, bool vec, bool gap, int rb, cudaStream_t st) {
   const int V = vec ? 4 : 1;
-  dim3 g = fused_grid(P.N, V);
+  dim3 g = fused_grid(P.N, V, rb);
   if (vec) {
-    if (gap) k_rof_fused<4, kRB, true><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
-    else k_rof_fused<4, kRB, false><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
+#define GP_L(R)                                                                                  \
+  if (gap) k_rof_fused<4, R, true><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);           \
+  else k_rof_fused<4, R, false><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P)
+    GP_RB_SWITCH(rb, GP_L)
+#undef GP_L
   } else {
-    if (gap) k_rof_fused<1, kRB, true><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
-    else k_rof_fused<1, kRB, false><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
+    if (gap) k_rof_fused<1, kRBDefault, true><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
+    else k_rof_fused<1, kRBDefault, false><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pin, const float* g, float* sout,
                              float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
-                             bool gap, cudaStream_t st) {
+                             bool gap, int rb, cudaStream_t st) {
   const int V = vec ? 4 : 1;
-  dim3 gr = fused_grid(P.N, V);
+  dim3 gr = fused_grid(P.N, V, rb);
   if (vec) {
-    if (gap) k_emd_fused<4, kRB, true><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
-    else k_emd_fused<4, kRB, false><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
+#define GP_L(R)                                                                                            \
+  if (gap) k_emd_fused<4, R, true><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);     \
+  else k_emd_fused<4, R, false><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P)
+    GP_RB_SWITCH(rb, GP_L)
+#undef GP_L
   } else {
-    if (gap) k_emd_fused<1, kRB, true><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
-    else k_emd_fused<1, kRB, false><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
+    if (gap) k_emd_fused<1, kRBDefault, true><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
+    else k_emd_fused<1, kRBDefault, false><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);
   }
   return cudaGetLastError();
 }

@@ -19,14 +19,15 @@ struct EmdParams {
   float tau, sigma;
 };
 
-dim3 fused_grid(int N, int V);
+// rb: row-block height of the fused kernels (4, 8, 16 or 32; anything else -> 16)
+dim3 fused_grid(int N, int V, int rb);
 int reduce_blocks_1d(size_t n);
 
 cudaError_t launch_rof_fused(const float* gu, const float* u, const float* pin, const float* I, float* pout, float* r,
-                             double* part, const RofParams& P, bool vec, bool gap, cudaStream_t st);
+                             double* part, const RofParams& P, bool vec, bool gap, int rb, cudaStream_t st);
 cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pin, const float* g, float* sout,
                              float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
-                             bool gap, cudaStream_t st);
+                             bool gap, int rb, cudaStream_t st);
 cudaError_t launch_emd_dual(const float* phi, const float* gphi, const float* f0, const float* f1, int N, double* part,
                             int nblk, cudaStream_t st);
 cudaError_t launch_rof_stats(const float* I, int N, double* part, int nblk, cudaStream_t st);

@@ -23,7 +23,7 @@ PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
 EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_last_error", "dct2_poisson",
            "rof_solve", "emd_solve", "gp_state_create_rof", "gp_state_create_emd", "pd_step", "gp_state_read",
            "gp_state_gap", "gp_state_destroy", "gp_profile", "gp_profile_kernels", "gp_profile_query",
-           "dct2_poisson_static", "dct2_poisson_grad", "emd_solve_batched"]
+           "dct2_poisson_static", "dct2_poisson_grad", "emd_solve_batched", "gp_autotune", "gp_tuned_row_block"]
 
 
 class Opts(C.Structure):
@@ -75,13 +75,17 @@ def lib():
     L.gp_state_destroy.argtypes = [vp]
     L.dct2_poisson_static.argtypes = [vp, vp, i, d, vp]
     L.dct2_poisson_grad.argtypes = [vp, vp, vp, i, d, i, vp]
+    L.gp_autotune.argtypes = [vp, i, C.c_char_p, vp]
+    L.gp_tuned_row_block.argtypes = [vp, C.c_char_p, i]
+    L.gp_tuned_row_block.restype = i
     L.emd_solve_batched.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i),
                                     C.POINTER(Opts), C.POINTER(Report), vp]
     L.gp_profile.argtypes = [vp, i]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
     for name in EXPORTS:
-        if name not in ("gp_abi_version", "gp_default_opts", "gp_last_error", "gp_profile_kernels"):
+        if name not in ("gp_abi_version", "gp_default_opts", "gp_last_error", "gp_profile_kernels",
+                        "gp_tuned_row_block"):
             getattr(L, name).restype = i
     _lib = L
     return L
@@ -251,6 +255,15 @@ class State:
             self.close()
         except Exception:
             pass
+
+
+def autotune(h: Handle, N: int, cache_path: str | None = None, stream=None) -> int:
+    """Time the fused kernels' row-block heights for size N; later solves on h use the fastest."""
+    return lib().gp_autotune(h.ptr, int(N), cache_path.encode() if cache_path else None, _stream(stream))
+
+
+def tuned_row_block(h: Handle, kernel: str, N: int) -> int:
+    return lib().gp_tuned_row_block(h.ptr, kernel.encode(), int(N))
 
 
 def profile(h: Handle, enable: bool) -> int:
