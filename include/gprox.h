@@ -290,6 +290,69 @@ GP_API int gp_profile_kernels(void);
 GP_API gp_status gp_profile_query(gp_handle h, int kernel, const char** name, double* total_ms,
                                   long long* launches);
 
+/*
+ * Learned warm start for the EMD solve (section 4.2's dual potential).  A
+ * 4-level encoder-decoder CNN maps (f0, f1) to a potential phi_0; the start
+ * is p_0 = proj(grad phi_0) (forward differences, unit-disc projection), and
+ * the method's own duality gap decides between it and the zero start.  The
+ * paper has no learned component: this is an addition on top of its method.
+ *
+ * Network, base width C: 3x3 convolutions with zero padding, ReLU after all
+ * but the last, 2x2 average pooling, nearest 2x upsampling, concatenated
+ * skips [upsampled, skip]:
+ *   3 -> C -> C | C -> 2C -> 2C | 2C -> 4C -> 4C | 4C -> 8C -> 8C |
+ *   12C -> 4C -> 4C | 6C -> 2C -> 2C | 3C -> C -> C | C -> 1.
+ * Inputs per cell: (f0 - f1)/16, (f0 + f1)/16, psi / rms(psi) with
+ * Lap psi = f0 - f1 (Neumann, mean zero).  Output: phi with its mean removed.
+ * Parameters (FP32, gp_cnn_num_params floats): conv by conv in that order,
+ * weights W[cout][cin][3][3] (tap (dy, dx) at index 3 (dy + 1) + dx + 1,
+ * correlation: y(p) = sum W x(p + (dy, dx))) followed by biases b[cout].
+ * bf16 != 0: weights and activations are stored as BF16 (FP32 accumulation;
+ * gradients, master weights and Adam moments FP32); bf16 == 0: all FP32.
+ *
+ * Loss for targets t (per sample, averaged over the batch), e = phi - t with
+ * both mean-free, D the forward difference without the 1/h factor and with
+ * zero last slots:  |e|^2 / |t|^2 + |D e|^2 / |D t|^2.
+ *
+ * All device arrays are float32 N x N row-major on the handle's device; f0,
+ * f1 and phi_target are HOST arrays of B device pointers; N must be a
+ * multiple of 8 in [8, 8192].  The network owns its parameters and its
+ * activation buffers (grown on demand).  Errors: GP_ERR_ARG for bad
+ * arguments, GP_ERR_CUDA for CUDA failures; text in gp_cnn_last_error.
+ *   gp_cnn_create      He-uniform weights from `seed`, zero biases.
+ *   gp_cnn_get_params / gp_cnn_set_params   host float32 copies; set resets
+ *                      the Adam moments and step count.
+ *   gp_cnn_forward     phi: device, B*N*N.
+ *   gp_cnn_loss_grad   forward + loss + backward; *loss (may be NULL) is the
+ *                      loss, grad (host, num_params, may be NULL) receives
+ *                      the parameter gradient, which also stays on the
+ *                      device for gp_cnn_adam_step.  Synchronises when loss
+ *                      or grad is requested.
+ *   gp_cnn_adam_step   one Adam step (beta 0.9 / 0.999, eps 1e-8, bias
+ *                      correction) with the last gradient.
+ *   emd_solve_learned  emd_solve from the network's start: the gaps at n = 0
+ *                      of the learned and of the zero start are compared and
+ *                      the smaller one is kept (*used_warm = 1 for the
+ *                      learned start).  Arguments as emd_solve (p may be
+ *                      NULL); opts->warm_start must be 0.  report->seconds
+ *                      includes the network and the two gap probes.
+ */
+typedef struct gp_cnn_s* gp_cnn;
+GP_API gp_status gp_cnn_create(gp_handle h, int base_channels, int bf16, unsigned long long seed, gp_cnn* out);
+GP_API gp_status gp_cnn_destroy(gp_cnn net);
+GP_API const char* gp_cnn_last_error(gp_cnn net);
+GP_API long long gp_cnn_num_params(gp_cnn net);
+GP_API gp_status gp_cnn_get_params(gp_cnn net, float* w);
+GP_API gp_status gp_cnn_set_params(gp_cnn net, const float* w);
+GP_API gp_status gp_cnn_forward(gp_cnn net, int B, const float* const* f0, const float* const* f1, int N,
+                                float* phi, void* stream);
+GP_API gp_status gp_cnn_loss_grad(gp_cnn net, int B, const float* const* f0, const float* const* f1,
+                                  const float* const* phi_target, int N, double* loss, float* grad, void* stream);
+GP_API gp_status gp_cnn_adam_step(gp_cnn net, double lr, void* stream);
+GP_API gp_status emd_solve_learned(gp_handle h, gp_cnn net, const float* f0, const float* f1, float* m, float* p,
+                                   float* phi, int N, const gp_opts* opts, gp_report* report, int* used_warm,
+                                   void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -113,6 +113,8 @@ struct gp_state_s {
   std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
 };
 
+int gp::handle_device(gp_handle h) { return h->device; }
+
 namespace {
 
 struct DeviceGuard {

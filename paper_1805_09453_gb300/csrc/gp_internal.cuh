@@ -69,6 +69,9 @@ cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp,
 cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp,
                                  float alpha, float scale, cudaStream_t st);
 
+// Device ordinal a handle was created on (api.cu).
+int handle_device(gp_handle h);
+
 // Error text of the last failed handle-free call on this thread (static_solve.cu).
 const char* static_last_error();
 

@@ -23,7 +23,9 @@ PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
 EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_last_error", "dct2_poisson",
            "rof_solve", "emd_solve", "gp_state_create_rof", "gp_state_create_emd", "pd_step", "gp_state_read",
            "gp_state_gap", "gp_state_destroy", "gp_profile", "gp_profile_kernels", "gp_profile_query",
-           "dct2_poisson_static", "dct2_poisson_grad", "emd_solve_batched", "gp_autotune", "gp_tuned_row_block"]
+           "dct2_poisson_static", "dct2_poisson_grad", "emd_solve_batched", "gp_autotune", "gp_tuned_row_block",
+           "gp_cnn_create", "gp_cnn_destroy", "gp_cnn_last_error", "gp_cnn_num_params", "gp_cnn_get_params",
+           "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned"]
 
 
 class Opts(C.Structure):
@@ -81,11 +83,24 @@ def lib():
     L.emd_solve_batched.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i),
                                     C.POINTER(Opts), C.POINTER(Report), vp]
     L.gp_profile.argtypes = [vp, i]
+    L.gp_cnn_create.argtypes = [vp, i, i, C.c_ulonglong, C.POINTER(vp)]
+    L.gp_cnn_destroy.argtypes = [vp]
+    L.gp_cnn_last_error.argtypes = [vp]
+    L.gp_cnn_last_error.restype = C.c_char_p
+    L.gp_cnn_num_params.argtypes = [vp]
+    L.gp_cnn_num_params.restype = C.c_longlong
+    L.gp_cnn_get_params.argtypes = [vp, vp]
+    L.gp_cnn_set_params.argtypes = [vp, vp]
+    L.gp_cnn_forward.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), i, vp, vp]
+    L.gp_cnn_loss_grad.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i, C.POINTER(d), vp, vp]
+    L.gp_cnn_adam_step.argtypes = [vp, d, vp]
+    L.emd_solve_learned.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, C.POINTER(Opts), C.POINTER(Report),
+                                    C.POINTER(i), vp]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
     for name in EXPORTS:
         if name not in ("gp_abi_version", "gp_default_opts", "gp_last_error", "gp_profile_kernels",
-                        "gp_tuned_row_block"):
+                        "gp_tuned_row_block", "gp_cnn_last_error", "gp_cnn_num_params"):
             getattr(L, name).restype = i
     _lib = L
     return L
@@ -284,3 +299,95 @@ def profile_read(h: Handle):
 def pd_step(state: State, n_steps: int, prec="fp32", stream=None) -> int:
     """Run n_steps G-prox PDHG iterations on an explicit state."""
     return state.step(n_steps, prec, stream)
+
+
+def _ptr_array(ts):
+    P = C.c_void_p * len(ts)
+    return P(*[_ptr(t) for t in ts])
+
+
+class Cnn:
+    """The learned warm-start network (gp_cnn): 4-level encoder-decoder of base
+    width C mapping (f0, f1) to a dual potential -- see include/gprox.h."""
+
+    def __init__(self, h: Handle, C_base: int = 32, bf16: bool = True, seed: int = 0):
+        self.h = h
+        self._n = C.c_void_p()
+        st = lib().gp_cnn_create(h.ptr, int(C_base), 1 if bf16 else 0, C.c_ulonglong(seed), C.byref(self._n))
+        if st != GP_OK:
+            raise GproxError(st, "gp_cnn_create failed")
+        self.C = C_base
+        self.bf16 = bf16
+
+    def last_error(self) -> str:
+        return lib().gp_cnn_last_error(self._n).decode()
+
+    def check(self, st, allow=(GP_OK,)):
+        if st not in allow:
+            raise GproxError(st, self.last_error())
+        return st
+
+    @property
+    def num_params(self) -> int:
+        return int(lib().gp_cnn_num_params(self._n))
+
+    def get_params(self):
+        import numpy as np
+
+        w = np.empty(self.num_params, np.float32)
+        self.check(lib().gp_cnn_get_params(self._n, w.ctypes.data_as(C.c_void_p)))
+        return w
+
+    def set_params(self, w):
+        import numpy as np
+
+        w = np.ascontiguousarray(w, np.float32)
+        if w.size != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters, got {w.size}")
+        self.check(lib().gp_cnn_set_params(self._n, w.ctypes.data_as(C.c_void_p)))
+
+    def forward(self, f0s, f1s, stream=None):
+        """phi (B, N, N), mean-free, for lists of (N, N) device tensors."""
+        B, N = len(f0s), int(f0s[0].shape[-1])
+        phi = torch.empty((B, N, N), device=f0s[0].device, dtype=torch.float32)
+        self.check(lib().gp_cnn_forward(self._n, B, _ptr_array(f0s), _ptr_array(f1s), N, _ptr(phi), _stream(stream)))
+        return phi
+
+    def loss_grad(self, f0s, f1s, targets, want_grad=False, want_loss=True, stream=None):
+        """Forward + loss + backward; returns (loss or None, gradient (numpy) or None)."""
+        import numpy as np
+
+        B, N = len(f0s), int(f0s[0].shape[-1])
+        loss = C.c_double(float("nan"))
+        g = np.empty(self.num_params, np.float32) if want_grad else None
+        self.check(lib().gp_cnn_loss_grad(self._n, B, _ptr_array(f0s), _ptr_array(f1s), _ptr_array(targets), N,
+                                          C.byref(loss) if want_loss else None,
+                                          g.ctypes.data_as(C.c_void_p) if g is not None else None, _stream(stream)))
+        return (loss.value if want_loss else None), g
+
+    def adam_step(self, lr: float, stream=None):
+        self.check(lib().gp_cnn_adam_step(self._n, float(lr), _stream(stream)))
+
+    def close(self):
+        if self._n:
+            lib().gp_cnn_destroy(self._n)
+            self._n = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def emd_solve_learned(h: Handle, net: Cnn, f0, f1, m, p=None, phi=None, opts: Opts | None = None, stream=None):
+    """EMD solve from the network's start with the zero-start fallback;
+    returns (status, report dict with 'used_warm')."""
+    rep = Report()
+    used = C.c_int(0)
+    st = lib().emd_solve_learned(h.ptr, net._n, _ptr(f0), _ptr(f1), _ptr(m), _ptr(p), _ptr(phi),
+                                 int(f0.shape[-1]), C.byref(opts) if opts is not None else None, C.byref(rep),
+                                 C.byref(used), _stream(stream))
+    d = rep.as_dict()
+    d["used_warm"] = bool(used.value)
+    return st, d
