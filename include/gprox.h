@@ -291,19 +291,41 @@ GP_API gp_status gp_profile_query(gp_handle h, int kernel, const char** name, do
                                   long long* launches);
 
 /*
+ * emd_coarse_start: a start for the EMD solve from a coarser grid.  The
+ * densities are restricted to (N/factor)^2 by block means (same total mass),
+ * the coarse problem is solved with emd_solve(opts), and its dual potential
+ * phi_c = Lap^{-1} div p (section 4.2: the dual variable is the gradient of
+ * a potential with |grad phi| <= 1) is interpolated to N x N, bilinearly
+ * between cell centres (fine centre j at coarse coordinate (j + 1/2)/factor
+ * - 1/2, clamped to [0, N/factor - 1]).
+ *   f0, f1  device, N*N; phi device N*N out.
+ *   factor  >= 2 with N % factor == 0 and N / factor >= 2.
+ *   opts    the coarse solve's options (warm_start must be 0); report (may
+ *           be NULL) receives the coarse solve's report.
+ * Returns the coarse solve's status (GP_ERR_MAXITER still writes phi).
+ * Allocates 5 (N/factor)^2 floats of scratch for the call; synchronises the
+ * stream.  The paper has no counterpart (it starts from zero).
+ */
+GP_API gp_status emd_coarse_start(gp_handle h, const float* f0, const float* f1, int N, int factor,
+                                  const gp_opts* opts, float* phi, gp_report* report, void* stream);
+
+/*
  * Learned warm start for the EMD solve (section 4.2's dual potential).  A
- * 4-level encoder-decoder CNN maps (f0, f1) to a potential phi_0; the start
- * is p_0 = proj(grad phi_0) (forward differences, unit-disc projection), and
- * the method's own duality gap decides between it and the zero start.  The
- * paper has no learned component: this is an addition on top of its method.
+ * 4-level encoder-decoder CNN maps (f0, f1, prior) to a potential phi_0; the
+ * start is p_0 = proj(grad phi_0) (forward differences, unit-disc
+ * projection), and the method's own duality gap decides between it and the
+ * other starts.  The paper has no learned component: this is an addition on
+ * top of its method.
  *
  * Network, base width C: 3x3 convolutions with zero padding, ReLU after all
  * but the last, 2x2 average pooling, nearest 2x upsampling, concatenated
  * skips [upsampled, skip]:
  *   3 -> C -> C | C -> 2C -> 2C | 2C -> 4C -> 4C | 4C -> 8C -> 8C |
  *   12C -> 4C -> 4C | 6C -> 2C -> 2C | 3C -> C -> C | C -> 1.
- * Inputs per cell: (f0 - f1)/16, (f0 + f1)/16, psi / rms(psi) with
- * Lap psi = f0 - f1 (Neumann, mean zero).  Output: phi with its mean removed.
+ * Inputs per cell: (f0 - f1)/16, (f0 + f1)/16 and a prior potential (e.g.
+ * emd_coarse_start's; zero when the prior array or its entry is NULL).
+ * Output: phi = prior + head output, mean removed (a correction of the prior;
+ * gp_cnn_create zeroes the head, so a new network returns the prior).
  * Parameters (FP32, gp_cnn_num_params floats): conv by conv in that order,
  * weights W[cout][cin][3][3] (tap (dy, dx) at index 3 (dy + 1) + dx + 1,
  * correlation: y(p) = sum W x(p + (dy, dx))) followed by biases b[cout].
@@ -315,11 +337,12 @@ GP_API gp_status gp_profile_query(gp_handle h, int kernel, const char** name, do
  * zero last slots:  |e|^2 / |t|^2 + |D e|^2 / |D t|^2.
  *
  * All device arrays are float32 N x N row-major on the handle's device; f0,
- * f1 and phi_target are HOST arrays of B device pointers; N must be a
- * multiple of 8 in [8, 8192].  The network owns its parameters and its
- * activation buffers (grown on demand).  Errors: GP_ERR_ARG for bad
- * arguments, GP_ERR_CUDA for CUDA failures; text in gp_cnn_last_error.
- *   gp_cnn_create      He-uniform weights from `seed`, zero biases.
+ * f1, prior and phi_target are HOST arrays of B device pointers (prior may be
+ * NULL); N must be a multiple of 8 in [8, 8192].  The network owns its
+ * parameters and its activation buffers (grown on demand).  Errors:
+ * GP_ERR_ARG for bad arguments, GP_ERR_CUDA for CUDA failures; text in
+ * gp_cnn_last_error.
+ *   gp_cnn_create      He-uniform weights from `seed`, zero biases, zero head.
  *   gp_cnn_get_params / gp_cnn_set_params   host float32 copies; set resets
  *                      the Adam moments and step count.
  *   gp_cnn_forward     phi: device, B*N*N.
@@ -330,12 +353,17 @@ GP_API gp_status gp_profile_query(gp_handle h, int kernel, const char** name, do
  *                      or grad is requested.
  *   gp_cnn_adam_step   one Adam step (beta 0.9 / 0.999, eps 1e-8, bias
  *                      correction) with the last gradient.
- *   emd_solve_learned  emd_solve from the network's start: the gaps at n = 0
- *                      of the learned and of the zero start are compared and
- *                      the smaller one is kept (*used_warm = 1 for the
- *                      learned start).  Arguments as emd_solve (p may be
- *                      NULL); opts->warm_start must be 0.  report->seconds
- *                      includes the network and the two gap probes.
+ *   emd_solve_learned  emd_solve from the best of three starts: the learned
+ *                      one (prior = emd_coarse_start(coarse_factor,
+ *                      coarse_opts) when coarse_factor >= 2, no prior when
+ *                      coarse_factor == 0; coarse_opts NULL: relative gap
+ *                      1e-4, at most 100000 iterations, opts->use_graph),
+ *                      the prior alone, and zero; the
+ *                      start with the smallest duality gap at n = 0 is kept
+ *                      (*start_used: 0 zero, 1 learned, 2 prior).  Other
+ *                      arguments as emd_solve (p may be NULL);
+ *                      opts->warm_start must be 0.  report->seconds includes
+ *                      the coarse solve, the network and the gap probes.
  */
 typedef struct gp_cnn_s* gp_cnn;
 GP_API gp_status gp_cnn_create(gp_handle h, int base_channels, int bf16, unsigned long long seed, gp_cnn* out);
@@ -344,14 +372,15 @@ GP_API const char* gp_cnn_last_error(gp_cnn net);
 GP_API long long gp_cnn_num_params(gp_cnn net);
 GP_API gp_status gp_cnn_get_params(gp_cnn net, float* w);
 GP_API gp_status gp_cnn_set_params(gp_cnn net, const float* w);
-GP_API gp_status gp_cnn_forward(gp_cnn net, int B, const float* const* f0, const float* const* f1, int N,
-                                float* phi, void* stream);
+GP_API gp_status gp_cnn_forward(gp_cnn net, int B, const float* const* f0, const float* const* f1,
+                                const float* const* prior, int N, float* phi, void* stream);
 GP_API gp_status gp_cnn_loss_grad(gp_cnn net, int B, const float* const* f0, const float* const* f1,
-                                  const float* const* phi_target, int N, double* loss, float* grad, void* stream);
+                                  const float* const* prior, const float* const* phi_target, int N, double* loss,
+                                  float* grad, void* stream);
 GP_API gp_status gp_cnn_adam_step(gp_cnn net, double lr, void* stream);
 GP_API gp_status emd_solve_learned(gp_handle h, gp_cnn net, const float* f0, const float* f1, float* m, float* p,
-                                   float* phi, int N, const gp_opts* opts, gp_report* report, int* used_warm,
-                                   void* stream);
+                                   float* phi, int N, int coarse_factor, const gp_opts* coarse_opts,
+                                   const gp_opts* opts, gp_report* report, int* start_used, void* stream);
 
 #ifdef __cplusplus
 }

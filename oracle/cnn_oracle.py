@@ -19,13 +19,17 @@ in float64, with no blocking or fusion:
   concatenation [upsampled, skip];
 * widths 3 -> C -> C | C -> 2C -> 2C | 2C -> 4C -> 4C | 4C -> 8C -> 8C |
   12C -> 4C -> 4C | 6C -> 2C -> 2C | 3C -> C -> C | C -> 1;
-* inputs (f0 - f1)/16, (f0 + f1)/16, psi / rms(psi) with Lap psi = f0 - f1
-  (Neumann, mean zero; the oracle's own cosine-basis solve);
-* output phi with its mean removed;
+* inputs (f0 - f1)/16, (f0 + f1)/16 and a prior potential (zero if none);
+* output phi = prior + head output, with its mean removed;
 * loss per sample |e|^2/|t|^2 + |D e|^2/|D t|^2 (e = phi - t, both
   mean-free, D the forward difference without 1/h, zero last slots),
   averaged over the batch;
 * Adam (beta 0.9 / 0.999, eps 1e-8, bias-corrected).
+
+The prior used by the library is the coarse-grid start: the densities'
+block means on an (N/k)^2 grid, the EMD solved there (the oracle's own
+iteration), and its potential interpolated bilinearly between cell centres
+(clamped at the outermost centres) -- ``coarse_start`` below.
 
 The backward pass is derived by hand (the adjoint of each linear map and
 the ReLU mask); tests pin it against central finite differences of the loss.
@@ -138,19 +142,46 @@ def up2_adjoint(dy):
 
 
 # ------------------------------------------------------------------ inputs
-def features(f0, f1):
+def features(f0, f1, prior=None):
     """(3, N, N) input channels of one density pair."""
     f0 = np.asarray(f0, np.float64)
     f1 = np.asarray(f1, np.float64)
-    N = f0.shape[0]
-    psi = O.helmholtz_solve(f1 - f0, 0.0, 1.0 / N)  # (0 - Lap) psi = f1 - f0, mean zero
-    rms = np.sqrt(np.mean(psi * psi))
-    return np.stack([(f0 - f1) / 16.0, (f0 + f1) / 16.0, psi / rms if rms > 0 else 0.0 * psi])
+    pr = np.zeros_like(f0) if prior is None else np.asarray(prior, np.float64)
+    return np.stack([(f0 - f1) / 16.0, (f0 + f1) / 16.0, pr])
+
+
+def restrict_mean(f, k: int):
+    """Block means over k x k blocks (an (N/k)^2 density of the same mass)."""
+    n = f.shape[0] // k
+    return np.asarray(f, np.float64).reshape(n, k, n, k).mean(axis=(1, 3))
+
+
+def upsample_bilinear(c, k: int):
+    """Cell-centred bilinear interpolation from n x n to nk x nk: fine centre j
+    sits at coarse coordinate (j + 1/2)/k - 1/2, clamped to [0, n - 1]."""
+    c = np.asarray(c, np.float64)
+    n = c.shape[0]
+    x = np.clip((np.arange(n * k) + 0.5) / k - 0.5, 0.0, n - 1.0)
+    i0 = np.minimum(np.floor(x).astype(int), n - 1)
+    i1 = np.minimum(i0 + 1, n - 1)
+    t = x - i0
+    rows = c[i0] * (1 - t)[:, None] + c[i1] * t[:, None]       # interpolate along y
+    return rows[:, i0] * (1 - t)[None, :] + rows[:, i1] * t[None, :]
+
+
+def coarse_start(f0, f1, k: int, n_iters: int):
+    """Potential of the EMD on the k-times coarser grid after n_iters
+    iterations of the oracle's iteration (from zero), interpolated to N x N."""
+    c0, c1 = restrict_mean(f0, k), restrict_mean(f1, k)
+    st = O.emd_solve(c0, c1, n_iters=n_iters)
+    _, phi, _ = O.emd_dual(st["px"], st["py"], c0, c1)
+    return upsample_bilinear(phi, k)
 
 
 # ----------------------------------------------------------------- network
 def forward(w, x, C: int, bf16: bool = False):
-    """Network on inputs x (B, 3, N, N); returns (phi (B, N, N) mean-free, cache)."""
+    """Network on inputs x (B, 3, N, N), channel 2 the prior; returns
+    (phi (B, N, N) mean-free, cache)."""
     rnd = round_bf16 if bf16 else (lambda a: a)
     P = unpack(w, C)
     Wc = [(rnd(W), b) for W, b in P]  # compute copy of the weights; biases stay FP32
@@ -181,7 +212,7 @@ def forward(w, x, C: int, bf16: bool = False):
     k1 = np.concatenate([up2(d2b), s1], axis=1)
     d1a = conv(12, k1)
     d1b = conv(13, d1a)
-    raw = conv(14, d1b, relu=False)[:, 0]
+    raw = conv(14, d1b, relu=False)[:, 0] + np.asarray(x, np.float64)[:, 2]  # the prior, unrounded
     phi = raw - raw.mean(axis=(1, 2), keepdims=True)
     cache.update(x0=x0, a1=a1, s1=s1, p1=p1, a2=a2, s2=s2, p2=p2, a3=a3, s3=s3, p3=p3, m1=m1, m2=m2, k3=k3,
                  d3a=d3a, d3b=d3b, k2=k2, d2a=d2a, d2b=d2b, k1=k1, d1a=d1a, d1b=d1b)

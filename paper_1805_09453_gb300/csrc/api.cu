@@ -280,10 +280,13 @@ size_t fused_blocks(int N, bool vec, int rb) {
 }
 
 size_t state_part_size(int N) {
-  // fused partials (<= 4 per block; most blocks: vector layout with the smallest row block,
-  // or the scalar layout), then dual partials
-  const size_t nb = std::max(fused_blocks(N, true, 4), fused_blocks(N, false, 16));
-  return nb * 4 + (size_t)reduce_blocks_1d((size_t)N * N) * 4;
+  // Gap partials: the first region holds <= 4 values per block of either the
+  // fused kernels (most blocks: vector layout with the smallest row block, or
+  // the scalar layout) or the unfused 1-D reduction (a gap taken before any
+  // step); the EMD dual partials (2 per 1-D block) follow it.
+  const size_t nd = (size_t)reduce_blocks_1d((size_t)N * N);
+  const size_t nb = std::max({fused_blocks(N, true, 4), fused_blocks(N, false, 16), nd});
+  return nb * 4 + nd * 2;
 }
 
 // Copy `nq` reduced scalars to the host and wait for them.

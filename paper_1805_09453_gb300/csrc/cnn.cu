@@ -17,11 +17,12 @@
 //   dec3: [up(8C), skip3] 12C -> 4C -> 4C    (N/4)
 //   dec2: [up(4C), skip2]  6C -> 2C -> 2C    (N/2)
 //   dec1: [up(2C), skip1]  3C -> C -> C      (N)
-//   head: C -> 1                   phi (FP32), mean removed
-// Input channels: (f0 - f1)/16, (f0 + f1)/16 and psi / rms(psi), where psi is
-// the L2 (Hodge) potential, Lap psi = f0 - f1 with Neumann conditions and mean
-// zero -- global information that a network whose receptive field spans a few
-// dozen cells cannot gather by itself.
+//   head: C -> 1                   phi = prior + head (FP32), mean removed
+// Input channels: (f0 - f1)/16, (f0 + f1)/16 and a prior potential phi_c
+// (the EMD potential solved on a coarser grid and interpolated, see
+// emd_coarse_start; zero when none is given).  The output is a correction:
+// phi = phi_c + head, mean removed.  The head starts at zero, so an untrained
+// network returns the prior itself.
 //
 // Loss (per sample, averaged over the batch), e = phi - t with both sides
 // mean-free and D the unscaled forward difference with zero last slots:
@@ -270,21 +271,20 @@ __global__ void k_plane_sum(const float* __restrict__ x, long xbs, long NN, int 
   }
   if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
-// out = a - b
-__global__ void k_diff(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out, long n) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) out[i] = a[i] - b[i];
-}
-// Input channels of one sample: (f0 - f1)/16, (f0 + f1)/16, psi / rms(psi).
+// Input channels of one sample: (f0 - f1)/16, (f0 + f1)/16, prior (0 if null).
 template <typename T>
-__global__ void k_cnn_input(const float* __restrict__ f0, const float* __restrict__ f1, const float* __restrict__ psi,
-                            const double* __restrict__ psi_sq, T* __restrict__ X, long NN) {
-  const float inv = psi_sq[0] > 0 ? (float)rsqrt(psi_sq[0] / (double)NN) : 0.f;
+__global__ void k_cnn_input(const float* __restrict__ f0, const float* __restrict__ f1, const float* __restrict__ prior,
+                            T* __restrict__ X, long NN) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < NN; i += (long)gridDim.x * blockDim.x) {
     const float a = f0[i], c = f1[i];
     stf(X + i, (a - c) * 0.0625f);
     stf(X + NN + i, (a + c) * 0.0625f);
-    stf(X + 2 * NN + i, psi[i] * inv);
+    stf(X + 2 * NN + i, prior ? prior[i] : 0.f);
   }
+}
+// phi += prior (one sample)
+__global__ void k_add(float* __restrict__ phi, const float* __restrict__ prior, long NN) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < NN; i += (long)gridDim.x * blockDim.x) phi[i] += prior[i];
 }
 // x[b] -= sum[b] / NN for B planes of NN values
 __global__ void k_sub_mean(float* __restrict__ x, long NN, int B, const double* __restrict__ sum) {
@@ -455,7 +455,7 @@ struct gp_cnn_s {
   int cap_B = 0, cap_N = 0;
   void* act[NACT] = {};
   float* grd[NACT] = {};
-  float *phi = nullptr, *dphi = nullptr, *tgt = nullptr, *psi = nullptr, *pw = nullptr;
+  float *phi = nullptr, *dphi = nullptr, *tgt = nullptr, *pw = nullptr, *prior = nullptr;
   double* dsc = nullptr;  // per-sample FP64 scalars
   std::string err;
 };
@@ -494,10 +494,10 @@ void free_bufs(gp_cnn n) {
   cudaFree(n->phi);
   cudaFree(n->dphi);
   cudaFree(n->tgt);
-  cudaFree(n->psi);
   cudaFree(n->pw);
+  cudaFree(n->prior);
   cudaFree(n->dsc);
-  n->phi = n->dphi = n->tgt = n->psi = n->pw = nullptr;
+  n->phi = n->dphi = n->tgt = n->pw = n->prior = nullptr;
   n->dsc = nullptr;
   n->cap_B = n->cap_N = 0;
 }
@@ -517,8 +517,8 @@ gp_status reserve(gp_cnn n, int B, int N) {
   CN_CUDA(n, cudaMalloc((void**)&n->phi, (size_t)B * NN * 4));
   CN_CUDA(n, cudaMalloc((void**)&n->dphi, (size_t)B * NN * 4));
   CN_CUDA(n, cudaMalloc((void**)&n->tgt, (size_t)B * NN * 4));
-  CN_CUDA(n, cudaMalloc((void**)&n->psi, NN * 4));
   CN_CUDA(n, cudaMalloc((void**)&n->pw, 2 * NN * 4));
+  CN_CUDA(n, cudaMalloc((void**)&n->prior, NN * 4));
   CN_CUDA(n, cudaMalloc((void**)&n->dsc, (size_t)(8 * B + 8) * sizeof(double)));
   n->cap_B = B;
   n->cap_N = N;
@@ -655,41 +655,43 @@ gp_status check_dev(gp_cnn n, const void* p, const char* what) {
   return GP_OK;
 }
 
-gp_status check_batch(gp_cnn n, int B, const float* const* f0, const float* const* f1, int N) {
+gp_status check_batch(gp_cnn n, int B, const float* const* f0, const float* const* f1, const float* const* prior,
+                      int N) {
   if (B < 1 || !f0 || !f1) return cfail(n, GP_ERR_ARG, "bad batch arguments");
   if (N < 8 || N > 8192 || N % 8) return cfail(n, GP_ERR_ARG, "N must be a multiple of 8 in [8, 8192] (three 2x2 poolings)");
   for (int b = 0; b < B; ++b) {
     gp_status r;
     if ((r = check_dev(n, f0[b], "f0[b]")) != GP_OK || (r = check_dev(n, f1[b], "f1[b]")) != GP_OK) return r;
+    if (prior && prior[b] && (r = check_dev(n, prior[b], "prior[b]")) != GP_OK) return r;
   }
   return GP_OK;
 }
 
-// Input features and the forward pass of B samples; n->phi receives the
-// mean-free output.
+// Input features and the forward pass of B samples; n->phi receives
+// prior + head output, mean removed.
 template <typename T>
-gp_status forward_impl(gp_cnn n, int B, const float* const* f0, const float* const* f1, int N, cudaStream_t st) {
+gp_status forward_impl(gp_cnn n, int B, const float* const* f0, const float* const* f1, const float* const* prior,
+                       int N, cudaStream_t st) {
   Net<T> net(n, B, N, st);
   const long NN = (long)N * N;
-  for (int b = 0; b < B; ++b) {
-    // psi: (0 - Lap) psi = f1 - f0, i.e. Lap psi = f0 - f1, with mean zero
-    k_diff<<<g1d(NN), 256, 0, st>>>(f1[b], f0[b], n->pw, NN);
-    gp_status r = dct2_poisson(n->h, n->pw, n->psi, N, 0.0, GP_PREC_FP32, st);
-    if (r != GP_OK) return cfail(n, r, std::string("psi solve: ") + gp_last_error(n->h));
-    k_plane_sum<<<1, 256, 0, st>>>(n->psi, 0, NN, 1, n->dsc + b);
-    k_cnn_input<T><<<g1d(NN), 256, 0, st>>>(f0[b], f1[b], n->psi, n->dsc + b, net.ptr(X0) + b * net.bs(X0), NN);
-  }
+  for (int b = 0; b < B; ++b)
+    k_cnn_input<T><<<g1d(NN), 256, 0, st>>>(f0[b], f1[b], prior ? prior[b] : nullptr, net.ptr(X0) + b * net.bs(X0), NN);
   net.forward();
+  if (prior)
+    for (int b = 0; b < B; ++b)
+      if (prior[b]) k_add<<<g1d(NN), 256, 0, st>>>(n->phi + b * NN, prior[b], NN);
   k_plane_sum<<<B, 256, 0, st>>>(n->phi, NN, NN, 0, n->dsc);
   k_sub_mean<<<g1d(B * NN), 256, 0, st>>>(n->phi, NN, B, n->dsc);
   CN_CUDA(n, cudaGetLastError());
   return GP_OK;
 }
 
-gp_status forward(gp_cnn n, int B, const float* const* f0, const float* const* f1, int N, cudaStream_t st) {
+gp_status forward(gp_cnn n, int B, const float* const* f0, const float* const* f1, const float* const* prior, int N,
+                  cudaStream_t st) {
   gp_status r = reserve(n, B, N);
   if (r != GP_OK) return r;
-  return n->bf16 ? forward_impl<__nv_bfloat16>(n, B, f0, f1, N, st) : forward_impl<float>(n, B, f0, f1, N, st);
+  return n->bf16 ? forward_impl<__nv_bfloat16>(n, B, f0, f1, prior, N, st)
+                 : forward_impl<float>(n, B, f0, f1, prior, N, st);
 }
 
 template <typename T>
@@ -728,10 +730,12 @@ GP_API gp_status gp_cnn_create(gp_handle h, int base_channels, int bf16, unsigne
     gp_cnn_destroy(n);
     return GP_ERR_CUDA;
   }
-  // He-uniform weights from a 64-bit LCG, zero biases
+  // He-uniform weights from a 64-bit LCG, zero biases, zero head (the
+  // untrained network returns its prior)
   std::vector<float> w(P, 0.f);
   unsigned long long s = seed;
-  for (const Conv& c : n->convs) {
+  for (size_t ci = 0; ci + 1 < n->convs.size(); ++ci) {
+    const Conv& c = n->convs[ci];
     const double lim = sqrt(6.0 / (9.0 * c.cin));
     for (long i = 0; i < (long)c.cin * c.cout * 9; ++i) {
       s = s * 6364136223846793005ull + 1442695040888963407ull;
@@ -787,32 +791,33 @@ GP_API gp_status gp_cnn_set_params(gp_cnn n, const float* w) {
   return GP_OK;
 }
 
-GP_API gp_status gp_cnn_forward(gp_cnn n, int B, const float* const* f0, const float* const* f1, int N, float* phi,
-                                void* stream) {
+GP_API gp_status gp_cnn_forward(gp_cnn n, int B, const float* const* f0, const float* const* f1,
+                                const float* const* prior, int N, float* phi, void* stream) {
   if (!n) return GP_ERR_ARG;
   n->err.clear();
   DevGuard g(n->device);
-  gp_status r = check_batch(n, B, f0, f1, N);
+  gp_status r = check_batch(n, B, f0, f1, prior, N);
   if (r != GP_OK) return r;
   if ((r = check_dev(n, phi, "phi")) != GP_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((r = forward(n, B, f0, f1, N, st)) != GP_OK) return r;
+  if ((r = forward(n, B, f0, f1, prior, N, st)) != GP_OK) return r;
   CN_CUDA(n, cudaMemcpyAsync(phi, n->phi, (size_t)B * N * N * 4, cudaMemcpyDeviceToDevice, st));
   return GP_OK;
 }
 
 GP_API gp_status gp_cnn_loss_grad(gp_cnn n, int B, const float* const* f0, const float* const* f1,
-                                  const float* const* phi_target, int N, double* loss, float* grad, void* stream) {
+                                  const float* const* prior, const float* const* phi_target, int N, double* loss,
+                                  float* grad, void* stream) {
   if (!n) return GP_ERR_ARG;
   n->err.clear();
   DevGuard g(n->device);
-  gp_status r = check_batch(n, B, f0, f1, N);
+  gp_status r = check_batch(n, B, f0, f1, prior, N);
   if (r != GP_OK) return r;
   if (!phi_target) return cfail(n, GP_ERR_ARG, "phi_target is null");
   for (int b = 0; b < B; ++b)
     if ((r = check_dev(n, phi_target[b], "phi_target[b]")) != GP_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((r = forward(n, B, f0, f1, N, st)) != GP_OK) return r;
+  if ((r = forward(n, B, f0, f1, prior, N, st)) != GP_OK) return r;
   const long NN = (long)N * N;
   for (int b = 0; b < B; ++b)
     CN_CUDA(n, cudaMemcpyAsync(n->tgt + b * NN, phi_target[b], NN * 4, cudaMemcpyDeviceToDevice, st));
@@ -860,43 +865,72 @@ GP_API gp_status gp_cnn_adam_step(gp_cnn n, double lr, void* stream) {
 }
 
 GP_API gp_status emd_solve_learned(gp_handle h, gp_cnn n, const float* f0, const float* f1, float* m, float* p,
-                                   float* phi, int N, const gp_opts* opts, gp_report* report, int* used_warm,
-                                   void* stream) {
+                                   float* phi, int N, int coarse_factor, const gp_opts* coarse_opts,
+                                   const gp_opts* opts, gp_report* report, int* start_used, void* stream) {
   if (!h || !n || n->h != h) return GP_ERR_ARG;
   n->err.clear();
   const auto t0 = std::chrono::steady_clock::now();
   DevGuard g(n->device);
-  gp_status r = check_batch(n, 1, &f0, &f1, N);
+  gp_status r = check_batch(n, 1, &f0, &f1, nullptr, N);
   if (r != GP_OK) return r;
+  if (coarse_factor < 0 || coarse_factor == 1) return cfail(n, GP_ERR_ARG, "coarse_factor must be 0 (none) or >= 2");
   gp_opts o;
   gp_default_opts(&o);
   if (opts) o = *opts;
-  if (o.warm_start) return cfail(n, GP_ERR_ARG, "opts.warm_start must be 0: the network supplies the start");
+  if (o.warm_start) return cfail(n, GP_ERR_ARG, "opts.warm_start must be 0: the start is chosen here");
+  if ((r = reserve(n, 1, N)) != GP_OK) return r;
   cudaStream_t st = (cudaStream_t)stream;
-  if ((r = forward(n, 1, &f0, &f1, N, st)) != GP_OK) return r;
+  const float* prior = nullptr;
+  if (coarse_factor) {
+    gp_opts oc;
+    gp_default_opts(&oc);
+    oc.tol_rel_gap = 1e-4;
+    oc.max_iters = 100000;
+    oc.use_graph = o.use_graph;
+    if (coarse_opts) oc = *coarse_opts;
+    gp_report rc;
+    r = emd_coarse_start(h, f0, f1, N, coarse_factor, &oc, n->prior, &rc, stream);
+    if (r != GP_OK && r != GP_ERR_MAXITER) return cfail(n, r, std::string("coarse start: ") + gp_last_error(h));
+    prior = n->prior;
+  }
+  if ((r = forward(n, 1, &f0, &f1, prior ? &prior : nullptr, N, st)) != GP_OK) return r;
   float* p0 = p ? p : n->pw;
-  k_warm_dual<<<g1d((long)N * N), 256, 0, st>>>(n->phi, p0, N);
-  CN_CUDA(n, cudaGetLastError());
-  // Fallback: keep the start whose duality gap at n = 0 is smaller.
+  // Candidates: the learned start, the prior alone, the zero start; the one
+  // with the smallest duality gap at n = 0 is kept.
   gp_opts probe = o;
   probe.max_iters = 0;
-  gp_report rw, rz;
-  probe.warm_start = 1;
-  r = emd_solve(h, f0, f1, m, p0, nullptr, N, &probe, &rw, stream);
-  if (r != GP_OK && r != GP_ERR_MAXITER) return cfail(n, r, std::string("warm probe: ") + gp_last_error(h));
+  double best = INFINITY;
+  int choice = 0;
+  const float* cand[2] = {n->phi, prior};
+  for (int c = 0; c < 2; ++c) {
+    if (!cand[c]) continue;
+    k_warm_dual<<<g1d((long)N * N), 256, 0, st>>>(cand[c], p0, N);
+    CN_CUDA(n, cudaGetLastError());
+    probe.warm_start = 1;
+    gp_report rw;
+    r = emd_solve(h, f0, f1, m, p0, nullptr, N, &probe, &rw, stream);
+    if (r != GP_OK && r != GP_ERR_MAXITER) return cfail(n, r, std::string("start probe: ") + gp_last_error(h));
+    if (rw.rel_gap < best) {
+      best = rw.rel_gap;
+      choice = c == 0 ? 1 : 2;
+    }
+  }
   probe.warm_start = 0;
+  gp_report rz;
   r = emd_solve(h, f0, f1, m, nullptr, nullptr, N, &probe, &rz, stream);
   if (r != GP_OK && r != GP_ERR_MAXITER) return cfail(n, r, std::string("zero probe: ") + gp_last_error(h));
-  const bool warm = rw.rel_gap < rz.rel_gap;
-  if (!warm) CN_CUDA(n, cudaMemsetAsync(p0, 0, 2 * (size_t)N * N * 4, st));
+  if (!(best < rz.rel_gap)) choice = 0;
+  if (choice == 0) CN_CUDA(n, cudaMemsetAsync(p0, 0, 2 * (size_t)N * N * 4, st));
+  else k_warm_dual<<<g1d((long)N * N), 256, 0, st>>>(choice == 1 ? n->phi : prior, p0, N);
   o.warm_start = 1;
   gp_report rep;
   r = emd_solve(h, f0, f1, m, p0, phi, N, &o, &rep, stream);
   if (r != GP_OK && !(r == GP_ERR_MAXITER || r == GP_ERR_DIVERGED || r == GP_ERR_NONFINITE))
     return cfail(n, r, gp_last_error(h));
+  if (r != GP_OK) n->err = gp_last_error(h);
   rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (report) *report = rep;
-  if (used_warm) *used_warm = warm ? 1 : 0;
+  if (start_used) *start_used = choice;
   return r;
 }
 

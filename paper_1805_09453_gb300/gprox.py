@@ -25,7 +25,8 @@ EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_l
            "gp_state_gap", "gp_state_destroy", "gp_profile", "gp_profile_kernels", "gp_profile_query",
            "dct2_poisson_static", "dct2_poisson_grad", "emd_solve_batched", "gp_autotune", "gp_tuned_row_block",
            "gp_cnn_create", "gp_cnn_destroy", "gp_cnn_last_error", "gp_cnn_num_params", "gp_cnn_get_params",
-           "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned"]
+           "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned",
+           "emd_coarse_start"]
 
 
 class Opts(C.Structure):
@@ -91,11 +92,13 @@ def lib():
     L.gp_cnn_num_params.restype = C.c_longlong
     L.gp_cnn_get_params.argtypes = [vp, vp]
     L.gp_cnn_set_params.argtypes = [vp, vp]
-    L.gp_cnn_forward.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), i, vp, vp]
-    L.gp_cnn_loss_grad.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i, C.POINTER(d), vp, vp]
+    L.gp_cnn_forward.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i, vp, vp]
+    L.gp_cnn_loss_grad.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i,
+                                   C.POINTER(d), vp, vp]
     L.gp_cnn_adam_step.argtypes = [vp, d, vp]
-    L.emd_solve_learned.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, C.POINTER(Opts), C.POINTER(Report),
-                                    C.POINTER(i), vp]
+    L.emd_solve_learned.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, C.POINTER(Opts), C.POINTER(Opts),
+                                    C.POINTER(Report), C.POINTER(i), vp]
+    L.emd_coarse_start.argtypes = [vp, vp, vp, i, i, C.POINTER(Opts), vp, C.POINTER(Report), vp]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
     for name in EXPORTS:
@@ -302,6 +305,8 @@ def pd_step(state: State, n_steps: int, prec="fp32", stream=None) -> int:
 
 
 def _ptr_array(ts):
+    if ts is None:
+        return None
     P = C.c_void_p * len(ts)
     return P(*[_ptr(t) for t in ts])
 
@@ -346,22 +351,23 @@ class Cnn:
             raise ValueError(f"expected {self.num_params} parameters, got {w.size}")
         self.check(lib().gp_cnn_set_params(self._n, w.ctypes.data_as(C.c_void_p)))
 
-    def forward(self, f0s, f1s, stream=None):
-        """phi (B, N, N), mean-free, for lists of (N, N) device tensors."""
+    def forward(self, f0s, f1s, priors=None, stream=None):
+        """phi (B, N, N), mean-free, for lists of (N, N) device tensors (priors: list or None)."""
         B, N = len(f0s), int(f0s[0].shape[-1])
         phi = torch.empty((B, N, N), device=f0s[0].device, dtype=torch.float32)
-        self.check(lib().gp_cnn_forward(self._n, B, _ptr_array(f0s), _ptr_array(f1s), N, _ptr(phi), _stream(stream)))
+        self.check(lib().gp_cnn_forward(self._n, B, _ptr_array(f0s), _ptr_array(f1s), _ptr_array(priors), N,
+                                        _ptr(phi), _stream(stream)))
         return phi
 
-    def loss_grad(self, f0s, f1s, targets, want_grad=False, want_loss=True, stream=None):
+    def loss_grad(self, f0s, f1s, targets, priors=None, want_grad=False, want_loss=True, stream=None):
         """Forward + loss + backward; returns (loss or None, gradient (numpy) or None)."""
         import numpy as np
 
         B, N = len(f0s), int(f0s[0].shape[-1])
         loss = C.c_double(float("nan"))
         g = np.empty(self.num_params, np.float32) if want_grad else None
-        self.check(lib().gp_cnn_loss_grad(self._n, B, _ptr_array(f0s), _ptr_array(f1s), _ptr_array(targets), N,
-                                          C.byref(loss) if want_loss else None,
+        self.check(lib().gp_cnn_loss_grad(self._n, B, _ptr_array(f0s), _ptr_array(f1s), _ptr_array(priors),
+                                          _ptr_array(targets), N, C.byref(loss) if want_loss else None,
                                           g.ctypes.data_as(C.c_void_p) if g is not None else None, _stream(stream)))
         return (loss.value if want_loss else None), g
 
@@ -380,14 +386,30 @@ class Cnn:
             pass
 
 
-def emd_solve_learned(h: Handle, net: Cnn, f0, f1, m, p=None, phi=None, opts: Opts | None = None, stream=None):
-    """EMD solve from the network's start with the zero-start fallback;
-    returns (status, report dict with 'used_warm')."""
+def emd_solve_learned(h: Handle, net: Cnn, f0, f1, m, p=None, phi=None, opts: Opts | None = None,
+                      coarse_factor: int = 4, coarse_opts: Opts | None = None, stream=None):
+    """EMD solve from the best (by the gap at n = 0) of the learned, prior and zero
+    starts; returns (status, report dict with 'start': 'zero' | 'learned' | 'prior')."""
     rep = Report()
     used = C.c_int(0)
     st = lib().emd_solve_learned(h.ptr, net._n, _ptr(f0), _ptr(f1), _ptr(m), _ptr(p), _ptr(phi),
-                                 int(f0.shape[-1]), C.byref(opts) if opts is not None else None, C.byref(rep),
-                                 C.byref(used), _stream(stream))
+                                 int(f0.shape[-1]), int(coarse_factor),
+                                 C.byref(coarse_opts) if coarse_opts is not None else None,
+                                 C.byref(opts) if opts is not None else None, C.byref(rep), C.byref(used),
+                                 _stream(stream))
     d = rep.as_dict()
-    d["used_warm"] = bool(used.value)
+    d["start"] = ("zero", "learned", "prior")[used.value]
     return st, d
+
+
+def emd_coarse_start(h: Handle, f0, f1, factor: int, opts: Opts | None = None, phi=None, stream=None):
+    """Potential of the EMD solved on an N/factor grid, interpolated to N x N;
+    returns (status, phi, coarse report dict)."""
+    N = int(f0.shape[-1])
+    if phi is None:
+        phi = torch.empty((N, N), device=f0.device, dtype=torch.float32)
+    rep = Report()
+    st = lib().emd_coarse_start(h.ptr, _ptr(f0), _ptr(f1), N, int(factor),
+                                C.byref(opts) if opts is not None else None, _ptr(phi), C.byref(rep),
+                                _stream(stream))
+    return st, phi, rep.as_dict()

@@ -2,10 +2,12 @@
 
 Every step runs in the library: the training targets come from the library's
 own EMD solve (the converged dual potential phi* = Lap^{-1} div p*), the
-network's forward pass, loss, backward pass and Adam step are the library's
-kernels (``gp_cnn_*``), and the evaluation compares ``emd_solve`` from the
-zero start with ``emd_solve_learned`` (learned start with the zero-start
-fallback decided by the duality gap at n = 0).
+network's prior is the library's coarse-grid start (``emd_coarse_start``),
+the network's forward pass, loss, backward pass and Adam step are the
+library's kernels (``gp_cnn_*``), and the evaluation compares three arms to
+the same relative gap: ``emd_solve`` from zero, the prior alone (a network
+whose head is zero returns its prior), and ``emd_solve_learned`` (the start
+with the smallest duality gap at n = 0 among learned, prior and zero).
 
     python -m paper_1805_09453_gb300.learn --N 512 --C 32 --train 512 --test 64 \
         --steps 2000 --out warm.npz --report warm.json
@@ -39,37 +41,76 @@ def pairs(N: int, seeds, device="cuda"):
     return f0, f1
 
 
+def coarse_opts(tol: float = 1e-4, max_iters: int = 100000, gap_every: int = 50):
+    return gprox.default_opts(max_iters=max_iters, tol_rel_gap=tol, gap_every=gap_every, use_graph=1)
+
+
 def generate(h: gprox.Handle, N: int, seeds, tol: float = 1e-6, max_iters: int = 40000, gap_every: int = 50,
-             verbose: bool = False):
-    """Solve each pair with the plain method; returns f0, f1, phi* (S, N, N), the iteration counts and gaps."""
+             coarse_factor: int = 4, coarse_tol: float = 1e-4, verbose: bool = False):
+    """Solve each pair with the plain method and compute its coarse-grid prior;
+    returns f0, f1, phi*, prior (S, N, N), the iteration counts and the gaps."""
     f0, f1 = pairs(N, seeds)
     phi = torch.empty_like(f0)
+    prior = torch.zeros_like(f0)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(torch.cuda.Stream()):  # a non-default stream: the solves replay CUDA graphs
+        out = _generate(h, N, f0, f1, phi, prior, tol, max_iters, gap_every, coarse_factor, coarse_tol, verbose)
+    torch.cuda.synchronize()
+    return out
+
+
+def _generate(h, N, f0, f1, phi, prior, tol, max_iters, gap_every, coarse_factor, coarse_tol, verbose):
+    seeds = range(f0.shape[0])
     m = torch.empty((2, N, N), device=f0.device)
     p = torch.empty((2, N, N), device=f0.device)
     o = gprox.default_opts(max_iters=max_iters, tol_rel_gap=tol, gap_every=gap_every, use_graph=1)
+    oc = coarse_opts(coarse_tol)
     iters, gaps = [], []
     for i in range(len(seeds)):
         st, rep = gprox.emd_solve(h, f0[i], f1[i], m, p, phi[i], o)
         h.check(st, allow=(gprox.GP_OK, gprox.GP_ERR_MAXITER))
         iters.append(rep["iters"])
         gaps.append(rep["rel_gap"])
+        if coarse_factor:
+            st, _, _ = gprox.emd_coarse_start(h, f0[i], f1[i], coarse_factor, oc, phi=prior[i])
+            h.check(st, allow=(gprox.GP_OK, gprox.GP_ERR_MAXITER))
         if verbose and (i + 1) % 32 == 0:
             print(f"generated {i + 1}/{len(seeds)} pairs (median iterations {statistics.median(iters)})", flush=True)
     torch.cuda.synchronize()
-    return f0, f1, phi, iters, gaps
+    return f0, f1, phi, prior, iters, gaps
 
 
-def train(net: gprox.Cnn, f0, f1, phi, steps: int, batch: int, lr: float, seed: int = 0, log_every: int = 50,
-          lr_final: float | None = None):
-    """Adam on random mini-batches; cosine decay of the step size to lr_final."""
+def augment(f0, f1, phi, prior, g: int):
+    """Symmetry g in [0, 16) of a training sample: bit 0 transposes, bits 1-2
+    flip rows / columns, bit 3 swaps f0 and f1 (which negates the potentials).
+    Transposition and the swap map solutions to solutions exactly; a flip
+    turns forward into backward differences, so its targets are approximate."""
+    out = [f0, f1, phi, prior]
+    if g & 1:
+        out = [t.transpose(-2, -1) for t in out]
+    dims = [d for d, bit in ((-2, 2), (-1, 4)) if g & bit]
+    if dims:
+        out = [torch.flip(t, dims) for t in out]
+    if g & 8:
+        out = [out[1], out[0], -out[2], -out[3]]
+    return [t.contiguous() for t in out]
+
+
+def train(net: gprox.Cnn, f0, f1, phi, prior, steps: int, batch: int, lr: float, seed: int = 0,
+          log_every: int = 50, lr_final: float | None = None, augment_data: bool = True):
+    """Adam on random mini-batches (random symmetries when augment_data);
+    cosine decay of the step size to lr_final."""
     rng = np.random.default_rng(seed)
     S = f0.shape[0]
     lr_final = lr * 0.05 if lr_final is None else lr_final
     hist = []
     for k in range(steps):
         idx = rng.choice(S, size=min(batch, S), replace=False)
+        gs = rng.integers(0, 16, size=len(idx)) if augment_data else np.zeros(len(idx), int)
+        smp = [augment(f0[i], f1[i], phi[i], prior[i], int(g)) for i, g in zip(idx, gs)]
         want = (k % log_every == 0) or k == steps - 1
-        L, _ = net.loss_grad([f0[i] for i in idx], [f1[i] for i in idx], [phi[i] for i in idx], want_loss=want)
+        L, _ = net.loss_grad([a[0] for a in smp], [a[1] for a in smp], [a[2] for a in smp], [a[3] for a in smp],
+                             want_loss=want)
         if want:
             hist.append((k, L))
         a = lr_final + 0.5 * (lr - lr_final) * (1 + np.cos(np.pi * k / max(1, steps)))
@@ -78,62 +119,89 @@ def train(net: gprox.Cnn, f0, f1, phi, steps: int, batch: int, lr: float, seed: 
     return hist
 
 
-def test_loss(net: gprox.Cnn, f0, f1, phi, batch: int = 8):
+def test_loss(net: gprox.Cnn, f0, f1, phi, prior, batch: int = 8):
     out = []
     for i in range(0, f0.shape[0], batch):
         j = range(i, min(i + batch, f0.shape[0]))
-        L, _ = net.loss_grad([f0[k] for k in j], [f1[k] for k in j], [phi[k] for k in j])
+        L, _ = net.loss_grad([f0[k] for k in j], [f1[k] for k in j], [phi[k] for k in j], [prior[k] for k in j])
         out.append(L * len(j))
     return sum(out) / f0.shape[0]
 
 
+def _timed(fn):
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = fn()
+    torch.cuda.synchronize()
+    return out, time.perf_counter() - t0
+
+
 def evaluate(h: gprox.Handle, net: gprox.Cnn, f0, f1, tol: float = 1e-5, max_iters: int = 40000,
-             gap_every: int = 10):
-    """Per pair: iterations and seconds to `tol` from the zero start and from the learned start."""
+             gap_every: int = 10, coarse_factor: int = 4, coarse_tol: float = 1e-4, prior_arm: bool = True):
+    """Per pair: iterations, seconds and status to `tol` from the zero start,
+    from the prior alone and from the learned start (seconds include the
+    coarse solve, the network and the start probes).  Runs on a non-default
+    stream, so every arm replays CUDA graphs."""
+    torch.cuda.synchronize()
+    with torch.cuda.stream(torch.cuda.Stream()):
+        return _evaluate(h, net, f0, f1, tol, max_iters, gap_every, coarse_factor, coarse_tol, prior_arm)
+
+
+def _evaluate(h, net, f0, f1, tol, max_iters, gap_every, coarse_factor, coarse_tol, prior_arm):
     N = f0.shape[-1]
     m = torch.empty((2, N, N), device=f0.device)
     o = gprox.default_opts(max_iters=max_iters, tol_rel_gap=tol, gap_every=gap_every, use_graph=1)
+    oc = coarse_opts(coarse_tol)
+    base = None
+    if prior_arm and coarse_factor:
+        base = gprox.Cnn(h, 1, seed=0)
+        base.set_params(np.zeros(base.num_params, np.float32))  # output = prior
+    name = gprox.STATUS_NAMES
     rows = []
     for i in range(f0.shape[0]):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        st, rz = gprox.emd_solve(h, f0[i], f1[i], m, None, None, o)
-        torch.cuda.synchronize()
-        tz = time.perf_counter() - t0
-        h.check(st, allow=(gprox.GP_OK, gprox.GP_ERR_MAXITER))
-        t0 = time.perf_counter()
-        st, rw = gprox.emd_solve_learned(h, net, f0[i], f1[i], m, None, None, o)
-        torch.cuda.synchronize()
-        tw = time.perf_counter() - t0
-        net.check(st, allow=(gprox.GP_OK, gprox.GP_ERR_MAXITER))
-        rows.append({"zero_iters": rz["iters"], "zero_s": tz, "zero_gap": rz["rel_gap"],
-                     "warm_iters": rw["iters"], "warm_s": tw, "warm_gap": rw["rel_gap"],
-                     "used_warm": rw["used_warm"]})
+        (st, rz), tz = _timed(lambda: gprox.emd_solve(h, f0[i], f1[i], m, None, None, o))
+        row = {"zero_iters": rz["iters"], "zero_s": tz, "zero_gap": rz["rel_gap"], "zero_status": name[st]}
+        if base is not None:
+            (st, rp), tp = _timed(lambda: gprox.emd_solve_learned(h, base, f0[i], f1[i], m, None, None, o,
+                                                                   coarse_factor, oc))
+            row.update(prior_iters=rp["iters"], prior_s=tp, prior_gap=rp["rel_gap"], prior_status=name[st],
+                       prior_start=rp["start"])
+        (st, rw), tw = _timed(lambda: gprox.emd_solve_learned(h, net, f0[i], f1[i], m, None, None, o,
+                                                               coarse_factor, oc))
+        row.update(warm_iters=rw["iters"], warm_s=tw, warm_gap=rw["rel_gap"], warm_status=name[st],
+                   warm_start=rw["start"])
+        rows.append(row)
+    if base is not None:
+        base.close()
     return rows
 
 
-def network_cost(net: gprox.Cnn, f0, f1, reps: int = 10):
+def network_cost(net: gprox.Cnn, f0, f1, prior, reps: int = 10):
     """Mean seconds of one forward pass (B = 1) on the device."""
-    net.forward([f0[0]], [f1[0]])
+    net.forward([f0[0]], [f1[0]], [prior[0]])
     torch.cuda.synchronize()
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     s.record()
     for _ in range(reps):
-        net.forward([f0[0]], [f1[0]])
+        net.forward([f0[0]], [f1[0]], [prior[0]])
     e.record()
     torch.cuda.synchronize()
     return s.elapsed_time(e) / 1e3 / reps
 
 
 def summarize(rows):
-    zi = [r["zero_iters"] for r in rows]
-    wi = [r["warm_iters"] for r in rows]
-    zs = [r["zero_s"] for r in rows]
-    ws = [r["warm_s"] for r in rows]
-    return {"pairs": len(rows), "median_zero_iters": statistics.median(zi), "median_warm_iters": statistics.median(wi),
-            "median_zero_s": statistics.median(zs), "median_warm_s": statistics.median(ws),
-            "median_iter_ratio": statistics.median([w / max(z, 1) for w, z in zip(wi, zi)]),
-            "fallback_rate": sum(not r["used_warm"] for r in rows) / len(rows)}
+    med = statistics.median
+    out = {"pairs": len(rows)}
+    for arm in ("zero", "prior", "warm"):
+        if f"{arm}_iters" not in rows[0]:
+            continue
+        out[f"median_{arm}_iters"] = med([r[f"{arm}_iters"] for r in rows])
+        out[f"median_{arm}_s"] = med([r[f"{arm}_s"] for r in rows])
+        out[f"{arm}_not_ok"] = sum(r[f"{arm}_status"] != "GP_OK" for r in rows)
+    out["median_iter_ratio"] = med([r["warm_iters"] / max(r["zero_iters"], 1) for r in rows])
+    out["median_time_ratio"] = med([r["warm_s"] / max(r["zero_s"], 1e-12) for r in rows])
+    out["fallback_rate"] = sum(r["warm_start"] != "learned" for r in rows) / len(rows)
+    return out
 
 
 def main(argv=None):
@@ -149,6 +217,8 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--tol", type=float, default=1e-5, help="evaluation gap")
+    ap.add_argument("--coarse", type=int, default=4, help="coarse-grid factor of the prior (0: none)")
+    ap.add_argument("--coarse-tol", type=float, default=1e-4)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--init", default=None, help="start from these weights (.npz)")
     ap.add_argument("--out", default=None, help="write the trained weights (.npz)")
@@ -161,24 +231,26 @@ def main(argv=None):
         net.set_params(np.load(a.init)["w"])
     rep = {"N": a.N, "C": a.C, "bf16": not a.fp32, "params": net.num_params}
     t0 = time.perf_counter()
-    f0, f1, phi, it, gaps = generate(h, a.N, range(a.train), a.data_tol, a.data_max_iters, verbose=True)
+    f0, f1, phi, pri, it, gaps = generate(h, a.N, range(a.train), a.data_tol, a.data_max_iters,
+                                          coarse_factor=a.coarse, coarse_tol=a.coarse_tol, verbose=True)
     rep["data"] = {"pairs": a.train, "seconds": time.perf_counter() - t0, "median_iters": statistics.median(it),
                    "max_gap": max(gaps)}
-    g0, g1, gphi, _, _ = generate(h, a.N, range(TEST_SEED0, TEST_SEED0 + a.test), a.data_tol, a.data_max_iters)
-    rep["test_loss_init"] = test_loss(net, g0, g1, gphi)
+    g0, g1, gphi, gpri, _, _ = generate(h, a.N, range(TEST_SEED0, TEST_SEED0 + a.test), a.data_tol,
+                                        a.data_max_iters, coarse_factor=a.coarse, coarse_tol=a.coarse_tol)
+    rep["test_loss_init"] = test_loss(net, g0, g1, gphi, gpri)
     t0 = time.perf_counter()
-    hist = train(net, f0, f1, phi, a.steps, a.batch, a.lr, a.seed)
+    hist = train(net, f0, f1, phi, pri, a.steps, a.batch, a.lr, a.seed)
     print(f"trained {a.steps} steps in {time.perf_counter() - t0:.1f} s, loss {hist[-1][1]:.4g}", flush=True)
     rep["train"] = {"steps": a.steps, "batch": a.batch, "lr": a.lr, "seconds": time.perf_counter() - t0,
                     "loss": hist[-1][1], "history": hist}
-    rep["test_loss"] = test_loss(net, g0, g1, gphi)
-    rep["network_seconds"] = network_cost(net, g0, g1)
-    rows = evaluate(h, net, g0, g1, a.tol)
+    rep["test_loss"] = test_loss(net, g0, g1, gphi, gpri)
+    rep["network_seconds"] = network_cost(net, g0, g1, gpri)
+    if a.out:
+        np.savez(a.out, w=net.get_params(), C=a.C, N=a.N, coarse=a.coarse)
+    rows = evaluate(h, net, g0, g1, a.tol, coarse_factor=a.coarse, coarse_tol=a.coarse_tol)
     rep["eval"] = summarize(rows)
     rep["eval"]["tol"] = a.tol
     rep["rows"] = rows
-    if a.out:
-        np.savez(a.out, w=net.get_params(), C=a.C, N=a.N)
     if a.report:
         with open(a.report, "w") as f:
             json.dump(rep, f, indent=1)

@@ -36,23 +36,31 @@ def h():
     hh.close()
 
 
-def _batch(N, seeds):
+def _batch(N, seeds, with_prior=True):
+    """Device pairs, smooth random priors (or None) and the oracle's input stack."""
     f = [synth.gaussian_mixture_pair(N, s) for s in seeds]
     f0 = [torch.from_numpy(a).cuda() for a, _ in f]
     f1 = [torch.from_numpy(b).cuda() for _, b in f]
-    x = np.stack([K.features(a, b) for a, b in f])
-    return f0, f1, x
+    pri = None
+    if with_prior:
+        xs = (np.arange(N) + 0.5) / N
+        pri = [(0.3 * np.sin(2.0 + s + 3 * xs)[None, :] * np.cos(1.0 + 2 * xs - s)[:, None]).astype(np.float32)
+               for s in seeds]
+    x = np.stack([K.features(a, b, None if pri is None else pri[i]) for i, (a, b) in enumerate(f)])
+    return f0, f1, (None if pri is None else [torch.from_numpy(q).cuda() for q in pri]), x
 
 
 def _net(h, C, bf16, seed=1):
     from paper_1805_09453_gb300 import gprox
 
     net = gprox.Cnn(h, C, bf16=bf16, seed=seed)
-    # small random biases so that every ReLU sees both signs
+    # small random biases so that every ReLU sees both signs, and a non-zero head
     w = net.get_params()
     rng = np.random.default_rng(seed)
     off = 0
     for ci, co in K.conv_specs(C):
+        if co == 1:
+            w[off:off + ci * 9] = rng.uniform(-1, 1, ci * 9) * np.sqrt(6.0 / (9 * ci))
         off += ci * co * 9
         w[off:off + co] = rng.uniform(-0.05, 0.05, co)
         off += co
@@ -65,8 +73,8 @@ def _net(h, C, bf16, seed=1):
 def test_cnn_forward_matches_oracle(h, bf16, N, C, B):
     net = _net(h, C, bf16)
     assert net.num_params == K.num_params(C)
-    f0, f1, x = _batch(N, range(B))
-    phi = net.forward(f0, f1).cpu().numpy()
+    f0, f1, pri, x = _batch(N, range(B), with_prior=(N != 8))
+    phi = net.forward(f0, f1, pri).cpu().numpy()
     w = net.get_params().astype(np.float64)
     ref, _ = K.forward(w, x, C, bf16=bf16)
     assert np.abs(phi.mean(axis=(1, 2))).max() < 1e-6 * np.abs(ref).max()
@@ -82,12 +90,11 @@ def test_cnn_forward_matches_oracle(h, bf16, N, C, B):
 @pytest.mark.parametrize("N,C,B", [(64, 4, 2), (40, 4, 2), (128, 8, 1)])
 def test_cnn_loss_grad_matches_oracle(h, bf16, N, C, B):
     net = _net(h, C, bf16, seed=3)
-    f0, f1, x = _batch(N, range(10, 10 + B))
+    f0, f1, pri, x = _batch(N, range(10, 10 + B))
     rng = np.random.default_rng(N)
-    t = np.stack([K.features(*synth.gaussian_mixture_pair(N, 50 + b))[2] * 0.05 + 0.01 * rng.normal(size=(N, N))
-                  for b in range(B)])
+    t = np.stack([x[b, 2] + 0.02 * rng.normal(size=(N, N)) for b in range(B)])
     tt = [torch.from_numpy(t[b].astype(np.float32)).cuda() for b in range(B)]
-    L, g = net.loss_grad(f0, f1, tt, want_grad=True)
+    L, g = net.loss_grad(f0, f1, tt, pri, want_grad=True)
     w = net.get_params().astype(np.float64)
     t64 = t.astype(np.float32).astype(np.float64)
     Lr, gr, _ = K.loss_and_grad(w, x, t64, C, bf16=bf16)
@@ -109,13 +116,13 @@ def test_cnn_loss_grad_matches_oracle(h, bf16, N, C, B):
 
 def test_cnn_adam_matches_oracle(h):
     net = _net(h, 4, True, seed=5)
-    f0, f1, _ = _batch(32, [0, 1])
+    f0, f1, pri, _ = _batch(32, [0, 1])
     tt = [torch.randn(32, 32, device="cuda") for _ in range(2)]
     w = net.get_params().astype(np.float64)
     m = np.zeros_like(w)
     v = np.zeros_like(w)
     for k in range(1, 4):
-        _, g = net.loss_grad(f0, f1, tt, want_grad=True, want_loss=False)
+        _, g = net.loss_grad(f0, f1, tt, pri, want_grad=True, want_loss=False)
         net.adam_step(1e-3)
         w, m, v = K.adam_step(w, m, v, g.astype(np.float64), k, 1e-3)
         got = net.get_params()
@@ -129,41 +136,69 @@ def test_cnn_errors(h):
     net = gprox.Cnn(h, 2)
     f = torch.zeros(12, 12, device="cuda")
     phi = torch.zeros(1, 12, 12, device="cuda")
-    assert gprox.lib().gp_cnn_forward(net._n, 1, gprox._ptr_array([f]), gprox._ptr_array([f]), 12, gprox._ptr(phi),
-                                      None) == gprox.GP_ERR_ARG
+    assert gprox.lib().gp_cnn_forward(net._n, 1, gprox._ptr_array([f]), gprox._ptr_array([f]), None, 12,
+                                      gprox._ptr(phi), None) == gprox.GP_ERR_ARG
     assert "multiple of 8" in net.last_error()
     fh = torch.zeros(16, 16)
-    assert gprox.lib().gp_cnn_forward(net._n, 1, gprox._ptr_array([fh]), gprox._ptr_array([fh]), 16,
+    assert gprox.lib().gp_cnn_forward(net._n, 1, gprox._ptr_array([fh]), gprox._ptr_array([fh]), None, 16,
                                       gprox._ptr(phi), None) == gprox.GP_ERR_ARG
+    fd = torch.zeros(16, 16, device="cuda")
+    assert gprox.lib().gp_cnn_forward(net._n, 1, gprox._ptr_array([fd]), gprox._ptr_array([fd]),
+                                      gprox._ptr_array([fh]), 16, gprox._ptr(phi), None) == gprox.GP_ERR_ARG
+    assert "prior" in net.last_error()
+    st, _, _ = gprox.emd_coarse_start(h, fd, fd, 3)
+    assert st == gprox.GP_ERR_ARG
     with pytest.raises(ValueError):
         net.set_params(np.zeros(3, np.float32))
     assert gprox.lib().gp_cnn_adam_step(net._n, -1.0, None) == gprox.GP_ERR_ARG
 
 
+@pytest.mark.parametrize("N,k", [(64, 2), (64, 4), (96, 4)])
+def test_coarse_start_matches_oracle(h, N, k):
+    """Restriction, the coarse EMD iteration (300 iterations) and the
+    interpolation against the oracle's coarse_start; potentials compared
+    mean-free at the EMD potential bar of 1e-3."""
+    from paper_1805_09453_gb300 import gprox
+
+    f0, f1 = synth.gaussian_mixture_pair(N, 21)
+    st, phi, rep = gprox.emd_coarse_start(h, torch.from_numpy(f0).cuda(), torch.from_numpy(f1).cuda(), k,
+                                          gprox.default_opts(max_iters=300, tol_rel_gap=0.0, gap_every=300))
+    h.check(st)
+    assert rep["iters"] == 300
+    ref = K.coarse_start(f0, f1, k, 300)
+    got = phi.cpu().numpy()
+    assert rel_l2(got - got.mean(), ref - ref.mean()) < 1e-3
+
+
 def test_learned_start_matches_warm_dual_and_zero_net_falls_back(h):
     """A network whose output is zero gives p_0 = 0: the gap probe keeps the
-    zero start and the result equals emd_solve from zero bit for bit.  And a
-    random network's start p_0 equals proj(grad phi_0) of its own output."""
+    zero start and the result equals emd_solve from zero bit for bit.  A new
+    network (zero head) returns its prior, the coarse start."""
     from paper_1805_09453_gb300 import gprox
 
     N = 64
     net = gprox.Cnn(h, 4, seed=2)
-    f0, f1, _ = _batch(N, [7])
+    f0, f1, _, _ = _batch(N, [7], with_prior=False)
     o = gprox.default_opts(max_iters=200, tol_rel_gap=0.0, gap_every=20)
-    phi0 = net.forward(f0, f1)[0].cpu().numpy().astype(np.float64)
     p = torch.zeros((2, N, N), device="cuda")
     m = torch.zeros((2, N, N), device="cuda")
+    oc = gprox.default_opts(max_iters=400, tol_rel_gap=0.0, gap_every=400)
+    st, prior, _ = gprox.emd_coarse_start(h, f0[0], f1[0], 4, oc)
+    h.check(st)
+    phi0 = net.forward(f0, f1, [prior])[0].cpu().numpy().astype(np.float64)
+    pr = prior.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(phi0, pr - pr.mean(), atol=1e-6)
     o0 = gprox.default_opts(max_iters=0, tol_rel_gap=0.0)
-    st, rep = gprox.emd_solve_learned(h, net, f0[0], f1[0], m, p, None, o0)
+    st, rep = gprox.emd_solve_learned(h, net, f0[0], f1[0], m, p, None, o0, coarse_factor=4, coarse_opts=oc)
     net.check(st)
-    if rep["used_warm"]:
-        px, py = K.warm_dual(phi0)
-        assert rel_l2(p.cpu().numpy(), np.stack([px, py])) < 1e-5
+    assert rep["start"] in ("learned", "prior")  # identical potentials; the first one wins the tie
+    px, py = K.warm_dual(phi0)
+    assert rel_l2(p.cpu().numpy(), np.stack([px, py])) < 1e-5
     net.set_params(np.zeros(net.num_params, np.float32))
     m1 = torch.zeros((2, N, N), device="cuda")
-    st, rep = gprox.emd_solve_learned(h, net, f0[0], f1[0], m1, None, None, o)
+    st, rep = gprox.emd_solve_learned(h, net, f0[0], f1[0], m1, None, None, o, coarse_factor=0)
     net.check(st)
-    assert not rep["used_warm"]
+    assert rep["start"] == "zero"
     m2 = torch.zeros((2, N, N), device="cuda")
     st, rep2 = gprox.emd_solve(h, f0[0], f1[0], m2, None, None, o)
     h.check(st)
@@ -173,22 +208,28 @@ def test_learned_start_matches_warm_dual_and_zero_net_falls_back(h):
 
 def test_trained_network_cuts_iterations(h):
     """Train a small network (C = 8) on 96 solved 64^2 pairs with the library's
-    own kernels, then solve 12 held-out pairs to a relative gap of 1e-5 from
-    the zero start and from the learned start."""
+    own kernels, its prior the 4x coarser solve, then solve 12 held-out pairs
+    to a relative gap of 1e-5 from the zero start and from the learned start.
+    The trained network must fit the held-out potentials better than its
+    prior does (the untrained network) and the learned start must save
+    iterations over the zero start."""
     from paper_1805_09453_gb300 import gprox, learn
 
-    N = 64
+    N, k = 64, 4
     # targets: dual potentials solved to a gap of 2e-6 (or 20000 iterations; a
     # start needs no more than ~1e-4)
-    f0, f1, phi, iters, gaps = learn.generate(h, N, range(96), tol=2e-6, max_iters=20000)
+    f0, f1, phi, pri, iters, gaps = learn.generate(h, N, range(96), tol=2e-6, max_iters=20000, coarse_factor=k)
     assert max(gaps) < 1e-4
-    g0, g1, gphi, _, _ = learn.generate(h, N, range(learn.TEST_SEED0, learn.TEST_SEED0 + 12), tol=2e-6,
-                                        max_iters=20000)
+    g0, g1, gphi, gpri, _, _ = learn.generate(h, N, range(learn.TEST_SEED0, learn.TEST_SEED0 + 12), tol=2e-6,
+                                              max_iters=20000, coarse_factor=k)
     net = gprox.Cnn(h, 8, seed=0)
-    L0 = learn.test_loss(net, g0, g1, gphi)
-    hist = learn.train(net, f0, f1, phi, steps=600, batch=16, lr=2e-3)
-    L1 = learn.test_loss(net, g0, g1, gphi)
-    assert L1 < 0.5 * L0, (L0, L1, hist[-3:])
-    s = learn.summarize(learn.evaluate(h, net, g0, g1, tol=1e-5))
+    L0 = learn.test_loss(net, g0, g1, gphi, gpri)
+    hist = learn.train(net, f0, f1, phi, pri, steps=600, batch=16, lr=1e-3)
+    L1 = learn.test_loss(net, g0, g1, gphi, gpri)
+    print("held-out loss: prior", L0, "trained", L1)
+    assert L1 < L0, (L0, L1, hist[-3:])
+    rows = learn.evaluate(h, net, g0, g1, tol=1e-5, coarse_factor=k)
+    s = learn.summarize(rows)
     print(s)
+    assert all(r["warm_status"] in ("GP_OK",) for r in rows), rows
     assert s["median_warm_iters"] < 0.8 * s["median_zero_iters"], s

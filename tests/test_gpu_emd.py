@@ -151,3 +151,28 @@ def test_emd_full_size_two_iterations(h):
     # so the bar is 30x that floor
     floor = O.emd_mass_residual(ref["mx"].astype(np.float32), ref["my"].astype(np.float32), f0, f1)
     assert rep["mass_residual"] < 30.0 * floor, (rep["mass_residual"], floor)
+
+
+@pytest.mark.parametrize("N", [256, 512])
+def test_gap_before_any_step_leaves_state_intact(h, N):
+    """A gap taken right after setup (max_iters = 0) uses the unfused
+    reductions; afterwards a solve on the same handle must equal the same
+    solve on a fresh handle bit for bit (the reductions stay inside their
+    buffers)."""
+    from paper_1805_09453_gb300 import gprox
+
+    f0, f1 = synth.gaussian_mixture_pair(N, 5)
+    f0d, f1d = _t(f0), _t(f1)
+    m = torch.zeros((2, N, N), device="cuda")
+    st, rep0 = gprox.emd_solve(h, f0d, f1d, m, None, None, gprox.default_opts(max_iters=0, tol_rel_gap=0.0))
+    h.check(st)
+    assert np.isfinite(rep0["rel_gap"])
+    o = gprox.default_opts(max_iters=100, tol_rel_gap=0.0, gap_every=50)
+    st, rep1 = gprox.emd_solve(h, f0d, f1d, m, None, None, o)
+    h.check(st)
+    h2 = gprox.Handle(0)
+    m2 = torch.zeros_like(m)
+    st, rep2 = gprox.emd_solve(h2, f0d, f1d, m2, None, None, o)
+    h2.check(st)
+    h2.close()
+    assert torch.equal(m, m2) and rep1["primal"] == rep2["primal"]
