@@ -219,6 +219,10 @@ def main(argv=None):
     ap.add_argument("--tol", type=float, default=1e-5, help="evaluation gap")
     ap.add_argument("--coarse", type=int, default=4, help="coarse-grid factor of the prior (0: none)")
     ap.add_argument("--coarse-tol", type=float, default=1e-4)
+    ap.add_argument("--eval-N", type=int, default=0, help="also evaluate on pairs of this size (0: no)")
+    ap.add_argument("--eval-pairs", type=int, default=1)
+    ap.add_argument("--eval-coarse", type=int, default=8)
+    ap.add_argument("--eval-coarse-tol", type=float, default=1e-6)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--init", default=None, help="start from these weights (.npz)")
     ap.add_argument("--out", default=None, help="write the trained weights (.npz)")
@@ -251,10 +255,17 @@ def main(argv=None):
     rep["eval"] = summarize(rows)
     rep["eval"]["tol"] = a.tol
     rep["rows"] = rows
+    if a.eval_N:
+        e0, e1 = pairs(a.eval_N, range(TEST_SEED0, TEST_SEED0 + a.eval_pairs))
+        big = evaluate(h, net, e0, e1, a.tol, max_iters=200000, coarse_factor=a.eval_coarse,
+                       coarse_tol=a.eval_coarse_tol)
+        rep["eval_large"] = {"N": a.eval_N, "coarse": a.eval_coarse, "coarse_tol": a.eval_coarse_tol,
+                             "summary": summarize(big), "rows": big}
+        print(json.dumps(rep["eval_large"]["summary"]), flush=True)
     if a.report:
         with open(a.report, "w") as f:
             json.dump(rep, f, indent=1)
-    print(json.dumps({k: v for k, v in rep.items() if k not in ("rows",)}, default=str))
+    print(json.dumps({k: v for k, v in rep.items() if k not in ("rows", "eval_large")}, default=str))
     return rep
 
 
