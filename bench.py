@@ -50,10 +50,10 @@ BYTES_PER_POINT = {
 }
 
 # ncu DRAM traffic (read + write bytes per launch) of the dominant kernel at
-# 4096^2, from the committed summary profiles/dct_passes_4096.md; valid only
-# while the source file holding that kernel is unchanged (sha256 prefix).
+# 4096^2, from the committed summary profiles/spectral_and_fused_4096.md; valid
+# only while the source file holding that kernel is unchanged (sha256 prefix).
 NCU_TRAFFIC = {
-    "dct_cols_grad": {"bytes": 145.8e6, "file": "dct.cu", "src": "1819ce7260332e55"},
+    "dct_cols_grad": {"bytes": 162.48e6, "file": "dct.cu", "src": "0b22b5973c8aa4e9"},
 }
 
 
