@@ -198,6 +198,107 @@ __device__ __forceinline__ void fft_smem(float2* buf, int t, const float2* __res
   if constexpr (REM > 1) fft_stage<N, REM, DIR, TPF>(buf, Ns, t, tw);
 }
 
+// Base twiddles (w1, w2, w4, w8 of e^{-2 pi i m / N}) of thread t's butterfly
+// in radix-16 stages 1 .. S16-1 (stage 0 has none).  With N/16 threads per
+// transform every thread owns one butterfly per stage, so these are the same
+// for every transform a kernel runs: kernels with several FFTs load them once
+// into registers instead of gathering them from the table in every stage.
+template <int LOG2N>
+struct StageTw {
+  static constexpr int N = 1 << LOG2N, S16 = LOG2N / 4, NS = S16 > 1 ? S16 - 1 : 1;
+  float2 w[NS][4];
+  __device__ __forceinline__ void load(const float2* __restrict__ tw, int t) {
+    int Ns = 16;
+#pragma unroll
+    for (int s = 0; s + 1 < S16; ++s) {
+      const int m = (t & (Ns - 1)) * ((N / 16) / Ns);
+      w[s][0] = __ldg(&tw[m]);
+      w[s][1] = __ldg(&tw[2 * m]);
+      w[s][2] = __ldg(&tw[4 * m]);
+      w[s][3] = __ldg(&tw[8 * m]);
+      Ns *= 16;
+    }
+  }
+};
+
+// fft_smem with the base twiddles of the radix-16 stages 1 .. S16-1 supplied
+// by get(s, q) (q = 0..3: w1, w2, w4, w8 of stage s); TPF = N/16.
+template <int LOG2N, int DIR, int TPF, typename GetTw>
+__device__ __forceinline__ void fft_smem_tw_impl(float2* buf, int t, const float2* __restrict__ tw, GetTw get) {
+  constexpr int N = 1 << LOG2N;
+  constexpr int S16 = LOG2N / 4;
+  constexpr int REM = 1 << (LOG2N % 4);
+  constexpr int NB = N / 16;
+  static_assert(TPF == NB, "stored twiddles need one radix-16 butterfly per thread");
+  fft_stage<N, 16, DIR, TPF>(buf, 1, t, tw);  // stage 0: no twiddles
+  int Ns = 16;
+#pragma unroll
+  for (int s = 1; s < S16; ++s) {
+    float2 v[16];
+    const float2* src = buf + padi(t);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = src[r * (NB + NB / 16)];
+    __syncthreads();
+    const int k = t & (Ns - 1);
+    float2 w[16];
+    w[0] = make_float2(1.f, 0.f);
+    w[1] = get(s, 0);
+    w[2] = get(s, 1);
+    w[3] = cmul(w[1], w[2]);
+    w[4] = get(s, 2);
+#pragma unroll
+    for (int r = 5; r < 8; ++r) w[r] = cmul(w[r - 4], w[4]);
+    w[8] = get(s, 3);
+#pragma unroll
+    for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+      if (DIR > 0) w[r].y = -w[r].y;
+      v[r] = cmul(v[r], w[r]);
+    }
+    dft_reg<16, DIR>(v);
+    const int base = (t - k) * 16 + k;
+    float2* dst = buf + padi(base);
+    const int SS = Ns + Ns / 16;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) dst[r * SS] = v[r];
+    __syncthreads();
+    Ns *= 16;
+  }
+  if constexpr (REM > 1) fft_stage<N, REM, DIR, TPF>(buf, Ns, t, tw);
+}
+
+// ... with the twiddles in registers
+template <int LOG2N, int DIR, int TPF>
+__device__ __forceinline__ void fft_smem_tw(float2* buf, int t, const float2* __restrict__ tw,
+                                            const StageTw<LOG2N>& stw) {
+  fft_smem_tw_impl<LOG2N, DIR, TPF>(buf, t, tw, [&](int s, int q) { return stw.w[s - 1][q]; });
+}
+
+// ... with the twiddles in a shared-memory table twsm[(s - 1) * 4 + q][t]
+// (filled by fill_stage_tw), for kernels without registers to spare.
+template <int LOG2N, int DIR, int TPF>
+__device__ __forceinline__ void fft_smem_tws(float2* buf, int t, const float2* __restrict__ tw,
+                                             const float2* twsm) {
+  fft_smem_tw_impl<LOG2N, DIR, TPF>(buf, t, tw, [&](int s, int q) { return twsm[((s - 1) * 4 + q) * TPF + t]; });
+}
+
+template <int LOG2N>
+__host__ __device__ constexpr int stage_tw_entries() { return (LOG2N / 4 > 1 ? LOG2N / 4 - 1 : 0) * 4 * ((1 << LOG2N) / 16); }
+
+// twsm[(s - 1) * 4 + q][t] = tw[2^q m(s, t)], filled by all `nthr` threads of the CTA.
+template <int LOG2N>
+__device__ __forceinline__ void fill_stage_tw(float2* twsm, const float2* __restrict__ tw, int tid, int nthr) {
+  constexpr int N = 1 << LOG2N, TPF = N / 16;
+  for (int e = tid; e < stage_tw_entries<LOG2N>(); e += nthr) {
+    const int t = e % TPF, q = (e / TPF) % 4, s = e / (4 * TPF) + 1;
+    int Ns = 1;
+    for (int i = 0; i < s; ++i) Ns *= 16;
+    const int m = (t & (Ns - 1)) * ((N / 16) / Ns);
+    twsm[e] = __ldg(&tw[m << q]);
+  }
+}
+
 // Makhoul position of sample n inside the reordered sequence v.
 __device__ __forceinline__ int mk_pos(int n, int N) { return (n & 1) ? (N - 1 - (n >> 1)) : (n >> 1); }
 
@@ -396,12 +497,14 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 4 : 1)) k_d
   constexpr int N = C::N, TPF = C::TPF;
   extern __shared__ float2 smem[];
   const int cp = blockIdx.x, t = threadIdx.x;
+  StageTw<LOG2N> stw;
+  stw.load(tw, t);
   load_cols<N, TPF>(smem, data, cp, t);
   __syncthreads();
-  fft_smem<LOG2N, -1, TPF>(smem, t, tw);
+  fft_smem_tw<LOG2N, -1, TPF>(smem, t, tw, stw);
   col_spectrum<N, TPF>(smem, nullptr, cp, t, wq, mu, alpha, sN2);
   __syncthreads();
-  fft_smem<LOG2N, +1, TPF>(smem, t, tw);
+  fft_smem_tw<LOG2N, +1, TPF>(smem, t, tw, stw);
   store_cols<N, TPF>(smem, data, cp, t);
 }
 
@@ -470,9 +573,11 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
   float2* X = smem + PADN;  // gained spectra of the two columns, N complex
   const int cp = blockIdx.x, t = threadIdx.x;
   const float fN = (float)N;
+  StageTw<LOG2N> stw;
+  stw.load(tw, t);
   load_cols<N, TPF>(buf, in, cp, t);
   __syncthreads();
-  fft_smem<LOG2N, -1, TPF>(buf, t, tw);
+  fft_smem_tw<LOG2N, -1, TPF>(buf, t, tw, stw);
   col_spectrum<N, TPF>(buf, X, cp, t, wq, mu, alpha, sN2);
   __syncthreads();
   for (int pass = 0; pass < 3; ++pass) {
@@ -506,7 +611,7 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
       }
     }
     __syncthreads();
-    fft_smem<LOG2N, +1, TPF>(buf, t, tw);
+    fft_smem_tw<LOG2N, +1, TPF>(buf, t, tw, stw);
     if (pass == 0) {
       store_cols<N, TPF>(buf, A, cp, t);
     } else {
@@ -543,6 +648,8 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
   extern __shared__ float2 smem[];
   const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
   float2* buf = smem + f * PADN;
+  float2* twsm = smem + 2 * PADN;
+  fill_stage_tw<LOG2N>(twsm, tw, threadIdx.x, 2 * TPF);
   const int rb = blockIdx.x;
   const int r0 = 4 * rb + 2 * f;
   const float fN = (float)N;
@@ -580,7 +687,7 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
       }
     }
     __syncthreads();
-    fft_smem<LOG2N, +1, TPF>(buf, t, tw);
+    fft_smem_tws<LOG2N, +1, TPF>(buf, t, tw, twsm);
     if (pass < 2) {
       float* __restrict__ o = gx + (size_t)(r0 + pass) * N;
       for (int j = 4 * t; j < N; j += 4 * TPF) {
@@ -650,7 +757,7 @@ cudaError_t launch_grad_rows(const DctPlan& p, const float* A, const float* B, f
                              cudaStream_t st) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
-  const size_t sm = 2 * (size_t)PADN * sizeof(float2);
+  const size_t sm = (2 * (size_t)PADN + stage_tw_entries<LOG2N>()) * sizeof(float2);
   cudaError_t e;
   if ((e = set_smem(k_dct_rows_grad<LOG2N>, sm))) return e;
   k_dct_rows_grad<LOG2N><<<N / 4, 2 * TPF, sm, st>>>(A, B, gx, gy, phi, p.tw, p.wq);
