@@ -390,14 +390,20 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
   const int rb = blockIdx.x;
   const float* __restrict__ xa = in + (size_t)(4 * rb + 2 * f) * N;
   const float* __restrict__ xb = xa + N;
-  for (int j = 4 * t; j < N; j += 4 * TPF)
+#pragma unroll
+  for (int ii = 0; ii < N / (4 * TPF); ++ii) {
+    const int j = 4 * t + ii * 4 * TPF;
     scatter4(buf, j, N, *reinterpret_cast<const float4*>(xa + j), *reinterpret_cast<const float4*>(xb + j));
+  }
   __syncthreads();
   fft_smem<LOG2N, -1, TPF>(buf, t, tw);
   float* __restrict__ o = out + (size_t)rb * 4 * N;
   const float2* b0 = smem;
   const float2* b1 = smem + PADN;
-  for (int k = threadIdx.x; k <= N / 2; k += 2 * TPF) {
+  #pragma unroll
+  for (int kk = 0; kk <= (N / 2) / (2 * TPF); ++kk) {
+    if (kk == (N / 2) / (2 * TPF) && threadIdx.x != 0) break;
+    const int k = threadIdx.x + kk * 2 * TPF;
     if (k == 0 || k == N / 2) {
       const float sc = k == 0 ? 1.f : kRsqrt2;
       const float2 z0 = b0[padi(k)], z1 = b1[padi(k)];
@@ -419,7 +425,9 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
 // four complex values.
 template <int N, int TPF>
 __device__ __forceinline__ void load_cols(float2* buf, const float* __restrict__ src, int cp, int t) {
-  for (int rb = t; rb < N / 4; rb += TPF) {
+  #pragma unroll
+  for (int ii = 0; ii < (N / 4) / TPF; ++ii) {
+    const int rb = t + ii * TPF;
     const float* p = src + (size_t)rb * 4 * N + (size_t)(2 * cp) * 4;
     const float4 a = *reinterpret_cast<const float4*>(p);
     const float4 b = *reinterpret_cast<const float4*>(p + 4);
@@ -434,7 +442,9 @@ __device__ __forceinline__ void load_cols(float2* buf, const float* __restrict__
 // Store the synthesised columns (real part -> column 2cp, imaginary -> 2cp+1).
 template <int N, int TPF>
 __device__ __forceinline__ void store_cols(const float2* buf, float* __restrict__ dst, int cp, int t) {
-  for (int rb = t; rb < N / 4; rb += TPF) {
+  #pragma unroll
+  for (int ii = 0; ii < (N / 4) / TPF; ++ii) {
+    const int rb = t + ii * TPF;
     const int n = 4 * rb;
     const float2 z0 = buf[padi(mk_pos(n, N))], z1 = buf[padi(mk_pos(n + 1, N))];
     const float2 z2 = buf[padi(mk_pos(n + 2, N))], z3 = buf[padi(mk_pos(n + 3, N))];
@@ -452,7 +462,10 @@ __device__ __forceinline__ void col_spectrum(float2* buf, float2* X, int cp, int
                                              const float* __restrict__ mu, float alpha, float sN2) {
   const int la = 2 * cp, lb = la + 1;
   const float mua = __ldg(&mu[la]), mub = __ldg(&mu[lb]);
-  for (int k = t; k <= N / 2; k += TPF) {
+  #pragma unroll
+  for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
+    if (kk == (N / 2) / TPF && t != 0) break;
+    const int k = t + kk * TPF;
     if (k == 0 || k == N / 2) {
       const int pk = padi(k);
       const float2 z = buf[pk];
@@ -521,7 +534,10 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
   const float* __restrict__ src = in + (size_t)rb * 4 * N;
   float2* b0 = smem;
   float2* b1 = smem + PADN;
-  for (int k = threadIdx.x; k <= N / 2; k += 2 * TPF) {
+  #pragma unroll
+  for (int kk = 0; kk <= (N / 2) / (2 * TPF); ++kk) {
+    if (kk == (N / 2) / (2 * TPF) && threadIdx.x != 0) break;
+    const int k = threadIdx.x + kk * 2 * TPF;
     const float4 vk = *reinterpret_cast<const float4*>(src + 4 * k);
     if (k == 0) {
       b0[0] = make_float2(vk.x, vk.y);
@@ -547,7 +563,9 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
   fft_smem<LOG2N, +1, TPF>(buf, t, tw);
   float* __restrict__ oa = out + (size_t)(4 * rb + 2 * f) * N;
   float* __restrict__ ob = oa + N;
-  for (int j = 4 * t; j < N; j += 4 * TPF) {
+  #pragma unroll
+  for (int ii = 0; ii < N / (4 * TPF); ++ii) {
+    const int j = 4 * t + ii * 4 * TPF;
     const int hj = j >> 1;
     const float2 z0 = buf[padi(hj)], z1 = buf[padi(N - 1 - hj)];
     const float2 z2 = buf[padi(hj + 1)], z3 = buf[padi(N - 2 - hj)];
@@ -581,7 +599,10 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
   col_spectrum<N, TPF>(buf, X, cp, t, wq, mu, alpha, sN2);
   __syncthreads();
   for (int pass = 0; pass < 3; ++pass) {
-    for (int k = t; k <= N / 2; k += TPF) {
+    #pragma unroll
+  for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
+    if (kk == (N / 2) / TPF && t != 0) break;
+    const int k = t + kk * TPF;
       const float2 xk = X[k];
       if (pass == 0) {
         if (k == 0) {
@@ -617,7 +638,9 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
     } else {
       // D_y of column (2cp + pass - 1): one float4 (4 rows) per row block
       const int col = 2 * cp + pass - 1;
-      for (int rb = t; rb < N / 4; rb += TPF) {
+      #pragma unroll
+  for (int ii = 0; ii < (N / 4) / TPF; ++ii) {
+    const int rb = t + ii * TPF;
         float v[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -657,7 +680,10 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
   for (int pass = 0; pass < npass; ++pass) {
     // pass 0: D_x of A row r0; 1: D_x of A row r0+1; 2: plain of B rows r0, r0+1; 3: plain of A rows
     const float* __restrict__ src = (pass == 2 ? B : A) + (size_t)rb * 4 * N;
-    for (int k = t; k <= N / 2; k += TPF) {
+    #pragma unroll
+  for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
+    if (kk == (N / 2) / TPF && t != 0) break;
+    const int k = t + kk * TPF;
       const float2 xk2 = *reinterpret_cast<const float2*>(src + 4 * k + 2 * f);
       if (pass < 2) {
         const float xk = pass == 0 ? xk2.x : xk2.y;
@@ -690,7 +716,9 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
     fft_smem_tws<LOG2N, +1, TPF>(buf, t, tw, twsm);
     if (pass < 2) {
       float* __restrict__ o = gx + (size_t)(r0 + pass) * N;
-      for (int j = 4 * t; j < N; j += 4 * TPF) {
+      #pragma unroll
+  for (int ii = 0; ii < N / (4 * TPF); ++ii) {
+    const int j = 4 * t + ii * 4 * TPF;
         const int hj = j >> 1;
         const float2 z0 = buf[padi(hj)], z1 = buf[padi(N - 1 - hj)];
         const float2 z2 = buf[padi(hj + 1)], z3 = buf[padi(N - 2 - hj)];
@@ -701,7 +729,9 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
     } else {
       float* __restrict__ oa = (pass == 2 ? gy : phi) + (size_t)r0 * N;
       float* __restrict__ ob = oa + N;
-      for (int j = 4 * t; j < N; j += 4 * TPF) {
+      #pragma unroll
+  for (int ii = 0; ii < N / (4 * TPF); ++ii) {
+    const int j = 4 * t + ii * 4 * TPF;
         const int hj = j >> 1;
         const float2 z0 = buf[padi(hj)], z1 = buf[padi(N - 1 - hj)];
         const float2 z2 = buf[padi(hj + 1)], z3 = buf[padi(N - 2 - hj)];
