@@ -147,7 +147,7 @@ gp_status cuda_fail(gp_handle h, cudaError_t e, const char* where) {
 // Launch through the profiler: when it is on (and no graph is being
 // captured), CUDA events bracket the launch on its stream.
 template <typename F>
-cudaError_t plaunch(gp_handle h, int id, cudaStream_t st, F&& f) {
+cudaError_t plaunch(gp_handle h, int id, cudaStream_t st, F&& f, int nlaunch = 0) {
   Profiler& P = h->prof;
   const bool rec = P.on && !h->capturing;
   cudaEvent_t a = nullptr, b = nullptr;
@@ -162,7 +162,7 @@ cudaError_t plaunch(gp_handle h, int id, cudaStream_t st, F&& f) {
     P.recs.push_back({id, a, b});
     P.resolved = false;
   }
-  if (P.on) P.launches[id] += kProfLaunches[id];
+  if (P.on) P.launches[id] += nlaunch > 0 ? nlaunch : kProfLaunches[id];
   return e;
 }
 
@@ -248,9 +248,9 @@ gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double
 }
 
 // g2 (two planes) = forward-difference gradient of x = scale (alpha - Lap)^{-1} b
-// and, when want_phi, phi = x.  Fast sizes take the gradient in the spectral
-// domain; other sizes difference the dense solve's output (phi is then always
-// written).  tmp holds 2 N^2.
+// and, when want_phi, phi = x.  Fast sizes (and the split-precision tensor-core
+// mode) take the gradient in the spectral domain; other sizes difference the
+// dense solve's output (phi is then always written).  tmp holds 2 N^2.
 gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, bool want_phi, float* tmp,
                      double alpha, double scale, int prec, cudaStream_t st) {
   const DctPlan* p = nullptr;
@@ -267,6 +267,21 @@ gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, 
     GP_CUDA(h, plaunch(h, PK_DCT_COLS_GRAD, st, [&] { return dct_grad_cols(*p, A, A, B, a, sc, st); }));
     GP_CUDA(h, plaunch(h, PK_DCT_ROWS_GRAD, st,
                        [&] { return dct_grad_rows(*p, A, B, g2, g2 + NN, want_phi ? phi : nullptr, st); }));
+    return GP_OK;
+  }
+  if (prec == GP_PREC_SPLIT_BF16 && tc_solve_supported(N)) {
+    // tensor-core GEMMs with the gradient synthesised from the spectrum
+    DctPlan* pm = &h->plans[N];
+    GP_CUDA(h, dct_plan_dense(*pm));
+    GP_CUDA(h, dct_plan_grad_dense(*pm));
+    if (!h->tc_err) {
+      GP_CUDA(h, cudaMalloc(&h->tc_err, sizeof(int)));
+      GP_CUDA(h, cudaMemset(h->tc_err, 0, sizeof(int)));
+    }
+    GP_CUDA(h, plaunch(
+                   h, PK_DCT_TC, st,
+                   [&] { return dct_grad_tc(*pm, b, g2, g2 + NN, want_phi ? phi : nullptr, tmp, a, sc, h->tc_err, st); },
+                   want_phi ? 8 : 7));
     return GP_OK;
   }
   if ((s = solve(h, N, b, phi, tmp, alpha, scale, prec, false, st)) != GP_OK) return s;

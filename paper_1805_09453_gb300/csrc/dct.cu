@@ -956,12 +956,42 @@ cudaError_t dct_plan_dense(DctPlan& p) {
   return cudaSuccess;
 }
 
+// E[k][j] = N (C[k][j+1] - C[k][j]) = -2N s_k sin(pi k (j+1) / N) sin(pi k / 2N)
+// (product form: no cancellation), j < N-1; the last column is the zero slot.
+cudaError_t dct_plan_grad_dense(DctPlan& p) {
+  if (p.E && p.ET) return cudaSuccess;
+  const int N = p.N;
+  const double PI = 3.14159265358979323846;
+  std::vector<float> E((size_t)N * N), ET((size_t)N * N);
+  for (int k = 0; k < N; ++k) {
+    const double s = (k == 0) ? sqrt(1.0 / N) : sqrt(2.0 / N);
+    const double sh = sin(PI * k / (2.0 * N));
+    for (int j = 0; j < N; ++j) {
+      const float v = j == N - 1 ? 0.f : (float)(-2.0 * N * s * sin(PI * k * (j + 1.0) / N) * sh);
+      E[(size_t)k * N + j] = v;
+      ET[(size_t)j * N + k] = v;
+    }
+  }
+  cudaError_t e;
+  if (!p.E) {
+    if ((e = cudaMalloc(&p.E, sizeof(float) * (size_t)N * N))) return e;
+    if ((e = cudaMemcpy(p.E, E.data(), sizeof(float) * (size_t)N * N, cudaMemcpyHostToDevice))) return e;
+  }
+  if (!p.ET) {
+    if ((e = cudaMalloc(&p.ET, sizeof(float) * (size_t)N * N))) return e;
+    if ((e = cudaMemcpy(p.ET, ET.data(), sizeof(float) * (size_t)N * N, cudaMemcpyHostToDevice))) return e;
+  }
+  return cudaSuccess;
+}
+
 void dct_plan_free(DctPlan& p) {
   if (p.tw) cudaFree(p.tw);
   if (p.wq) cudaFree(p.wq);
   if (p.mu) cudaFree(p.mu);
   if (p.C) cudaFree(p.C);
   if (p.CT) cudaFree(p.CT);
+  if (p.E) cudaFree(p.E);
+  if (p.ET) cudaFree(p.ET);
   p = DctPlan();
 }
 

@@ -37,6 +37,8 @@ struct DctPlan {
   float* mu = nullptr;       // (4/h^2) sin^2(pi k / 2N), k < N
   float* C = nullptr;        // orthonormal DCT-II matrix, N x N   (dense)
   float* CT = nullptr;       // its transpose (tensor-core path)
+  float* E = nullptr;        // derivative synthesis C D^T: E[k][j] = N (C[k][j+1] - C[k][j]), 0 at j = N-1
+  float* ET = nullptr;       // its transpose
 };
 
 // Launchers (dct.cu)
@@ -65,6 +67,12 @@ cudaError_t dct_plan_dense(DctPlan& p);
 bool tc_solve_supported(int N);
 cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
                          cudaStream_t st);
+// Gradient of the split-precision solve, taken in the spectral domain with
+// tensor-core GEMMs (7, or 8 with phi): gx = C^T Q E, gy = E^T Q C with
+// Q = gain .* (C b C^T).  tmp holds 2*N*N floats; gy doubles as scratch.
+cudaError_t dct_plan_grad_dense(DctPlan& p);
+cudaError_t dct_grad_tc(const DctPlan& p, const float* b, float* gx, float* gy, float* phi, float* tmp, float alpha,
+                        float scale, int* err, cudaStream_t st);
 // Dense-matrix form (any N): tmp must hold 2*N*N floats.
 cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp,
                                  float alpha, float scale, cudaStream_t st);

@@ -268,4 +268,28 @@ cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp,
   return gemm<true>(t0, p.CT, x, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st);                // x = T3 C
 }
 
+// Spectral gradient in the split-precision mode (the forward differences of
+// the solution synthesised from its spectrum, as the FP32 path does, so that
+// the solve's error is not amplified by 1/h):
+//   t0 = C b^T,  Q = gain .* (C t0^T) (and Q^T),  U = C^T Q,
+//   gx = U E,  phi = U C (optional),  V^T = (Q C)^T,  gy = E^T V.
+// Buffers: X = tmp, Z = tmp + N^2, Q lives in gy until the last product.
+cudaError_t dct_grad_tc(const DctPlan& p, const float* b, float* gx, float* gy, float* phi, float* tmp, float alpha,
+                        float scale, int* err, cudaStream_t st) {
+  const int N = p.N;
+  if (!p.C || !p.CT || !p.E || !p.ET || !tc_solve_supported(N)) return cudaErrorInvalidValue;
+  float* X = tmp;
+  float* Z = tmp + (size_t)N * N;
+  float* Q = gy;
+  cudaError_t e;
+  if ((e = gemm<true>(b, p.C, X, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;   // X = C b^T
+  if ((e = gemm<true>(p.C, X, Q, N, 0, p.mu, alpha, scale, 1.f, 1.f, err, st))) return e;      // Q
+  if ((e = gemm<true>(p.C, X, Z, N, 1, p.mu, alpha, scale, 1.f, 1.f, err, st))) return e;      // Z = Q^T
+  if ((e = gemm<true>(p.CT, Z, X, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;  // X = U = C^T Q
+  if ((e = gemm<true>(X, p.ET, gx, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e; // gx = U E
+  if (phi && (e = gemm<true>(X, p.CT, phi, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;  // phi = U C
+  if ((e = gemm<true>(Q, p.CT, Z, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;  // Z = (Q C)^T
+  return gemm<true>(p.ET, Z, gy, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st);              // gy = E^T V
+}
+
 }  // namespace gp
