@@ -95,6 +95,7 @@ struct gp_state_s {
   const float* f1 = nullptr;
   float* prim = nullptr;  // ROF: u (N^2); EMD: grad q (2 N^2), also grad phi at gap checks
   float* gu = nullptr;    // ROF: grad u (2 N^2)
+  float* Ic = nullptr;    // ROF: the state's own copy of I (captured graphs never see the caller's pointer)
   float* r = nullptr;     // ROF: next right-hand side; EMD: d = g - div s (= tau div pbar)
   float* p[2] = {nullptr, nullptr};
   float* s[2] = {nullptr, nullptr};  // EMD only
@@ -341,6 +342,7 @@ gp_status alloc_state(gp_handle h, int kind, int N, gp_state* out) {
   if (!e) e = A(&s->p[1], 2 * NN);
   if (!e) e = A(&s->tmp, 2 * NN);
   if (kind == KIND_ROF && !e) e = A(&s->gu, 2 * NN);
+  if (kind == KIND_ROF && !e) e = A(&s->Ic, NN);
   if (kind == KIND_EMD) {
     if (!e) e = A(&s->s[0], 2 * NN);
     if (!e) e = A(&s->s[1], 2 * NN);
@@ -379,16 +381,19 @@ gp_status rof_setup(gp_state s, const float* I, double lam, double tau, double s
   gp_handle h = s->h;
   const int N = s->N;
   const size_t NN = (size_t)N * N;
-  if (s->I != I || s->lam != lam || s->tau != tau || s->sigma != sigma) drop_graphs(s);
+  if (s->lam != lam || s->tau != tau || s->sigma != sigma) drop_graphs(s);
   s->I = I;
+  GP_CUDA(h, cudaMemcpyAsync(s->Ic, I, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
   s->lam = lam;
   s->tau = tau;
   s->sigma = sigma;
   s->n = 0;
   s->cur = 0;
   s->partials_valid = false;
-  s->vec = (N % 4 == 0) && aligned16(I);
-  s->rb = tuned_rb(h, "rof_fused", N);
+  s->vec = N % 4 == 0;  // all fused-kernel operands are state buffers
+  const int rb = tuned_rb(h, "rof_fused", N);
+  if (rb != s->rb) drop_graphs(s);  // the graphs hold the previous tile shape
+  s->rb = rb;
   if (u0) GP_CUDA(h, cudaMemcpyAsync(s->prim, u0, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
   else GP_CUDA(h, cudaMemsetAsync(s->prim, 0, NN * sizeof(float), st));
   if (p0) GP_CUDA(h, cudaMemcpyAsync(s->p[0], p0, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -416,7 +421,7 @@ gp_status rof_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
     float* pin = s->p[s->cur];
     float* pout = s->p[1 - s->cur];
     GP_CUDA(h, plaunch(h, PK_ROF_FUSED, st, [&] {
-              return launch_rof_fused(s->gu, s->prim, pin, s->I, pout, s->r, s->part, P, s->vec, g, s->rb, st);
+              return launch_rof_fused(s->gu, s->prim, pin, s->Ic, pout, s->r, s->part, P, s->vec, g, s->rb, st);
             }));
     s->cur = 1 - s->cur;
     s->n++;
@@ -501,7 +506,9 @@ gp_status emd_setup(gp_state s, const float* f0, const float* f1, double tau, do
   gp_handle h = s->h;
   const int N = s->N;
   const size_t NN = (size_t)N * N;
-  if (s->f0 != f0 || s->f1 != f1 || s->tau != tau || s->sigma != sigma) drop_graphs(s);
+  // the captured step graphs read only state buffers (g = f0 - f1 is formed here), so new
+  // input pointers need no recapture; the step sizes are kernel arguments
+  if (s->tau != tau || s->sigma != sigma) drop_graphs(s);
   s->f0 = f0;
   s->f1 = f1;
   s->tau = tau;
@@ -510,7 +517,9 @@ gp_status emd_setup(gp_state s, const float* f0, const float* f1, double tau, do
   s->cur = 0;
   s->partials_valid = false;
   s->vec = N % 4 == 0;  // all fused-kernel operands are state buffers
-  s->rb = tuned_rb(h, "emd_fused", N);
+  const int rb = tuned_rb(h, "emd_fused", N);
+  if (rb != s->rb) drop_graphs(s);  // the graphs hold the previous tile shape
+  s->rb = rb;
   GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_sub(f0, f1, s->g, NN, st); }));
   if (m0) {
     GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_copy_field(m0, s->m, N, st); }));
@@ -553,7 +562,7 @@ gp_status state_gap_enqueue(gp_state s, double* dst, int prec, cudaStream_t st) 
   if (s->kind == KIND_ROF) {
     if (!fused)
       GP_CUDA(h, plaunch(h, PK_REDUCE, st,
-                         [&] { return launch_rof_gap(s->prim, s->p[s->cur], s->I, N, s->part, nb, st); }));
+                         [&] { return launch_rof_gap(s->prim, s->p[s->cur], s->Ic, N, s->part, nb, st); }));
     GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 4, 0u, dst, st); }));
     return GP_OK;
   }
