@@ -8,13 +8,15 @@
 //     A B^T ~= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
 // is accumulated in FP32 in tensor memory (the dropped A_lo B_lo^T term is
 // ~2^-16 relative; BF16 keeps FP32's exponent range, so no operand scaling
-// is needed).  One CTA computes a 128 x 128 tile: all 128 threads load
-// and split a 128 x 64 slab of each operand into shared memory (canonical
-// K-major layout without swizzle), one thread issues the tcgen05.mma
-// instructions, tcgen05.commit signals an mbarrier when they have read shared
-// memory and written the accumulator, and the epilogue moves the accumulator
-// out of tensor memory with tcgen05.ld (thread = tile row), applies the
-// spectral gain when asked, and stores the tile, transposed when asked, so
+// is needed).  One CTA (256 threads) computes a 128 x 128 tile.  Its K loop
+// is a two-stage pipeline: all threads load and split the next 128 x 64 slab
+// of each operand into one shared-memory stage (canonical K-major layout
+// without swizzle) while the tensor core multiplies the other; one thread
+// issues the tcgen05.mma instructions, and tcgen05.commit signals the stage's
+// mbarrier when they have read it.  The epilogue moves the accumulator out of
+// tensor memory with tcgen05.ld (a warp reads its lane quadrant, two warps
+// share the columns), applies the spectral gain when asked, and stores the
+// tile, transposed when asked, so
 // that every operand of the next GEMM is again K-major:
 //     G1: T1^T <- (b C^T)^T      G2: T2^T <- (gain .* (C T1))^T
 //     G3: T3   <- C^T T2         G4: x    <- T3 C
@@ -31,7 +33,9 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int TILE_BYTES = BM * BK * 2;  // one 16-bit operand slab, 16 KiB
-constexpr int SMEM_BYTES = 4 * TILE_BYTES + 64;
+constexpr int STAGES = 2;                // shared-memory stages (a_hi, a_lo, b_hi, b_lo each)
+constexpr int THREADS = 256;
+constexpr int SMEM_BYTES = STAGES * 4 * TILE_BYTES + 64;
 constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -105,8 +109,9 @@ __device__ __forceinline__ void split4(float4 v, uint2& hi, uint2& lo) {
 template <bool BF16>
 __device__ __forceinline__ void load_split(const float* __restrict__ src, int ld, int r0, int k0, float s,
                                            uint8_t* hi, uint8_t* lo) {
-  // 128 rows x 16 float4 = 2048 float4; 16 per thread, 16 consecutive threads per row
-  for (int idx = threadIdx.x; idx < BM * (BK / 4); idx += blockDim.x) {
+  // 128 rows x 16 float4 = 2048 float4, 16 consecutive threads per row
+#pragma unroll 4
+  for (int idx = threadIdx.x; idx < BM * (BK / 4); idx += THREADS) {
     const int row = idx >> 4, q = idx & 15;
     float4 v = *reinterpret_cast<const float4*>(src + (size_t)(r0 + row) * ld + k0 + 4 * q);
     v.x *= s;
@@ -126,20 +131,15 @@ __device__ __forceinline__ void load_split(const float* __restrict__ src, int ld
 // gain (mu != nullptr): D[m][n] *= gscale / (alpha + mu[m] + mu[n]), 0 when
 // the denominator is 0.  Operand scales sa, sb are undone in the epilogue.
 template <bool BF16>
-__global__ void __launch_bounds__(128) k_tc_gemm_split(const float* __restrict__ A, const float* __restrict__ B,
-                                                       float* __restrict__ D, int Nn, int K, int mode,
-                                                       const float* __restrict__ mu, float alpha, float gscale,
-                                                       float sa, float sb, int* __restrict__ err) {
+__global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restrict__ A, const float* __restrict__ B,
+                                                           float* __restrict__ D, int Nn, int K, int mode,
+                                                           const float* __restrict__ mu, float alpha, float gscale,
+                                                           float sa, float sb, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* a_hi = smem;
-  uint8_t* a_lo = smem + TILE_BYTES;
-  uint8_t* b_hi = smem + 2 * TILE_BYTES;
-  uint8_t* b_lo = smem + 3 * TILE_BYTES;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 4 * TILE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 4 * TILE_BYTES + 16);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * 4 * TILE_BYTES);  // one mbarrier per stage
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + STAGES * 4 * TILE_BYTES + 32);
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t bar_addr = smem_u32(bar);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm_split(const float* __restrict__
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_addr), "r"(1));
+    for (int st = 0; st < STAGES; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + st)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -156,12 +157,21 @@ __global__ void __launch_bounds__(128) k_tc_gemm_split(const float* __restrict__
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = instr_desc<BF16>();
   bool ok = true;
-  uint32_t phase = 0;
+  uint32_t phase[STAGES] = {0u, 0u};  // parity of the next completion of each stage's mbarrier
+  int last = -1;                      // stage of the last committed tile
   const int nk = K / BK;
+  // Two-stage pipeline: while the tensor core multiplies tile kt (stage kt % 2),
+  // all threads load and split tile kt + 1 into the other stage.  A stage is
+  // refilled only after the commit of the tile that used it (kt - 2) arrived.
   for (int kt = 0; kt < nk; ++kt) {
-    if (kt > 0) {  // the previous MMAs must have read the slabs before they are overwritten
-      if (!mbar_wait(bar_addr, phase, kWaitLimit)) ok = false;
-      phase ^= 1u;
+    const int st = kt & 1;
+    uint8_t* a_hi = smem + st * 4 * TILE_BYTES;
+    uint8_t* a_lo = a_hi + TILE_BYTES;
+    uint8_t* b_hi = a_hi + 2 * TILE_BYTES;
+    uint8_t* b_lo = a_hi + 3 * TILE_BYTES;
+    if (kt >= STAGES) {
+      if (!mbar_wait(smem_u32(bar + st), phase[st], kWaitLimit)) ok = false;
+      phase[st] ^= 1u;
     }
     if (!__syncthreads_and(ok)) {
       ok = false;
@@ -181,27 +191,31 @@ __global__ void __launch_bounds__(128) k_tc_gemm_split(const float* __restrict__
         mma_f16(tmem, smem_desc(ah + off), smem_desc(bl + off), idesc, 1u);
         mma_f16(tmem, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_addr)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(bar + st))
                    : "memory");
     }
+    last = st;
   }
-  if (ok && nk > 0) {
-    if (!mbar_wait(bar_addr, phase, kWaitLimit)) ok = false;
+  // the last commit arrives when every MMA issued before it has completed
+  if (ok && last >= 0) {
+    if (!mbar_wait(smem_u32(bar + last), phase[last], kWaitLimit)) ok = false;
   }
   if (!__syncthreads_and(ok)) {
     if (threadIdx.x == 0) atomicExch(err, 1);
     // let the tensor core finish (bounded) before the memory is released
-    mbar_wait(bar_addr, phase, kWaitLimit);
+    if (last >= 0) mbar_wait(smem_u32(bar + last), phase[last], kWaitLimit);
     __syncthreads();
   } else {
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const int m = m0 + warp * 32 + lane;  // this thread's accumulator row
+    const int quad = warp & 3;            // a warp reads the tensor-memory lanes of its quadrant
+    const int m = m0 + quad * 32 + lane;  // this thread's accumulator row
     const float inv = 1.f / (sa * sb);
     const float mum = mu ? __ldg(&mu[m]) : 0.f;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
+    for (int c0 = (warp >> 2) * (BN / 2); c0 < (warp >> 2) * (BN / 2) + BN / 2; c0 += 32) {
       uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
           "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
@@ -247,7 +261,7 @@ cudaError_t gemm(const float* A, const float* B, float* D, int N, int mode, cons
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_split<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
   dim3 grid(N / BN, N / BM);
-  k_tc_gemm_split<BF16><<<grid, 128, SMEM_BYTES, st>>>(A, B, D, N, N, mode, mu, alpha, gscale, sa, sb, err);
+  k_tc_gemm_split<BF16><<<grid, THREADS, SMEM_BYTES, st>>>(A, B, D, N, N, mode, mu, alpha, gscale, sa, sb, err);
   return cudaGetLastError();
 }
 
