@@ -397,7 +397,7 @@ def run_ours(args):
             ttg["rof"] = {"seconds": time.perf_counter() - t0, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
                           "status": rep["status_name"], "tau": rep["tau"]}
             if N % 64 == 0:
-                # warm-started form: the EMD solved 8x coarser to gap 1e-6, interpolated, as the start
+                # warm-started form: the EMD solved 4x coarser to gap 1e-6, interpolated, as the start
                 # (emd_solve_learned with a network whose output is its prior; the duality gap at
                 # n = 0 picks between that start and zero)
                 base = gprox.Cnn(h, 1, seed=0)
@@ -405,11 +405,11 @@ def run_ours(args):
                 oc = gprox.default_opts(max_iters=200000, tol_rel_gap=1e-6, gap_every=50, use_graph=1)
                 stream.synchronize()
                 t0 = time.perf_counter()
-                st, rep = gprox.emd_solve_learned(h, base, f0d, f1d, m, None, None, o, 8, oc)
+                st, rep = gprox.emd_solve_learned(h, base, f0d, f1d, m, None, None, o, 4, oc)
                 sec = time.perf_counter() - t0
                 ttg["emd_coarse_start"] = {"seconds": sec, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
                                            "status": rep["status_name"], "start": rep["start"],
-                                           "mass_residual": rep["mass_residual"], "coarse_factor": 8,
+                                           "mass_residual": rep["mass_residual"], "coarse_factor": 4,
                                            "coarse_tol": 1e-6, "speedup": ttg["emd"]["seconds"] / sec}
                 base.close()
 

@@ -370,9 +370,13 @@ std::string tune_key(gp_handle h, const char* kernel, int N) {
   return std::string(kernel) + "/N=" + std::to_string(N) + "/sm=" + std::to_string(maj * 10 + mnr);
 }
 
+// Row-block height of the fused kernels: the autotuned one, else a default
+// that keeps small grids from running a few long per-thread row chains (at
+// 1024^2, 16-row blocks give 128 CTAs of 128 threads: latency-bound).
 int tuned_rb(gp_handle h, const char* kernel, int N) {
   auto it = h->tune.find(tune_key(h, kernel, N));
-  return it == h->tune.end() ? 16 : it->second;
+  if (it != h->tune.end()) return it->second;
+  return N <= 1024 ? 4 : (N <= 2048 ? 8 : 16);
 }
 
 // --------------------------------------------------------------- ROF state

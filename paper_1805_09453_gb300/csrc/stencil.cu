@@ -574,7 +574,7 @@ dim3 fused_grid(int N, int V, int rb) { return dim3(ceil_div(ceil_div(N, V), 128
 cudaError_t launch_rof_fused(const float* gu, const float* u, const float* pin, const float* I, float* pout, float* r,
                              double* part, const RofParams& P, bool vec, bool gap, int rb, cudaStream_t st) {
   const int V = vec ? 4 : 1;
-  dim3 g = fused_grid(P.N, V, rb);
+  dim3 g = fused_grid(P.N, V, vec ? rb : kRBDefault);  // the scalar kernel walks kRBDefault rows per block
   if (vec) {
 #define GP_L(R)                                                                                  \
   if (gap) k_rof_fused<4, R, true><<<g, 128, 0, st>>>(gu, u, pin, I, pout, r, part, P);           \
@@ -592,7 +592,7 @@ cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pi
                              float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
                              bool gap, int rb, cudaStream_t st) {
   const int V = vec ? 4 : 1;
-  dim3 gr = fused_grid(P.N, V, rb);
+  dim3 gr = fused_grid(P.N, V, vec ? rb : kRBDefault);  // the scalar kernel walks kRBDefault rows per block
   if (vec) {
 #define GP_L(R)                                                                                            \
   if (gap) k_emd_fused<4, R, true><<<gr, 128, 0, st>>>(gq, sin_, pin, g, sout, pout, d, m, e, part, P);     \
