@@ -132,9 +132,16 @@ __device__ __forceinline__ void stage_twiddles(const float2* __restrict__ tw, in
 // NB and Ns multiples of 16, padi(a + r*S) = padi(a) + r*(S + S/16); for the
 // first stage (Ns = 1) the store index is 16j + r, whose padded form is
 // padi(16j) + r.
+// Barrier of a transform's threads: the whole CTA (bar == 0) or named barrier
+// `bar` shared by the NT threads of one transform group (NT a multiple of 32).
+__device__ __forceinline__ void gsync(int bar, int nt) {
+  if (bar == 0) __syncthreads();
+  else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(nt) : "memory");
+}
+
 template <int N, int R, int DIR, int TPF>
 __device__ __forceinline__ void fft_stage(float2* buf, const int Ns, const int t,
-                                          const float2* __restrict__ tw) {
+                                          const float2* __restrict__ tw, int bar = 0) {
   constexpr int NB = N / R;
   constexpr int BPT = NB / TPF;
   static_assert(BPT >= 1 && NB % TPF == 0, "threads per transform must divide N/R");
@@ -152,7 +159,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const int Ns, const int t
       for (int r = 0; r < R; ++r) v[b][r] = buf[padi(j + r * NB)];
     }
   }
-  __syncthreads();
+  gsync(bar, TPF);
 #pragma unroll
   for (int b = 0; b < BPT; ++b) {
     const int j = t + b * TPF;
@@ -179,7 +186,7 @@ __device__ __forceinline__ void fft_stage(float2* buf, const int Ns, const int t
       for (int r = 0; r < R; ++r) buf[padi(base + r * Ns)] = v[b][r];
     }
   }
-  __syncthreads();
+  gsync(bar, TPF);
 }
 
 // Length-2^LOG2N complex FFT in shared memory (unnormalised), natural order.
@@ -224,13 +231,14 @@ struct StageTw {
 // fft_smem with the base twiddles of the radix-16 stages 1 .. S16-1 supplied
 // by get(s, q) (q = 0..3: w1, w2, w4, w8 of stage s); TPF = N/16.
 template <int LOG2N, int DIR, int TPF, typename GetTw>
-__device__ __forceinline__ void fft_smem_tw_impl(float2* buf, int t, const float2* __restrict__ tw, GetTw get) {
+__device__ __forceinline__ void fft_smem_tw_impl(float2* buf, int t, const float2* __restrict__ tw, GetTw get,
+                                                 int bar) {
   constexpr int N = 1 << LOG2N;
   constexpr int S16 = LOG2N / 4;
   constexpr int REM = 1 << (LOG2N % 4);
   constexpr int NB = N / 16;
   static_assert(TPF == NB, "stored twiddles need one radix-16 butterfly per thread");
-  fft_stage<N, 16, DIR, TPF>(buf, 1, t, tw);  // stage 0: no twiddles
+  fft_stage<N, 16, DIR, TPF>(buf, 1, t, tw, bar);  // stage 0: no twiddles
   int Ns = 16;
 #pragma unroll
   for (int s = 1; s < S16; ++s) {
@@ -238,7 +246,7 @@ __device__ __forceinline__ void fft_smem_tw_impl(float2* buf, int t, const float
     const float2* src = buf + padi(t);
 #pragma unroll
     for (int r = 0; r < 16; ++r) v[r] = src[r * (NB + NB / 16)];
-    __syncthreads();
+    gsync(bar, TPF);
     const int k = t & (Ns - 1);
     float2 w[16];
     w[0] = make_float2(1.f, 0.f);
@@ -262,25 +270,26 @@ __device__ __forceinline__ void fft_smem_tw_impl(float2* buf, int t, const float
     const int SS = Ns + Ns / 16;
 #pragma unroll
     for (int r = 0; r < 16; ++r) dst[r * SS] = v[r];
-    __syncthreads();
+    gsync(bar, TPF);
     Ns *= 16;
   }
-  if constexpr (REM > 1) fft_stage<N, REM, DIR, TPF>(buf, Ns, t, tw);
+  if constexpr (REM > 1) fft_stage<N, REM, DIR, TPF>(buf, Ns, t, tw, bar);
 }
 
 // ... with the twiddles in registers
 template <int LOG2N, int DIR, int TPF>
 __device__ __forceinline__ void fft_smem_tw(float2* buf, int t, const float2* __restrict__ tw,
-                                            const StageTw<LOG2N>& stw) {
-  fft_smem_tw_impl<LOG2N, DIR, TPF>(buf, t, tw, [&](int s, int q) { return stw.w[s - 1][q]; });
+                                            const StageTw<LOG2N>& stw, int bar = 0) {
+  fft_smem_tw_impl<LOG2N, DIR, TPF>(buf, t, tw, [&](int s, int q) { return stw.w[s - 1][q]; }, bar);
 }
 
 // ... with the twiddles in a shared-memory table twsm[(s - 1) * 4 + q][t]
 // (filled by fill_stage_tw), for kernels without registers to spare.
 template <int LOG2N, int DIR, int TPF>
 __device__ __forceinline__ void fft_smem_tws(float2* buf, int t, const float2* __restrict__ tw,
-                                             const float2* twsm) {
-  fft_smem_tw_impl<LOG2N, DIR, TPF>(buf, t, tw, [&](int s, int q) { return twsm[((s - 1) * 4 + q) * TPF + t]; });
+                                             const float2* twsm, int bar = 0) {
+  fft_smem_tw_impl<LOG2N, DIR, TPF>(buf, t, tw, [&](int s, int q) { return twsm[((s - 1) * 4 + q) * TPF + t]; },
+                                    bar);
 }
 
 template <int LOG2N>
@@ -579,30 +588,38 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
 // syntheses along the column:
 //   A[:, pair] = S_c(X)                      (plain; feeds the x-derivative and phi)
 //   B[:, a]    = D_y S_c(X_a),  B[:, b] = D_y S_c(X_b)
-// `in` may alias A.  Shared memory: transform buffer, gained spectra, D_y of a.
-template <int LOG2N>
-__global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
+// `in` may alias A.  Shared memory: transform buffer(s), gained spectra.
+// PAR (small N, where one CTA's chain of transforms is the latency): three
+// groups of TPF threads run the three syntheses at once in their own
+// buffers, each synchronising on its own named barrier.
+template <int LOG2N, bool PAR>
+__global__ void __launch_bounds__((PAR ? 3 : 1) * FftCfg<LOG2N>::TPF, (LOG2N == 12 && !PAR ? 3 : 1))
     k_dct_cols_grad(const float* __restrict__ in, float* A, float* B, const float2* __restrict__ tw,
                     const float2* __restrict__ wq, const float* __restrict__ mu, float alpha, float sN2) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
   extern __shared__ float2 smem[];
-  float2* buf = smem;
-  float2* X = smem + PADN;  // gained spectra of the two columns, N complex
-  const int cp = blockIdx.x, t = threadIdx.x;
+  const int grp = PAR ? (int)threadIdx.x / TPF : 0, t = (int)threadIdx.x % TPF;
+  float2* buf = smem + grp * PADN;
+  float2* X = smem + (PAR ? 3 : 1) * PADN;  // gained spectra of the two columns, N complex
+  const int cp = blockIdx.x;
   const float fN = (float)N;
   StageTw<LOG2N> stw;
   stw.load(tw, t);
-  load_cols<N, TPF>(buf, in, cp, t);
+  if (grp == 0) {
+    const int bar0 = PAR ? 1 : 0;
+    load_cols<N, TPF>(buf, in, cp, t);
+    gsync(bar0, TPF);
+    fft_smem_tw<LOG2N, -1, TPF>(buf, t, tw, stw, bar0);
+    col_spectrum<N, TPF>(buf, X, cp, t, wq, mu, alpha, sN2);
+  }
   __syncthreads();
-  fft_smem_tw<LOG2N, -1, TPF>(buf, t, tw, stw);
-  col_spectrum<N, TPF>(buf, X, cp, t, wq, mu, alpha, sN2);
-  __syncthreads();
-  for (int pass = 0; pass < 3; ++pass) {
-    #pragma unroll
-  for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
-    if (kk == (N / 2) / TPF && t != 0) break;
-    const int k = t + kk * TPF;
+  const int bar = PAR ? grp + 1 : 0;
+  for (int pass = PAR ? grp : 0; pass < (PAR ? grp + 1 : 3); ++pass) {
+#pragma unroll
+    for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
+      if (kk == (N / 2) / TPF && t != 0) break;
+      const int k = t + kk * TPF;
       const float2 xk = X[k];
       if (pass == 0) {
         if (k == 0) {
@@ -631,16 +648,16 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
         }
       }
     }
-    __syncthreads();
-    fft_smem_tw<LOG2N, +1, TPF>(buf, t, tw, stw);
+    gsync(bar, TPF);
+    fft_smem_tw<LOG2N, +1, TPF>(buf, t, tw, stw, bar);
     if (pass == 0) {
       store_cols<N, TPF>(buf, A, cp, t);
     } else {
       // D_y of column (2cp + pass - 1): one float4 (4 rows) per row block
       const int col = 2 * cp + pass - 1;
-      #pragma unroll
-  for (int ii = 0; ii < (N / 4) / TPF; ++ii) {
-    const int rb = t + ii * TPF;
+#pragma unroll
+      for (int ii = 0; ii < (N / 4) / TPF; ++ii) {
+        const int rb = t + ii * TPF;
         float v[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -651,39 +668,45 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
         *reinterpret_cast<float4*>(B + (size_t)rb * 4 * N + (size_t)col * 4) = make_float4(v[0], v[1], v[2], v[3]);
       }
     }
-    __syncthreads();
+    gsync(bar, TPF);
   }
 }
 
 // ------------------------------------------------------ row pass, gradient
-// CTA = one block of 4 rows (two transforms).  Per transform slot f (rows
+// CTA = one block of 4 rows (two transform slots).  Per slot f (rows
 // r0 = 4 rb + 2f and r0 + 1):
 //   gx[r0] = D_x S_c(A[r0]),  gx[r0+1] = D_x S_c(A[r0+1]),  gy[r0, r0+1] = S_c(B[r0, r0+1]),
 //   and phi[r0, r0+1] = S_c(A[r0, r0+1]) when phi != nullptr.
 // A, B interleaved; gx, gy, phi row-major; gx has its zero slot at j = N-1.
-template <int LOG2N>
-__global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
+// PAR (small N): one group of TPF threads per (slot, pass), all at once, each
+// in its own buffer on its own named barrier; blockDim = 2 npass TPF.
+template <int LOG2N, bool PAR>
+__global__ void __launch_bounds__((PAR ? 8 : 2) * FftCfg<LOG2N>::TPF, (LOG2N == 12 && !PAR ? 2 : 1))
     k_dct_rows_grad(const float* __restrict__ A, const float* __restrict__ B, float* __restrict__ gx,
                     float* __restrict__ gy, float* __restrict__ phi, const float2* __restrict__ tw,
                     const float2* __restrict__ wq) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
   extern __shared__ float2 smem[];
-  const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
-  float2* buf = smem + f * PADN;
-  float2* twsm = smem + 2 * PADN;
-  fill_stage_tw<LOG2N>(twsm, tw, threadIdx.x, 2 * TPF);
+  const int npass = phi ? 4 : 3;
+  const int grp = (int)threadIdx.x / TPF, t = (int)threadIdx.x % TPF;
+  const int f = PAR ? grp / npass : grp;
+  float2* buf = smem + grp * PADN;
+  float2* twsm = smem + (PAR ? 2 * npass : 2) * PADN;
+  fill_stage_tw<LOG2N>(twsm, tw, threadIdx.x, blockDim.x);
+  __syncthreads();
   const int rb = blockIdx.x;
   const int r0 = 4 * rb + 2 * f;
   const float fN = (float)N;
-  const int npass = phi ? 4 : 3;
-  for (int pass = 0; pass < npass; ++pass) {
+  const int bar = PAR ? grp + 1 : 0;
+  const int p0 = PAR ? grp % npass : 0;
+  for (int pass = p0; pass < (PAR ? p0 + 1 : npass); ++pass) {
     // pass 0: D_x of A row r0; 1: D_x of A row r0+1; 2: plain of B rows r0, r0+1; 3: plain of A rows
     const float* __restrict__ src = (pass == 2 ? B : A) + (size_t)rb * 4 * N;
-    #pragma unroll
-  for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
-    if (kk == (N / 2) / TPF && t != 0) break;
-    const int k = t + kk * TPF;
+#pragma unroll
+    for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
+      if (kk == (N / 2) / TPF && t != 0) break;
+      const int k = t + kk * TPF;
       const float2 xk2 = *reinterpret_cast<const float2*>(src + 4 * k + 2 * f);
       if (pass < 2) {
         const float xk = pass == 0 ? xk2.x : xk2.y;
@@ -712,13 +735,13 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
         }
       }
     }
-    __syncthreads();
-    fft_smem_tws<LOG2N, +1, TPF>(buf, t, tw, twsm);
+    gsync(bar, (PAR ? 1 : 2) * TPF);
+    fft_smem_tws<LOG2N, +1, TPF>(buf, t, tw, twsm, bar);
     if (pass < 2) {
       float* __restrict__ o = gx + (size_t)(r0 + pass) * N;
-      #pragma unroll
-  for (int ii = 0; ii < N / (4 * TPF); ++ii) {
-    const int j = 4 * t + ii * 4 * TPF;
+#pragma unroll
+      for (int ii = 0; ii < N / (4 * TPF); ++ii) {
+        const int j = 4 * t + ii * 4 * TPF;
         const int hj = j >> 1;
         const float2 z0 = buf[padi(hj)], z1 = buf[padi(N - 1 - hj)];
         const float2 z2 = buf[padi(hj + 1)], z3 = buf[padi(N - 2 - hj)];
@@ -729,9 +752,9 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
     } else {
       float* __restrict__ oa = (pass == 2 ? gy : phi) + (size_t)r0 * N;
       float* __restrict__ ob = oa + N;
-      #pragma unroll
-  for (int ii = 0; ii < N / (4 * TPF); ++ii) {
-    const int j = 4 * t + ii * 4 * TPF;
+#pragma unroll
+      for (int ii = 0; ii < N / (4 * TPF); ++ii) {
+        const int j = 4 * t + ii * 4 * TPF;
         const int hj = j >> 1;
         const float2 z0 = buf[padi(hj)], z1 = buf[padi(N - 1 - hj)];
         const float2 z2 = buf[padi(hj + 1)], z3 = buf[padi(N - 2 - hj)];
@@ -739,7 +762,7 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
         *reinterpret_cast<float4*>(ob + j) = make_float4(z0.y, z1.y, z2.y, z3.y);
       }
     }
-    __syncthreads();
+    gsync(bar, (PAR ? 1 : 2) * TPF);
   }
 }
 
@@ -774,11 +797,14 @@ cudaError_t launch_grad_cols(const DctPlan& p, const float* in, float* A, float*
                              cudaStream_t st) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
-  const size_t sm = (size_t)PADN * sizeof(float2) + (size_t)N * sizeof(float2);
+  // small N (one CTA's transform chain is the latency): the three syntheses in
+  // parallel groups; named barriers need whole warps per group (TPF >= 32)
+  constexpr bool PAR = LOG2N == 9 || LOG2N == 10;
+  const size_t sm = (size_t)(PAR ? 3 : 1) * PADN * sizeof(float2) + (size_t)N * sizeof(float2);
   cudaError_t e;
-  if ((e = set_smem(k_dct_cols_grad<LOG2N>, sm))) return e;
+  if ((e = set_smem(k_dct_cols_grad<LOG2N, PAR>, sm))) return e;
   const float sN2 = (float)((double)scale / ((double)N * (double)N));
-  k_dct_cols_grad<LOG2N><<<N / 2, TPF, sm, st>>>(in, A, B, p.tw, p.wq, p.mu, alpha, sN2);
+  k_dct_cols_grad<LOG2N, PAR><<<N / 2, (PAR ? 3 : 1) * TPF, sm, st>>>(in, A, B, p.tw, p.wq, p.mu, alpha, sN2);
   return cudaGetLastError();
 }
 
@@ -787,10 +813,12 @@ cudaError_t launch_grad_rows(const DctPlan& p, const float* A, const float* B, f
                              cudaStream_t st) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
-  const size_t sm = (2 * (size_t)PADN + stage_tw_entries<LOG2N>()) * sizeof(float2);
+  constexpr bool PAR = LOG2N == 9 || LOG2N == 10;  // as in the column pass
+  const int groups = PAR ? 2 * (phi ? 4 : 3) : 2;
+  const size_t sm = ((size_t)groups * PADN + stage_tw_entries<LOG2N>()) * sizeof(float2);
   cudaError_t e;
-  if ((e = set_smem(k_dct_rows_grad<LOG2N>, sm))) return e;
-  k_dct_rows_grad<LOG2N><<<N / 4, 2 * TPF, sm, st>>>(A, B, gx, gy, phi, p.tw, p.wq);
+  if ((e = set_smem(k_dct_rows_grad<LOG2N, PAR>, sm))) return e;
+  k_dct_rows_grad<LOG2N, PAR><<<N / 4, groups * TPF, sm, st>>>(A, B, gx, gy, phi, p.tw, p.wq);
   return cudaGetLastError();
 }
 

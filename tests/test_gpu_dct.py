@@ -67,7 +67,7 @@ def test_dct2_poisson_errors(h):
     assert "device pointer" in h.last_error()
 
 
-@pytest.mark.parametrize("N", [7, 16, 33, 64, 128, 1024, 4096])
+@pytest.mark.parametrize("N", [7, 16, 33, 64, 128, 512, 1024, 2048, 4096])
 @pytest.mark.parametrize("alpha", [0.0, 3.7])
 def test_dct2_poisson_grad_matches_oracle(h, N, alpha):
     """Spectral gradient of the solve vs the FP64 oracle's forward differences:
