@@ -229,6 +229,7 @@ gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double
     if (!tc_solve_supported(N)) return fail(h, GP_ERR_UNSUPPORTED, "split-precision solve needs N a multiple of 128");
     DctPlan* pm = &h->plans[N];
     GP_CUDA(h, dct_plan_dense(*pm));
+    GP_CUDA(h, dct_plan_tc_split(*pm, st));
     if (!h->tc_err) {
       GP_CUDA(h, cudaMalloc(&h->tc_err, sizeof(int)));
       GP_CUDA(h, cudaMemset(h->tc_err, 0, sizeof(int)));
@@ -275,6 +276,7 @@ gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, 
     DctPlan* pm = &h->plans[N];
     GP_CUDA(h, dct_plan_dense(*pm));
     GP_CUDA(h, dct_plan_grad_dense(*pm));
+    GP_CUDA(h, dct_plan_tc_split(*pm, st));
     if (!h->tc_err) {
       GP_CUDA(h, cudaMalloc(&h->tc_err, sizeof(int)));
       GP_CUDA(h, cudaMemset(h->tc_err, 0, sizeof(int)));

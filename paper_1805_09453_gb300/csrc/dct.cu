@@ -1020,6 +1020,10 @@ void dct_plan_free(DctPlan& p) {
   if (p.CT) cudaFree(p.CT);
   if (p.E) cudaFree(p.E);
   if (p.ET) cudaFree(p.ET);
+  if (p.Cs) cudaFree(p.Cs);
+  if (p.CTs) cudaFree(p.CTs);
+  if (p.Es) cudaFree(p.Es);
+  if (p.ETs) cudaFree(p.ETs);
   p = DctPlan();
 }
 

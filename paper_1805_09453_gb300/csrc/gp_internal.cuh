@@ -39,6 +39,12 @@ struct DctPlan {
   float* CT = nullptr;       // its transpose (tensor-core path)
   float* E = nullptr;        // derivative synthesis C D^T: E[k][j] = N (C[k][j+1] - C[k][j]), 0 at j = N-1
   float* ET = nullptr;       // its transpose
+  // C, C^T, E, E^T split into hi / lo BF16 in the tensor-core tile layout
+  // (128 x 64 tiles, hi slab then lo slab, 32 KiB per tile; 4 N^2 bytes each)
+  void* Cs = nullptr;
+  void* CTs = nullptr;
+  void* Es = nullptr;
+  void* ETs = nullptr;
 };
 
 // Launchers (dct.cu)
@@ -71,6 +77,8 @@ cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp,
 // tensor-core GEMMs (7, or 8 with phi): gx = C^T Q E, gy = E^T Q C with
 // Q = gain .* (C b C^T).  tmp holds 2*N*N floats; gy doubles as scratch.
 cudaError_t dct_plan_grad_dense(DctPlan& p);
+// Pre-split tile copies of the dense matrices the plan has (tensor-core path).
+cudaError_t dct_plan_tc_split(DctPlan& p, cudaStream_t st);
 cudaError_t dct_grad_tc(const DctPlan& p, const float* b, float* gx, float* gy, float* phi, float* tmp, float alpha,
                         float scale, int* err, cudaStream_t st);
 // Dense-matrix form (any N): tmp must hold 2*N*N floats.

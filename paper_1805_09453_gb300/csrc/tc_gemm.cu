@@ -26,6 +26,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "gp_internal.cuh"
 
 namespace gp {
@@ -35,7 +37,7 @@ constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int TILE_BYTES = BM * BK * 2;  // one 16-bit operand slab, 16 KiB
 constexpr int STAGES = 2;                // shared-memory stages (a_hi, a_lo, b_hi, b_lo each)
 constexpr int THREADS = 256;
-constexpr int SMEM_BYTES = STAGES * 4 * TILE_BYTES + 64;
+constexpr int SMEM_BYTES = STAGES * 4 * TILE_BYTES + 128;  // stages, 2 x STAGES mbarriers, TMEM slot
 constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -126,18 +128,56 @@ __device__ __forceinline__ void load_split(const float* __restrict__ src, int ld
   }
 }
 
+// One tile (hi slab then lo slab, 2 x TILE_BYTES) of a pre-split operand into
+// shared memory by the bulk-copy engine; the mbarrier counts the bytes.
+__device__ __forceinline__ void bulk_tile(uint32_t dst, const void* src, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)(2 * TILE_BYTES))
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"((uint32_t)(2 * TILE_BYTES)), "r"(bar)
+               : "memory");
+}
+
+// Byte offset of tile (row block rb, K block kb) of an N x N operand in the
+// pre-split layout: 128 x 64 tiles, row blocks outermost, hi then lo slab.
+__host__ __device__ __forceinline__ size_t split_tile_offset(int rb, int kb, int N) {
+  return ((size_t)rb * (size_t)(N / BK) + (size_t)kb) * (size_t)(2 * TILE_BYTES);
+}
+
+// M (N x N, row-major FP32) -> pre-split tiles.  One thread per 4 consecutive
+// elements of a row.
+__global__ void k_split_tiles(const float* __restrict__ M, uint8_t* __restrict__ out, int N) {
+  const long n4 = (long)N * N / 4;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / (N / 4)), k = (int)(i % (N / 4)) * 4;
+    const float4 v = *reinterpret_cast<const float4*>(M + (size_t)r * N + k);
+    uint2 h, l;
+    split4<true>(v, h, l);
+    uint8_t* tile = out + split_tile_offset(r / BM, k / BK, N);
+    const uint32_t off = kmajor_offset(r % BM, k % BK);
+    *reinterpret_cast<uint2*>(tile + off) = h;
+    *reinterpret_cast<uint2*>(tile + TILE_BYTES + off) = l;
+  }
+}
+
 // D(m0.., n0..) = epi( A(m0.., :) B(n0.., :)^T ), A: M x K, B: Nc x K, both
 // row-major (K-major) FP32.  mode 0: D[m][n] stored; 1: D^T stored (D[n][m]).
 // gain (mu != nullptr): D[m][n] *= gscale / (alpha + mu[m] + mu[n]), 0 when
 // the denominator is 0.  Operand scales sa, sb are undone in the epilogue.
-template <bool BF16>
+// PRE = 1 (2): A (B) comes pre-split (k_split_tiles layout, pointer As / Bs)
+// and is copied by the bulk-copy engine; the other operand is loaded and
+// split by the threads.  PRE = 0: both split on the fly.
+template <bool BF16, int PRE>
 __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restrict__ A, const float* __restrict__ B,
-                                                           float* __restrict__ D, int Nn, int K, int mode,
-                                                           const float* __restrict__ mu, float alpha, float gscale,
-                                                           float sa, float sb, int* __restrict__ err) {
+                                                           const uint8_t* __restrict__ As,
+                                                           const uint8_t* __restrict__ Bs, float* __restrict__ D,
+                                                           int Nn, int K, int mode, const float* __restrict__ mu,
+                                                           float alpha, float gscale, float sa, float sb,
+                                                           int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * 4 * TILE_BYTES);  // one mbarrier per stage
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + STAGES * 4 * TILE_BYTES + 32);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * 4 * TILE_BYTES);  // per stage: MMAs done
+  uint64_t* full = bar + STAGES;                                                 // per stage: bulk copy landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + STAGES * 4 * TILE_BYTES + 64);
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -147,7 +187,7 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    for (int st = 0; st < STAGES; ++st)
+    for (int st = 0; st < 2 * STAGES; ++st)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + st)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -157,7 +197,8 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = instr_desc<BF16>();
   bool ok = true;
-  uint32_t phase[STAGES] = {0u, 0u};  // parity of the next completion of each stage's mbarrier
+  uint32_t phase[STAGES] = {0u, 0u};   // parity of the next completion of each stage's mbarrier
+  uint32_t fphase[STAGES] = {0u, 0u};  // same for the bulk-copy mbarriers
   int last = -1;                      // stage of the last committed tile
   const int nk = K / BK;
   // Two-stage pipeline: while the tensor core multiplies tile kt (stage kt % 2),
@@ -177,10 +218,21 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
       ok = false;
       break;
     }
-    load_split<BF16>(A, K, m0, kt * BK, sa, a_hi, a_lo);
-    load_split<BF16>(B, K, n0, kt * BK, sb, b_hi, b_lo);
+    if (PRE != 0 && threadIdx.x == 0) {  // the pre-split operand: one bulk copy (hi and lo slabs)
+      if (PRE == 1) bulk_tile(smem_u32(a_hi), As + split_tile_offset(m0 / BM, kt, K), smem_u32(full + st));
+      else bulk_tile(smem_u32(b_hi), Bs + split_tile_offset(n0 / BN, kt, K), smem_u32(full + st));
+    }
+    if (PRE != 1) load_split<BF16>(A, K, m0, kt * BK, sa, a_hi, a_lo);
+    if (PRE != 2) load_split<BF16>(B, K, n0, kt * BK, sb, b_hi, b_lo);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    if (PRE != 0 && threadIdx.x == 0) {
+      if (!mbar_wait(smem_u32(full + st), fphase[st], kWaitLimit)) ok = false;
+      fphase[st] ^= 1u;
+    }
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
     if (threadIdx.x == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
@@ -255,19 +307,47 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
   }
 }
 
-template <bool BF16>
-cudaError_t gemm(const float* A, const float* B, float* D, int N, int mode, const float* mu, float alpha,
-                 float gscale, float sa, float sb, int* err, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_split<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+template <bool BF16, int PRE>
+cudaError_t gemm_launch(const float* A, const float* B, const void* As, const void* Bs, float* D, int N, int mode,
+                        const float* mu, float alpha, float gscale, float sa, float sb, int* err, cudaStream_t st) {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_tc_gemm_split<BF16, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
   dim3 grid(N / BN, N / BM);
-  k_tc_gemm_split<BF16><<<grid, THREADS, SMEM_BYTES, st>>>(A, B, D, N, N, mode, mu, alpha, gscale, sa, sb, err);
+  k_tc_gemm_split<BF16, PRE><<<grid, THREADS, SMEM_BYTES, st>>>(A, B, (const uint8_t*)As, (const uint8_t*)Bs, D, N,
+                                                                 N, mode, mu, alpha, gscale, sa, sb, err);
   return cudaGetLastError();
+}
+
+// D = epi(A B^T); As / Bs (may be null): the same operand pre-split (at most one).
+template <bool BF16>
+cudaError_t gemm(const float* A, const float* B, float* D, int N, int mode, const float* mu, float alpha,
+                 float gscale, float sa, float sb, int* err, cudaStream_t st, const void* As = nullptr,
+                 const void* Bs = nullptr) {
+  if (As) return gemm_launch<BF16, 1>(A, B, As, nullptr, D, N, mode, mu, alpha, gscale, sa, sb, err, st);
+  if (Bs) return gemm_launch<BF16, 2>(A, B, nullptr, Bs, D, N, mode, mu, alpha, gscale, sa, sb, err, st);
+  return gemm_launch<BF16, 0>(A, B, nullptr, nullptr, D, N, mode, mu, alpha, gscale, sa, sb, err, st);
 }
 
 }  // namespace
 
 bool tc_solve_supported(int N) { return N >= 128 && N <= 8192 && N % 128 == 0; }
+
+cudaError_t dct_plan_tc_split(DctPlan& p, cudaStream_t st) {
+  const int N = p.N;
+  const size_t bytes = (size_t)N * N * 4;
+  const float* src[4] = {p.C, p.CT, p.E, p.ET};
+  void** dst[4] = {&p.Cs, &p.CTs, &p.Es, &p.ETs};
+  for (int i = 0; i < 4; ++i) {
+    if (!src[i] || *dst[i]) continue;
+    cudaError_t e = cudaMalloc(dst[i], bytes);
+    if (e != cudaSuccess) return e;
+    const int blocks = (int)std::min<long>(((long)N * N / 4 + 255) / 256, 8192);
+    k_split_tiles<<<blocks, 256, 0, st>>>(src[i], (uint8_t*)*dst[i], N);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
                          cudaStream_t st) {
@@ -276,10 +356,11 @@ cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp,
   float* t0 = tmp;
   float* t1 = tmp + (size_t)N * N;
   cudaError_t e;
-  if ((e = gemm<true>(b, p.C, t0, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;    // T1^T = (b C^T)^T
-  if ((e = gemm<true>(p.C, t0, t1, N, 1, p.mu, alpha, scale, 1.f, 1.f, err, st))) return e;      // T2^T = (gain .* C T1)^T
-  if ((e = gemm<true>(p.CT, t1, t0, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;  // T3 = C^T T2
-  return gemm<true>(t0, p.CT, x, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st);                // x = T3 C
+  // the constant operand of every product comes pre-split (p.Cs, p.CTs) when the plan has it
+  if ((e = gemm<true>(b, p.C, t0, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.Cs))) return e;  // T1^T
+  if ((e = gemm<true>(p.C, t0, t1, N, 1, p.mu, alpha, scale, 1.f, 1.f, err, st, p.Cs))) return e;            // T2^T
+  if ((e = gemm<true>(p.CT, t1, t0, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, p.CTs))) return e;      // T3
+  return gemm<true>(t0, p.CT, x, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.CTs);             // x
 }
 
 // Spectral gradient in the split-precision mode (the forward differences of
@@ -296,14 +377,15 @@ cudaError_t dct_grad_tc(const DctPlan& p, const float* b, float* gx, float* gy, 
   float* Z = tmp + (size_t)N * N;
   float* Q = gy;
   cudaError_t e;
-  if ((e = gemm<true>(b, p.C, X, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;   // X = C b^T
-  if ((e = gemm<true>(p.C, X, Q, N, 0, p.mu, alpha, scale, 1.f, 1.f, err, st))) return e;      // Q
-  if ((e = gemm<true>(p.C, X, Z, N, 1, p.mu, alpha, scale, 1.f, 1.f, err, st))) return e;      // Z = Q^T
-  if ((e = gemm<true>(p.CT, Z, X, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;  // X = U = C^T Q
-  if ((e = gemm<true>(X, p.ET, gx, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e; // gx = U E
-  if (phi && (e = gemm<true>(X, p.CT, phi, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;  // phi = U C
-  if ((e = gemm<true>(Q, p.CT, Z, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st))) return e;  // Z = (Q C)^T
-  return gemm<true>(p.ET, Z, gy, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st);              // gy = E^T V
+  if ((e = gemm<true>(b, p.C, X, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.Cs))) return e;    // X = C b^T
+  if ((e = gemm<true>(p.C, X, Q, N, 0, p.mu, alpha, scale, 1.f, 1.f, err, st, p.Cs))) return e;               // Q
+  if ((e = gemm<true>(p.C, X, Z, N, 1, p.mu, alpha, scale, 1.f, 1.f, err, st, p.Cs))) return e;               // Z = Q^T
+  if ((e = gemm<true>(p.CT, Z, X, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, p.CTs))) return e;          // U = C^T Q
+  if ((e = gemm<true>(X, p.ET, gx, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.ETs))) return e;  // gx = U E
+  if (phi && (e = gemm<true>(X, p.CT, phi, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.CTs)))
+    return e;                                                                                                   // phi = U C
+  if ((e = gemm<true>(Q, p.CT, Z, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.CTs))) return e;  // (Q C)^T
+  return gemm<true>(p.ET, Z, gy, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, p.ETs);                      // gy = E^T V
 }
 
 }  // namespace gp
