@@ -128,11 +128,12 @@ __device__ __forceinline__ void load_split(const float* __restrict__ src, int ld
   }
 }
 
-// One tile (hi slab then lo slab, 2 x TILE_BYTES) of a pre-split operand into
-// shared memory by the bulk-copy engine; the mbarrier counts the bytes.
+// The bulk-copy engine brings pre-split tiles (hi slab then lo slab,
+// 2 x TILE_BYTES) into shared memory; the mbarrier counts the bytes.
+__device__ __forceinline__ void expect_bytes(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ void bulk_tile(uint32_t dst, const void* src, uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)(2 * TILE_BYTES))
-               : "memory");
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                "l"(src), "r"((uint32_t)(2 * TILE_BYTES)), "r"(bar)
                : "memory");
@@ -164,10 +165,11 @@ __global__ void k_split_tiles(const float* __restrict__ M, uint8_t* __restrict__
 // row-major (K-major) FP32.  mode 0: D[m][n] stored; 1: D^T stored (D[n][m]).
 // gain (mu != nullptr): D[m][n] *= gscale / (alpha + mu[m] + mu[n]), 0 when
 // the denominator is 0.  Operand scales sa, sb are undone in the epilogue.
-// PRE = 1 (2): A (B) comes pre-split (k_split_tiles layout, pointer As / Bs)
-// and is copied by the bulk-copy engine; the other operand is loaded and
-// split by the threads.  PRE = 0: both split on the fly.
-template <bool BF16, int PRE>
+// PRE bit 0 (1): A (B) comes pre-split (k_split_tiles layout, pointer As / Bs)
+// and is copied by the bulk-copy engine; an operand without its bit is loaded
+// and split by the threads.  OSPLIT: the epilogue writes D (or D^T) as
+// pre-split tiles for the next product instead of FP32.
+template <bool BF16, int PRE, bool OSPLIT>
 __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restrict__ A, const float* __restrict__ B,
                                                            const uint8_t* __restrict__ As,
                                                            const uint8_t* __restrict__ Bs, float* __restrict__ D,
@@ -218,12 +220,13 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
       ok = false;
       break;
     }
-    if (PRE != 0 && threadIdx.x == 0) {  // the pre-split operand: one bulk copy (hi and lo slabs)
-      if (PRE == 1) bulk_tile(smem_u32(a_hi), As + split_tile_offset(m0 / BM, kt, K), smem_u32(full + st));
-      else bulk_tile(smem_u32(b_hi), Bs + split_tile_offset(n0 / BN, kt, K), smem_u32(full + st));
+    if (PRE != 0 && threadIdx.x == 0) {  // pre-split operands: one bulk copy each (hi and lo slabs)
+      expect_bytes(smem_u32(full + st), (uint32_t)((PRE == 3 ? 2 : 1) * 2 * TILE_BYTES));
+      if (PRE & 1) bulk_tile(smem_u32(a_hi), As + split_tile_offset(m0 / BM, kt, K), smem_u32(full + st));
+      if (PRE & 2) bulk_tile(smem_u32(b_hi), Bs + split_tile_offset(n0 / BN, kt, K), smem_u32(full + st));
     }
-    if (PRE != 1) load_split<BF16>(A, K, m0, kt * BK, sa, a_hi, a_lo);
-    if (PRE != 2) load_split<BF16>(B, K, n0, kt * BK, sb, b_hi, b_lo);
+    if (!(PRE & 1)) load_split<BF16>(A, K, m0, kt * BK, sa, a_hi, a_lo);
+    if (!(PRE & 2)) load_split<BF16>(B, K, n0, kt * BK, sb, b_hi, b_lo);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (PRE != 0 && threadIdx.x == 0) {
       if (!mbar_wait(smem_u32(full + st), fphase[st], kWaitLimit)) ok = false;
@@ -289,7 +292,32 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
         }
         v[c] = x;
       }
-      if (mode == 0) {
+      if constexpr (OSPLIT) {
+        uint8_t* Ds = reinterpret_cast<uint8_t*>(D);
+        if (mode == 0) {  // operand row m, K index n: four consecutive K per 8-byte store
+#pragma unroll
+          for (int c = 0; c < 32; c += 4) {
+            const int n = n0 + c0 + c;
+            uint2 hv, lv;
+            split4<BF16>(make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]), hv, lv);
+            uint8_t* tile = Ds + split_tile_offset(m / BM, n / BK, Nn);
+            const uint32_t off = kmajor_offset(m % BM, n % BK);
+            *reinterpret_cast<uint2*>(tile + off) = hv;
+            *reinterpret_cast<uint2*>(tile + TILE_BYTES + off) = lv;
+          }
+        } else {  // D^T: operand row n, K index m (consecutive across the warp's lanes)
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            const int n = n0 + c0 + c;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v[c]);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v[c] - __bfloat162float(hi));
+            uint8_t* tile = Ds + split_tile_offset(n / BM, m / BK, Nn);
+            const uint32_t off = kmajor_offset(n % BM, m % BK);
+            *reinterpret_cast<__nv_bfloat16*>(tile + off) = hi;
+            *reinterpret_cast<__nv_bfloat16*>(tile + TILE_BYTES + off) = lo;
+          }
+        }
+      } else if (mode == 0) {
         float* row = D + (size_t)m * Nn + n0 + c0;
 #pragma unroll
         for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4*>(row + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
@@ -307,26 +335,41 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
   }
 }
 
-template <bool BF16, int PRE>
-cudaError_t gemm_launch(const float* A, const float* B, const void* As, const void* Bs, float* D, int N, int mode,
-                        const float* mu, float alpha, float gscale, float sa, float sb, int* err, cudaStream_t st) {
-  cudaError_t e =
-      cudaFuncSetAttribute(k_tc_gemm_split<BF16, PRE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+template <bool BF16, int PRE, bool OSPLIT>
+cudaError_t gemm_launch(const float* A, const float* B, const void* As, const void* Bs, void* D, int N, int mode,
+                        const float* mu, float alpha, float gscale, int* err, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_split<BF16, PRE, OSPLIT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
   dim3 grid(N / BN, N / BM);
-  k_tc_gemm_split<BF16, PRE><<<grid, THREADS, SMEM_BYTES, st>>>(A, B, (const uint8_t*)As, (const uint8_t*)Bs, D, N,
-                                                                 N, mode, mu, alpha, gscale, sa, sb, err);
+  k_tc_gemm_split<BF16, PRE, OSPLIT><<<grid, THREADS, SMEM_BYTES, st>>>(
+      A, B, (const uint8_t*)As, (const uint8_t*)Bs, (float*)D, N, N, mode, mu, alpha, gscale, 1.f, 1.f, err);
   return cudaGetLastError();
 }
 
-// D = epi(A B^T); As / Bs (may be null): the same operand pre-split (at most one).
+// An operand of a product: FP32 (split on the fly) or pre-split tiles.
+struct Op {
+  const float* f = nullptr;
+  const void* s = nullptr;
+};
+inline Op fp(const float* f) { return Op{f, nullptr}; }
+inline Op pre(const void* s) { return Op{nullptr, s}; }
+
+// D (FP32, or pre-split tiles when dsplit) = epi(A B^T).
 template <bool BF16>
-cudaError_t gemm(const float* A, const float* B, float* D, int N, int mode, const float* mu, float alpha,
-                 float gscale, float sa, float sb, int* err, cudaStream_t st, const void* As = nullptr,
-                 const void* Bs = nullptr) {
-  if (As) return gemm_launch<BF16, 1>(A, B, As, nullptr, D, N, mode, mu, alpha, gscale, sa, sb, err, st);
-  if (Bs) return gemm_launch<BF16, 2>(A, B, nullptr, Bs, D, N, mode, mu, alpha, gscale, sa, sb, err, st);
-  return gemm_launch<BF16, 0>(A, B, nullptr, nullptr, D, N, mode, mu, alpha, gscale, sa, sb, err, st);
+cudaError_t gemm(Op A, Op B, void* D, bool dsplit, int N, int mode, const float* mu, float alpha, float gscale,
+                 int* err, cudaStream_t st) {
+  const int pre_mask = (A.s ? 1 : 0) | (B.s ? 2 : 0);
+#define GP_G(P)                                                                                            \
+  return dsplit ? gemm_launch<BF16, P, true>(A.f, B.f, A.s, B.s, D, N, mode, mu, alpha, gscale, err, st) \
+                : gemm_launch<BF16, P, false>(A.f, B.f, A.s, B.s, D, N, mode, mu, alpha, gscale, err, st)
+  switch (pre_mask) {
+    case 1: GP_G(1);
+    case 2: GP_G(2);
+    case 3: GP_G(3);
+    default: GP_G(0);
+  }
+#undef GP_G
 }
 
 }  // namespace
@@ -352,40 +395,41 @@ cudaError_t dct_plan_tc_split(DctPlan& p, cudaStream_t st) {
 cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
                          cudaStream_t st) {
   const int N = p.N;
-  if (!p.C || !p.CT || !tc_solve_supported(N)) return cudaErrorInvalidValue;
-  float* t0 = tmp;
-  float* t1 = tmp + (size_t)N * N;
+  if (!p.Cs || !p.CTs || !tc_solve_supported(N)) return cudaErrorInvalidValue;
+  // intermediates are stored as pre-split tiles (4 bytes per element, as FP32)
+  void* t0 = tmp;
+  void* t1 = tmp + (size_t)N * N;
   cudaError_t e;
-  // the constant operand of every product comes pre-split (p.Cs, p.CTs) when the plan has it
-  if ((e = gemm<true>(b, p.C, t0, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.Cs))) return e;  // T1^T
-  if ((e = gemm<true>(p.C, t0, t1, N, 1, p.mu, alpha, scale, 1.f, 1.f, err, st, p.Cs))) return e;            // T2^T
-  if ((e = gemm<true>(p.CT, t1, t0, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, p.CTs))) return e;      // T3
-  return gemm<true>(t0, p.CT, x, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.CTs);             // x
+  if ((e = gemm<true>(fp(b), pre(p.Cs), t0, true, N, 1, nullptr, alpha, scale, err, st))) return e;   // T1^T = (b C^T)^T
+  if ((e = gemm<true>(pre(p.Cs), pre(t0), t1, true, N, 1, p.mu, alpha, scale, err, st))) return e;   // T2^T = (gain .* C T1)^T
+  if ((e = gemm<true>(pre(p.CTs), pre(t1), t0, true, N, 0, nullptr, alpha, scale, err, st))) return e;  // T3 = C^T T2
+  return gemm<true>(pre(t0), pre(p.CTs), x, false, N, 0, nullptr, alpha, scale, err, st);            // x = T3 C
 }
 
 // Spectral gradient in the split-precision mode (the forward differences of
 // the solution synthesised from its spectrum, as the FP32 path does, so that
 // the solve's error is not amplified by 1/h):
-//   t0 = C b^T,  Q = gain .* (C t0^T) (and Q^T),  U = C^T Q,
+//   X = C b^T,  Q = gain .* (C X^T) (and Q^T),  U = C^T Q,
 //   gx = U E,  phi = U C (optional),  V^T = (Q C)^T,  gy = E^T V.
-// Buffers: X = tmp, Z = tmp + N^2, Q lives in gy until the last product.
+// X, Z = tmp; Q lives in gy until the last product; intermediates are
+// pre-split tiles.
 cudaError_t dct_grad_tc(const DctPlan& p, const float* b, float* gx, float* gy, float* phi, float* tmp, float alpha,
                         float scale, int* err, cudaStream_t st) {
   const int N = p.N;
-  if (!p.C || !p.CT || !p.E || !p.ET || !tc_solve_supported(N)) return cudaErrorInvalidValue;
-  float* X = tmp;
-  float* Z = tmp + (size_t)N * N;
-  float* Q = gy;
+  if (!p.Cs || !p.CTs || !p.ETs || !tc_solve_supported(N)) return cudaErrorInvalidValue;
+  void* X = tmp;
+  void* Z = tmp + (size_t)N * N;
+  void* Q = gy;
   cudaError_t e;
-  if ((e = gemm<true>(b, p.C, X, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.Cs))) return e;    // X = C b^T
-  if ((e = gemm<true>(p.C, X, Q, N, 0, p.mu, alpha, scale, 1.f, 1.f, err, st, p.Cs))) return e;               // Q
-  if ((e = gemm<true>(p.C, X, Z, N, 1, p.mu, alpha, scale, 1.f, 1.f, err, st, p.Cs))) return e;               // Z = Q^T
-  if ((e = gemm<true>(p.CT, Z, X, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, p.CTs))) return e;          // U = C^T Q
-  if ((e = gemm<true>(X, p.ET, gx, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.ETs))) return e;  // gx = U E
-  if (phi && (e = gemm<true>(X, p.CT, phi, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.CTs)))
-    return e;                                                                                                   // phi = U C
-  if ((e = gemm<true>(Q, p.CT, Z, N, 1, nullptr, alpha, scale, 1.f, 1.f, err, st, nullptr, p.CTs))) return e;  // (Q C)^T
-  return gemm<true>(p.ET, Z, gy, N, 0, nullptr, alpha, scale, 1.f, 1.f, err, st, p.ETs);                      // gy = E^T V
+  if ((e = gemm<true>(fp(b), pre(p.Cs), X, true, N, 1, nullptr, alpha, scale, err, st))) return e;       // X = C b^T
+  if ((e = gemm<true>(pre(p.Cs), pre(X), Q, true, N, 0, p.mu, alpha, scale, err, st))) return e;        // Q
+  if ((e = gemm<true>(pre(p.Cs), pre(X), Z, true, N, 1, p.mu, alpha, scale, err, st))) return e;        // Z = Q^T
+  if ((e = gemm<true>(pre(p.CTs), pre(Z), X, true, N, 0, nullptr, alpha, scale, err, st))) return e;    // X = U = C^T Q
+  if ((e = gemm<true>(pre(X), pre(p.ETs), gx, false, N, 0, nullptr, alpha, scale, err, st))) return e;  // gx = U E
+  if (phi && (e = gemm<true>(pre(X), pre(p.CTs), phi, false, N, 0, nullptr, alpha, scale, err, st)))
+    return e;                                                                                            // phi = U C
+  if ((e = gemm<true>(pre(Q), pre(p.CTs), Z, true, N, 1, nullptr, alpha, scale, err, st))) return e;    // Z = (Q C)^T
+  return gemm<true>(pre(p.ETs), pre(Z), gy, false, N, 0, nullptr, alpha, scale, err, st);               // gy = E^T V
 }
 
 }  // namespace gp
