@@ -8,15 +8,19 @@
 //     A B^T ~= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
 // is accumulated in FP32 in tensor memory (the dropped A_lo B_lo^T term is
 // ~2^-16 relative; BF16 keeps FP32's exponent range, so no operand scaling
-// is needed).  One CTA (256 threads) computes a 128 x 128 tile.  Its K loop
-// is a two-stage pipeline: all threads load and split the next 128 x 64 slab
-// of each operand into one shared-memory stage (canonical K-major layout
-// without swizzle) while the tensor core multiplies the other; one thread
-// issues the tcgen05.mma instructions, and tcgen05.commit signals the stage's
-// mbarrier when they have read it.  The epilogue moves the accumulator out of
-// tensor memory with tcgen05.ld (a warp reads its lane quadrant, two warps
-// share the columns), applies the spectral gain when asked, and stores the
-// tile, transposed when asked, so
+// is needed).  One CTA (256 threads) computes a 128 x 128 tile.  Operands
+// come either as FP32 (loaded and split by the threads) or pre-split into
+// 128 x 64 tiles of the canonical K-major layout without swizzle (the
+// constant cosine / derivative matrices, split once per plan, and every
+// intermediate product, which the epilogue writes in that form), copied by
+// the bulk-copy engine.  The K loop runs over three shared-memory stages: the
+// next slab's copies are in flight while the tensor core multiplies the
+// current one; one thread issues the tcgen05.mma instructions, and
+// tcgen05.commit signals the stage's mbarrier when they have read it.  The
+// epilogue moves the accumulator out of tensor memory with tcgen05.ld (a warp
+// reads its lane quadrant, two warps share the columns), applies the spectral
+// gain when asked, and stores the tile (FP32 or split), transposed when asked,
+// so
 // that every operand of the next GEMM is again K-major:
 //     G1: T1^T <- (b C^T)^T      G2: T2^T <- (gain .* (C T1))^T
 //     G3: T3   <- C^T T2         G4: x    <- T3 C
@@ -35,7 +39,7 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int TILE_BYTES = BM * BK * 2;  // one 16-bit operand slab, 16 KiB
-constexpr int STAGES = 2;                // shared-memory stages (a_hi, a_lo, b_hi, b_lo each)
+constexpr int STAGES = 3;                // shared-memory stages (a_hi, a_lo, b_hi, b_lo each)
 constexpr int THREADS = 256;
 constexpr int SMEM_BYTES = STAGES * 4 * TILE_BYTES + 128;  // stages, 2 x STAGES mbarriers, TMEM slot
 constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds before giving up
@@ -199,31 +203,44 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = instr_desc<BF16>();
   bool ok = true;
-  uint32_t phase[STAGES] = {0u, 0u};   // parity of the next completion of each stage's mbarrier
-  uint32_t fphase[STAGES] = {0u, 0u};  // same for the bulk-copy mbarriers
-  int last = -1;                      // stage of the last committed tile
+  uint32_t phase[STAGES], fphase[STAGES];  // parity of each stage's next MMA / bulk-copy completion
+#pragma unroll
+  for (int i = 0; i < STAGES; ++i) phase[i] = fphase[i] = 0u;
+  int last = -1;  // stage of the last committed tile
   const int nk = K / BK;
-  // Two-stage pipeline: while the tensor core multiplies tile kt (stage kt % 2),
-  // all threads load and split tile kt + 1 into the other stage.  A stage is
-  // refilled only after the commit of the tile that used it (kt - 2) arrived.
+  auto stage_ptr = [&](int st) { return smem + st * 4 * TILE_BYTES; };
+  // bulk copies of tile kt's pre-split operands into stage kt % STAGES (thread 0)
+  auto prefetch = [&](int kt) {
+    if (PRE == 0 || threadIdx.x != 0) return;
+    const int st = kt % STAGES;
+    uint8_t* a_hi = stage_ptr(st);
+    expect_bytes(smem_u32(full + st), (uint32_t)((PRE == 3 ? 2 : 1) * 2 * TILE_BYTES));
+    if (PRE & 1) bulk_tile(smem_u32(a_hi), As + split_tile_offset(m0 / BM, kt, K), smem_u32(full + st));
+    if (PRE & 2) bulk_tile(smem_u32(a_hi + 2 * TILE_BYTES), Bs + split_tile_offset(n0 / BN, kt, K), smem_u32(full + st));
+  };
+  // Pipeline over STAGES stages: iteration kt first frees the stage of tile
+  // kt + 1 (its previous user, tile kt + 1 - STAGES, committed two iterations
+  // ago) and starts that tile's bulk copies, then fills the thread-split
+  // operand of tile kt, waits for tile kt's copies and issues its MMAs; the
+  // tensor core works on tile kt while tile kt + 1 is in flight.
+  prefetch(0);
   for (int kt = 0; kt < nk; ++kt) {
-    const int st = kt & 1;
-    uint8_t* a_hi = smem + st * 4 * TILE_BYTES;
+    const int st = kt % STAGES;
+    uint8_t* a_hi = stage_ptr(st);
     uint8_t* a_lo = a_hi + TILE_BYTES;
     uint8_t* b_hi = a_hi + 2 * TILE_BYTES;
     uint8_t* b_lo = a_hi + 3 * TILE_BYTES;
-    if (kt >= STAGES) {
-      if (!mbar_wait(smem_u32(bar + st), phase[st], kWaitLimit)) ok = false;
-      phase[st] ^= 1u;
-    }
-    if (!__syncthreads_and(ok)) {
-      ok = false;
-      break;
-    }
-    if (PRE != 0 && threadIdx.x == 0) {  // pre-split operands: one bulk copy each (hi and lo slabs)
-      expect_bytes(smem_u32(full + st), (uint32_t)((PRE == 3 ? 2 : 1) * 2 * TILE_BYTES));
-      if (PRE & 1) bulk_tile(smem_u32(a_hi), As + split_tile_offset(m0 / BM, kt, K), smem_u32(full + st));
-      if (PRE & 2) bulk_tile(smem_u32(b_hi), Bs + split_tile_offset(n0 / BN, kt, K), smem_u32(full + st));
+    if (kt + 1 < nk) {
+      const int sn = (kt + 1) % STAGES;
+      if (kt + 1 >= STAGES) {
+        if (!mbar_wait(smem_u32(bar + sn), phase[sn], kWaitLimit)) ok = false;
+        phase[sn] ^= 1u;
+      }
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      prefetch(kt + 1);
     }
     if (!(PRE & 1)) load_split<BF16>(A, K, m0, kt * BK, sa, a_hi, a_lo);
     if (!(PRE & 2)) load_split<BF16>(B, K, n0, kt * BK, sb, b_hi, b_lo);
