@@ -369,7 +369,6 @@ struct Op {
   const float* f = nullptr;
   const void* s = nullptr;
 };
-inline Op fp(const float* f) { return Op{f, nullptr}; }
 inline Op pre(const void* s) { return Op{nullptr, s}; }
 
 // D (FP32, or pre-split tiles when dsplit) = epi(A B^T).
@@ -392,6 +391,16 @@ cudaError_t gemm(Op A, Op B, void* D, bool dsplit, int N, int mode, const float*
 }  // namespace
 
 bool tc_solve_supported(int N) { return N >= 128 && N <= 8192 && N % 128 == 0; }
+
+namespace {
+// The FP32 input of the first product as pre-split tiles (so that every
+// product's operands arrive by bulk copy).
+cudaError_t split_input(const float* b, void* out, int N, cudaStream_t st) {
+  const int blocks = (int)std::min<long>(((long)N * N / 4 + 255) / 256, 8192);
+  k_split_tiles<<<blocks, 256, 0, st>>>(b, (uint8_t*)out, N);
+  return cudaGetLastError();
+}
+}  // namespace
 
 cudaError_t dct_plan_tc_split(DctPlan& p, cudaStream_t st) {
   const int N = p.N;
@@ -417,7 +426,8 @@ cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp,
   void* t0 = tmp;
   void* t1 = tmp + (size_t)N * N;
   cudaError_t e;
-  if ((e = gemm<true>(fp(b), pre(p.Cs), t0, true, N, 1, nullptr, alpha, scale, err, st))) return e;   // T1^T = (b C^T)^T
+  if ((e = split_input(b, t1, N, st))) return e;                                                         // t1 = split(b)
+  if ((e = gemm<true>(pre(t1), pre(p.Cs), t0, true, N, 1, nullptr, alpha, scale, err, st))) return e;  // T1^T = (b C^T)^T
   if ((e = gemm<true>(pre(p.Cs), pre(t0), t1, true, N, 1, p.mu, alpha, scale, err, st))) return e;   // T2^T = (gain .* C T1)^T
   if ((e = gemm<true>(pre(p.CTs), pre(t1), t0, true, N, 0, nullptr, alpha, scale, err, st))) return e;  // T3 = C^T T2
   return gemm<true>(pre(t0), pre(p.CTs), x, false, N, 0, nullptr, alpha, scale, err, st);            // x = T3 C
@@ -438,7 +448,8 @@ cudaError_t dct_grad_tc(const DctPlan& p, const float* b, float* gx, float* gy, 
   void* Z = tmp + (size_t)N * N;
   void* Q = gy;
   cudaError_t e;
-  if ((e = gemm<true>(fp(b), pre(p.Cs), X, true, N, 1, nullptr, alpha, scale, err, st))) return e;       // X = C b^T
+  if ((e = split_input(b, Z, N, st))) return e;                                                            // Z = split(b)
+  if ((e = gemm<true>(pre(Z), pre(p.Cs), X, true, N, 1, nullptr, alpha, scale, err, st))) return e;      // X = C b^T
   if ((e = gemm<true>(pre(p.Cs), pre(X), Q, true, N, 0, p.mu, alpha, scale, err, st))) return e;        // Q
   if ((e = gemm<true>(pre(p.Cs), pre(X), Z, true, N, 1, p.mu, alpha, scale, err, st))) return e;        // Z = Q^T
   if ((e = gemm<true>(pre(p.CTs), pre(Z), X, true, N, 0, nullptr, alpha, scale, err, st))) return e;    // X = U = C^T Q
