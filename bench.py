@@ -47,6 +47,8 @@ BYTES_PER_POINT = {
     "dct_tc_split": 32,    # four GEMMs, each reads two N^2 operands and writes one (contraction-bound)
     "rof_fused": 32,       # read grad u(2), p(2), I; write p(2), r   (gap steps also read u)
     "emd_fused": 48,       # read grad q(2), s(2), p(2), g; write s(2), p(2), d  (gap steps add m(2), e)
+    "rof_step_fwd": 28,    # read grad u(2), p(2), I; write p(2), row spectrum of r
+    "emd_step_fwd": 48,    # read grad q(2), s(2), p(2), g; write s(2), p(2), row spectrum of d
 }
 
 # ncu DRAM traffic (read + write bytes per launch) of the dominant kernel at
@@ -309,9 +311,10 @@ def run_ours(args):
     # window replays them from CUDA graphs, kernel for kernel)
     launches = int(round(sum(v[1] for v in prof.values()) * args.steps / prof_steps))
 
-    # whole-iteration HBM fraction (algorithmic bytes of all passes / step time)
-    it_bytes = (8 + 12 + 16 + 32) * N * N + (8 + 12 + 16 + 48) * N * N  # ROF + EMD per iteration
-    whole_frac = (it_bytes * ITERS_PER_STEP * args.steps / (ms_max / 1e3) / 1e9) / peak
+    # whole-step HBM fraction: algorithmic bytes of every pass the step launches (profiled pass,
+    # per step) over the step time
+    step_bytes = sum(BYTES_PER_POINT[k] * v[1] for k, v in prof.items() if k in BYTES_PER_POINT) * N * N / prof_steps
+    whole_frac = (step_bytes * args.steps / (ms_max / 1e3) / 1e9) / peak
 
     # end to end through the public solve calls with host (pinned) buffers: every step copies
     # its inputs in and its results out; the copies run on their own streams into / out of

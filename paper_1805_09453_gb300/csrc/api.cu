@@ -33,13 +33,16 @@ enum {
   PK_EMD_FUSED,
   PK_REDUCE,
   PK_SETUP,
+  PK_ROF_STEP_FWD,
+  PK_EMD_STEP_FWD,
   PK_COUNT
 };
 static const char* kProfNames[PK_COUNT] = {"dct_rows_fwd", "dct_cols_solve", "dct_rows_inv", "dct_cols_grad",
                                            "dct_rows_grad", "dct_dense",     "dct_tc_split", "rof_fused",
-                                           "emd_fused",     "reduce",        "setup"};
+                                           "emd_fused",     "reduce",        "setup",         "rof_step_fwd",
+                                           "emd_step_fwd"};
 // Kernel launches behind one recorded launch of a class.
-static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 4, 1, 1, 1, 1};
+static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 4, 1, 1, 1, 1, 1, 1};
 
 struct Profiler {
   bool on = false;
@@ -104,6 +107,8 @@ struct gp_state_s {
   float* phi = nullptr;              // EMD: dual potential
   float* g = nullptr;                // EMD: f0 - f1
   float* tmp = nullptr;              // solve scratch, 2 N^2
+  float* rh = nullptr;               // fast sizes: row spectra of the next right-hand side, left by a
+                                     // fused step kernel for the next step of the same chunk
   double* part = nullptr;            // this state's per-block partial sums
   bool vec = false;
   int rb = 16;                  // row-block height of the fused kernel (autotuned tile shape)
@@ -253,20 +258,25 @@ gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double
 // and, when want_phi, phi = x.  Fast sizes (and the split-precision tensor-core
 // mode) take the gradient in the spectral domain; other sizes difference the
 // dense solve's output (phi is then always written).  tmp holds 2 N^2.
+// b_rows: b already holds the row spectra of the right-hand side (the
+// interleaved output of the forward row pass; fast sizes, FP32 only).
 gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, bool want_phi, float* tmp,
-                     double alpha, double scale, int prec, cudaStream_t st) {
+                     double alpha, double scale, int prec, cudaStream_t st, bool b_rows = false) {
   const DctPlan* p = nullptr;
   gp_status s = get_plan(h, N, &p);
   if (s != GP_OK) return s;
   if (prec != GP_PREC_FP32 && prec != GP_PREC_SPLIT_BF16)
     return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
+  if (b_rows && !(p->fft && prec == GP_PREC_FP32)) return fail(h, GP_ERR_ARG, "row spectra need the FP32 fast path");
   const float a = (float)alpha, sc = (float)scale;
   const size_t NN = (size_t)N * N;
   if (p->fft && prec == GP_PREC_FP32) {
     float* A = tmp;
     float* B = tmp + NN;
-    GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return dct_fft_pass(*p, 0, b, A, a, sc, st); }));
-    GP_CUDA(h, plaunch(h, PK_DCT_COLS_GRAD, st, [&] { return dct_grad_cols(*p, A, A, B, a, sc, st); }));
+    if (!b_rows)
+      GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return dct_fft_pass(*p, 0, b, A, a, sc, st); }));
+    const float* in = b_rows ? b : A;
+    GP_CUDA(h, plaunch(h, PK_DCT_COLS_GRAD, st, [&] { return dct_grad_cols(*p, in, A, B, a, sc, st); }));
     GP_CUDA(h, plaunch(h, PK_DCT_ROWS_GRAD, st,
                        [&] { return dct_grad_rows(*p, A, B, g2, g2 + NN, want_phi ? phi : nullptr, st); }));
     return GP_OK;
@@ -343,6 +353,7 @@ gp_status alloc_state(gp_handle h, int kind, int N, gp_state* out) {
   if (!e) e = A(&s->p[0], 2 * NN);
   if (!e) e = A(&s->p[1], 2 * NN);
   if (!e) e = A(&s->tmp, 2 * NN);
+  if (!e && N >= 16 && N <= 8192 && (N & (N - 1)) == 0) e = A(&s->rh, NN);
   if (kind == KIND_ROF && !e) e = A(&s->gu, 2 * NN);
   if (kind == KIND_ROF && !e) e = A(&s->Ic, NN);
   if (kind == KIND_EMD) {
@@ -415,20 +426,40 @@ gp_status rof_setup(gp_state s, const float* I, double lam, double tau, double s
   return GP_OK;
 }
 
+// Within a chunk of steps, every step but the last runs its stencil fused
+// with the next solve's forward row pass (fast sizes, FP32): the right-hand
+// side reaches the next step as row spectra in s->rh.  The last step of a
+// chunk (the gap step, when there is one) writes the right-hand side itself,
+// so a chunk always starts and ends with s->r current.
+const DctPlan* fused_step_plan(gp_state s, int prec) {
+  if (prec != GP_PREC_FP32 || !s->rh || !s->vec) return nullptr;
+  auto it = s->h->plans.find(s->N);
+  return it != s->h->plans.end() && it->second.fft ? &it->second : nullptr;
+}
+
 gp_status rof_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cudaStream_t st) {
   gp_handle h = s->h;
   const int N = s->N;
   RofParams P{N, (float)N, (float)((double)N * N), (float)(s->lam * s->tau), (float)s->tau, (float)s->sigma};
   for (int k = 0; k < n_steps; ++k) {
     const bool g = gap_last && (k == n_steps - 1);
+    const DctPlan* fp = fused_step_plan(s, prec);  // the plan exists after the first solve
+    const bool rows_in = fp && k > 0;
     // grad u_{n+1} from the spectrum; u_{n+1} itself only when the step reports the objective
-    gp_status r = solve_grad(h, N, s->r, s->gu, s->prim, g, s->tmp, s->lam * s->tau, 1.0, prec, st);
+    gp_status r = solve_grad(h, N, rows_in ? s->rh : s->r, s->gu, s->prim, g, s->tmp, s->lam * s->tau, 1.0, prec, st,
+                             rows_in);
     if (r != GP_OK) return r;
     float* pin = s->p[s->cur];
     float* pout = s->p[1 - s->cur];
-    GP_CUDA(h, plaunch(h, PK_ROF_FUSED, st, [&] {
-              return launch_rof_fused(s->gu, s->prim, pin, s->Ic, pout, s->r, s->part, P, s->vec, g, s->rb, st);
-            }));
+    fp = fused_step_plan(s, prec);
+    if (fp && k < n_steps - 1) {
+      GP_CUDA(h, plaunch(h, PK_ROF_STEP_FWD, st,
+                         [&] { return dct_rof_step_fwd(*fp, s->gu, pin, s->Ic, pout, s->rh, P, st); }));
+    } else {
+      GP_CUDA(h, plaunch(h, PK_ROF_FUSED, st, [&] {
+                return launch_rof_fused(s->gu, s->prim, pin, s->Ic, pout, s->r, s->part, P, s->vec, g, s->rb, st);
+              }));
+    }
     s->cur = 1 - s->cur;
     s->n++;
   }
@@ -440,15 +471,26 @@ gp_status emd_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
   const int N = s->N;
   EmdParams P{N, (float)N, (float)s->tau, (float)s->sigma};
   for (int k = 0; k < n_steps; ++k) {
+    const DctPlan* fp = fused_step_plan(s, prec);
+    const bool rows_in = fp && k > 0;
     // grad q, q = Lap^{-1} d  <=>  (0 - Lap) q = -d
-    gp_status r = solve_grad(h, N, s->r, s->prim, s->phi, false, s->tmp, 0.0, -1.0, prec, st);
+    gp_status r = solve_grad(h, N, rows_in ? s->rh : s->r, s->prim, s->phi, false, s->tmp, 0.0, -1.0, prec, st,
+                             rows_in);
     if (r != GP_OK) return r;
     const bool g = gap_last && (k == n_steps - 1);
     const int c = s->cur;
-    GP_CUDA(h, plaunch(h, PK_EMD_FUSED, st, [&] {
-              return launch_emd_fused(s->prim, s->s[c], s->p[c], s->g, s->s[1 - c], s->p[1 - c], s->r, s->m, s->e,
-                                      s->part, P, s->vec, g, s->rb, st);
-            }));
+    fp = fused_step_plan(s, prec);
+    if (fp && k < n_steps - 1) {
+      GP_CUDA(h, plaunch(h, PK_EMD_STEP_FWD, st, [&] {
+                return dct_emd_step_fwd(*fp, s->prim, s->s[c], s->p[c], s->g, s->s[1 - c], s->p[1 - c], s->rh, P,
+                                        st);
+              }));
+    } else {
+      GP_CUDA(h, plaunch(h, PK_EMD_FUSED, st, [&] {
+                return launch_emd_fused(s->prim, s->s[c], s->p[c], s->g, s->s[1 - c], s->p[1 - c], s->r, s->m, s->e,
+                                        s->part, P, s->vec, g, s->rb, st);
+              }));
+    }
     s->cur = 1 - s->cur;
     s->n++;
   }

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "gp_internal.cuh"
+#include "stencil.cuh"
 
 namespace gp {
 namespace {
@@ -384,6 +385,39 @@ __device__ __forceinline__ void scatter4(float2* buf, int j, int N, float4 a, fl
   buf[padi(N - 2 - hj)] = make_float2(a.w, b.w);
 }
 
+// Second half of the forward row pass: the two Makhoul-ordered complex
+// buffers in shared memory (rows 4rb, 4rb+1 in buffer 0, 4rb+2, 4rb+3 in
+// buffer 1) are transformed and their spectra written to the interleaved
+// layout.  Called after a barrier that publishes the buffers.
+template <int LOG2N>
+__device__ __forceinline__ void rows_fwd_tail(float2* smem, float* __restrict__ out, int rb,
+                                              const float2* __restrict__ tw, const float2* __restrict__ wq) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
+  fft_smem<LOG2N, -1, TPF>(smem + f * PADN, t, tw);
+  float* __restrict__ o = out + (size_t)rb * 4 * N;
+  const float2* b0 = smem;
+  const float2* b1 = smem + PADN;
+  #pragma unroll
+  for (int kk = 0; kk <= (N / 2) / (2 * TPF); ++kk) {
+    if (kk == (N / 2) / (2 * TPF) && threadIdx.x != 0) break;
+    const int k = threadIdx.x + kk * 2 * TPF;
+    if (k == 0 || k == N / 2) {
+      const float sc = k == 0 ? 1.f : kRsqrt2;
+      const float2 z0 = b0[padi(k)], z1 = b1[padi(k)];
+      *reinterpret_cast<float4*>(o + 4 * k) = make_float4(sc * z0.x, sc * z0.y, sc * z1.x, sc * z1.y);
+    } else {
+      const float2 w = __ldg(&wq[k]);
+      float4 vk, vn;
+      fwd_post(b0[padi(k)], b0[padi(N - k)], w, vk.x, vn.x, vk.y, vn.y);
+      fwd_post(b1[padi(k)], b1[padi(N - k)], w, vk.z, vn.z, vk.w, vn.w);
+      *reinterpret_cast<float4*>(o + 4 * k) = vk;
+      *reinterpret_cast<float4*>(o + 4 * (N - k)) = vn;
+    }
+  }
+}
+
 // ------------------------------------------------------- row pass, forward
 // CTA = one block of 4 rows (two transforms of two rows each); input
 // row-major, output spectra in the 4-row-interleaved layout.
@@ -405,27 +439,206 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
     scatter4(buf, j, N, *reinterpret_cast<const float4*>(xa + j), *reinterpret_cast<const float4*>(xb + j));
   }
   __syncthreads();
-  fft_smem<LOG2N, -1, TPF>(buf, t, tw);
-  float* __restrict__ o = out + (size_t)rb * 4 * N;
-  const float2* b0 = smem;
-  const float2* b1 = smem + PADN;
-  #pragma unroll
-  for (int kk = 0; kk <= (N / 2) / (2 * TPF); ++kk) {
-    if (kk == (N / 2) / (2 * TPF) && threadIdx.x != 0) break;
-    const int k = threadIdx.x + kk * 2 * TPF;
-    if (k == 0 || k == N / 2) {
-      const float sc = k == 0 ? 1.f : kRsqrt2;
-      const float2 z0 = b0[padi(k)], z1 = b1[padi(k)];
-      *reinterpret_cast<float4*>(o + 4 * k) = make_float4(sc * z0.x, sc * z0.y, sc * z1.x, sc * z1.y);
+  rows_fwd_tail<LOG2N>(smem, out, rb, tw, wq);
+}
+
+// ------------------------------------- stencil fused with the forward row pass
+// One non-gap iteration's pointwise / stencil update (the same arithmetic as
+// k_rof_fused and k_emd_fused, sections 3.1 / 3.2) run by the CTA of the
+// forward row pass of the next solve: the block's 4 rows are updated (dual
+// and auxiliary variables to HBM), the new right-hand side is scattered in
+// Makhoul order straight into the two transform buffers, and the block then
+// transforms it.  The right-hand side never travels through HBM, and the
+// transform's shared-memory work overlaps other blocks' streaming.  The row
+// above the block is recomputed from its inputs, so blocks are independent.
+// Thread layout: NT = N/8 threads, each owning 4 consecutive columns in two
+// chunks (j0 = 4 tid and j0 + N/2), walking the block's rows downwards.
+// Requires every pointer 16-byte aligned (state buffers).
+
+__device__ __forceinline__ void ld4(float* d, const float* __restrict__ p) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  d[0] = t.x; d[1] = t.y; d[2] = t.z; d[3] = t.w;
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, const float* s) {
+  *reinterpret_cast<float4*>(p) = make_float4(s[0], s[1], s[2], s[3]);
+}
+
+// EMD (section 3.2, affine Leray form): with m = s + grad q,
+//   p' = proj(p + sigma m),  s' = m - tau (2 p' - p),  d' = g - div s'.
+template <int LOG2N>
+__global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
+    k_emd_step_rows_fwd(const float* __restrict__ gq, const float* __restrict__ sin_, const float* __restrict__ pin,
+                        const float* __restrict__ g, float* __restrict__ sout, float* __restrict__ pout,
+                        float* __restrict__ out, const float2* __restrict__ tw, const float2* __restrict__ wq,
+                        EmdParams P) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, NT = 2 * C::TPF;
+  constexpr size_t NN = (size_t)N * N;
+  extern __shared__ float2 smem[];
+  const int rb = blockIdx.x, i0 = 4 * rb;
+  const float* __restrict__ gx_ = gq;
+  const float* __restrict__ gy_ = gq + NN;
+  const float* __restrict__ sx_ = sin_;
+  const float* __restrict__ sy_ = sin_ + NN;
+  const float* __restrict__ px_ = pin;
+  const float* __restrict__ py_ = pin + NN;
+#pragma unroll 1
+  for (int ch = 0; ch < N / (4 * NT); ++ch) {
+    const int j0 = 4 * ((int)threadIdx.x + ch * NT);
+    float syu[4];  // s'_y of the row above
+    if (i0 > 0) {
+      const size_t ro = (size_t)(i0 - 1) * N + j0;
+      float gx[4], gy[4], sx[4], sy[4], px[4], py[4];
+      ld4(gx, gx_ + ro); ld4(gy, gy_ + ro); ld4(sx, sx_ + ro); ld4(sy, sy_ + ro); ld4(px, px_ + ro); ld4(py, py_ + ro);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const bool xr = j0 + c < N - 1;
+        const float mx = xr ? sx[c] + gx[c] : 0.f, my = sy[c] + gy[c];
+        float p1x, p1y;
+        proj2(px[c] + P.sigma * mx, py[c] + P.sigma * my, p1x, p1y);
+        syu[c] = my - P.tau * (2.f * p1y - py[c]);
+      }
     } else {
-      const float2 w = __ldg(&wq[k]);
-      float4 vk, vn;
-      fwd_post(b0[padi(k)], b0[padi(N - k)], w, vk.x, vn.x, vk.y, vn.y);
-      fwd_post(b1[padi(k)], b1[padi(N - k)], w, vk.z, vn.z, vk.w, vn.w);
-      *reinterpret_cast<float4*>(o + 4 * k) = vk;
-      *reinterpret_cast<float4*>(o + 4 * (N - k)) = vn;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) syu[c] = 0.f;
+    }
+    float dprev[4];  // d' of the block's even row, written with its odd partner
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + r;
+      const size_t ro = (size_t)i * N + j0;
+      float gx[5], gy[5], sx[5], sy[5], px[5], py[5];  // [0]: column j0 - 1
+      ld4(&gx[1], gx_ + ro); ld4(&gy[1], gy_ + ro); ld4(&sx[1], sx_ + ro);
+      ld4(&sy[1], sy_ + ro); ld4(&px[1], px_ + ro); ld4(&py[1], py_ + ro);
+      if (j0 > 0) {
+        gx[0] = gx_[ro - 1]; gy[0] = gy_[ro - 1]; sx[0] = sx_[ro - 1];
+        sy[0] = sy_[ro - 1]; px[0] = px_[ro - 1]; py[0] = py_[ro - 1];
+      } else {
+        gx[0] = gy[0] = sx[0] = sy[0] = px[0] = py[0] = 0.f;
+      }
+      float gv[4];
+      ld4(gv, g + ro);
+      float p1x[5], p1y[5], snx[5], sny[5];
+#pragma unroll
+      for (int c = 0; c <= 4; ++c) {
+        const bool xr = j0 - 1 + c < N - 1, yd = i < N - 1;
+        const float mx = xr ? sx[c] + gx[c] : 0.f, my = yd ? sy[c] + gy[c] : 0.f;
+        proj2(px[c] + P.sigma * mx, py[c] + P.sigma * my, p1x[c], p1y[c]);
+        if (!xr) p1x[c] = 0.f;
+        if (!yd) p1y[c] = 0.f;
+        snx[c] = xr ? mx - P.tau * (2.f * p1x[c] - px[c]) : 0.f;
+        sny[c] = yd ? my - P.tau * (2.f * p1y[c] - py[c]) : 0.f;
+      }
+      float od[4];
+#pragma unroll
+      for (int c = 1; c <= 4; ++c) {
+        const bool xl = j0 + c - 1 > 0, yu = i > 0;
+        const float divs = (snx[c] - (xl ? snx[c - 1] : 0.f) + sny[c] - (yu ? syu[c - 1] : 0.f)) * P.invh;
+        od[c - 1] = gv[c - 1] - divs;
+      }
+      st4(sout + ro, &snx[1]);
+      st4(sout + NN + ro, &sny[1]);
+      st4(pout + ro, &p1x[1]);
+      st4(pout + NN + ro, &p1y[1]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) syu[c] = sny[c + 1];
+      if (r & 1) {
+        scatter4(smem + (r >> 1) * PADN, j0, N, make_float4(dprev[0], dprev[1], dprev[2], dprev[3]),
+                 make_float4(od[0], od[1], od[2], od[3]));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dprev[c] = od[c];
+      }
     }
   }
+  __syncthreads();
+  rows_fwd_tail<LOG2N>(smem, out, rb, tw, wq);
+}
+
+// ROF (section 3.1): p' = proj(p + sigma grad u), pbar = 2 p' - p,
+//   r' = lambda tau I + tau div pbar - div grad u.
+template <int LOG2N>
+__global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
+    k_rof_step_rows_fwd(const float* __restrict__ gu, const float* __restrict__ pin, const float* __restrict__ I,
+                        float* __restrict__ pout, float* __restrict__ out, const float2* __restrict__ tw,
+                        const float2* __restrict__ wq, RofParams P) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, NT = 2 * C::TPF;
+  constexpr size_t NN = (size_t)N * N;
+  extern __shared__ float2 smem[];
+  const int rb = blockIdx.x, i0 = 4 * rb;
+  const float* __restrict__ gx_ = gu;
+  const float* __restrict__ gy_ = gu + NN;
+  const float* __restrict__ px_ = pin;
+  const float* __restrict__ py_ = pin + NN;
+#pragma unroll 1
+  for (int ch = 0; ch < N / (4 * NT); ++ch) {
+    const int j0 = 4 * ((int)threadIdx.x + ch * NT);
+    float pbu[4], gyu[4];  // pbar_y and (grad u)_y of the row above
+    if (i0 > 0) {
+      const size_t ro = (size_t)(i0 - 1) * N + j0;
+      float gx[4], px[4], py[4];
+      ld4(gx, gx_ + ro); ld4(gyu, gy_ + ro); ld4(px, px_ + ro); ld4(py, py_ + ro);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float p1x, p1y;
+        proj2(px[c] + P.sigma * gx[c], py[c] + P.sigma * gyu[c], p1x, p1y);
+        pbu[c] = 2.f * p1y - py[c];
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) pbu[c] = gyu[c] = 0.f;
+    }
+    float rprev[4];
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + r;
+      const size_t ro = (size_t)i * N + j0;
+      float gx[5], gy[5], px[5], py[5];  // [0]: column j0 - 1
+      ld4(&gx[1], gx_ + ro); ld4(&gy[1], gy_ + ro); ld4(&px[1], px_ + ro); ld4(&py[1], py_ + ro);
+      if (j0 > 0) {
+        gx[0] = gx_[ro - 1]; gy[0] = gy_[ro - 1]; px[0] = px_[ro - 1]; py[0] = py_[ro - 1];
+      } else {
+        gx[0] = gy[0] = px[0] = py[0] = 0.f;
+      }
+      float Iv[4];
+      ld4(Iv, I + ro);
+      float p1x[5], p1y[5], pbx[5], pby[5];
+#pragma unroll
+      for (int c = 0; c <= 4; ++c) {
+        const bool xr = j0 - 1 + c < N - 1, yd = i < N - 1;
+        proj2(px[c] + P.sigma * gx[c], py[c] + P.sigma * gy[c], p1x[c], p1y[c]);
+        if (!xr) p1x[c] = 0.f;
+        if (!yd) p1y[c] = 0.f;
+        pbx[c] = 2.f * p1x[c] - (xr ? px[c] : 0.f);
+        pby[c] = 2.f * p1y[c] - (yd ? py[c] : 0.f);
+      }
+      float rv[4];
+#pragma unroll
+      for (int c = 1; c <= 4; ++c) {
+        const bool xl = j0 + c - 1 > 0, yu = i > 0;
+        const float dpb = (pbx[c] - (xl ? pbx[c - 1] : 0.f) + pby[c] - (yu ? pbu[c - 1] : 0.f)) * P.invh;
+        const float lap = (gx[c] - (xl ? gx[c - 1] : 0.f) + gy[c] - (yu ? gyu[c - 1] : 0.f)) * P.invh;
+        rv[c - 1] = P.lt * Iv[c - 1] + P.tau * dpb - lap;
+      }
+      st4(pout + ro, &p1x[1]);
+      st4(pout + NN + ro, &p1y[1]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        pbu[c] = pby[c + 1];
+        gyu[c] = gy[c + 1];
+      }
+      if (r & 1) {
+        scatter4(smem + (r >> 1) * PADN, j0, N, make_float4(rprev[0], rprev[1], rprev[2], rprev[3]),
+                 make_float4(rv[0], rv[1], rv[2], rv[3]));
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) rprev[c] = rv[c];
+      }
+    }
+  }
+  __syncthreads();
+  rows_fwd_tail<LOG2N>(smem, out, rb, tw, wq);
 }
 
 // Load the two columns (2cp, 2cp+1) of the interleaved layout into one
@@ -822,6 +1035,29 @@ cudaError_t launch_grad_rows(const DctPlan& p, const float* A, const float* B, f
   return cudaGetLastError();
 }
 
+template <int LOG2N>
+cudaError_t launch_emd_step_fwd(const DctPlan& p, const float* gq, const float* sin_, const float* pin,
+                                const float* g, float* sout, float* pout, float* out, const EmdParams& P,
+                                cudaStream_t st) {
+  using C = FftCfg<LOG2N>;
+  const size_t sm = 2 * (size_t)C::PADN * sizeof(float2);
+  cudaError_t e;
+  if ((e = set_smem(k_emd_step_rows_fwd<LOG2N>, sm))) return e;
+  k_emd_step_rows_fwd<LOG2N><<<C::N / 4, 2 * C::TPF, sm, st>>>(gq, sin_, pin, g, sout, pout, out, p.tw, p.wq, P);
+  return cudaGetLastError();
+}
+
+template <int LOG2N>
+cudaError_t launch_rof_step_fwd(const DctPlan& p, const float* gu, const float* pin, const float* I, float* pout,
+                                float* out, const RofParams& P, cudaStream_t st) {
+  using C = FftCfg<LOG2N>;
+  const size_t sm = 2 * (size_t)C::PADN * sizeof(float2);
+  cudaError_t e;
+  if ((e = set_smem(k_rof_step_rows_fwd<LOG2N>, sm))) return e;
+  k_rof_step_rows_fwd<LOG2N><<<C::N / 4, 2 * C::TPF, sm, st>>>(gu, pin, I, pout, out, p.tw, p.wq, P);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ dense path
 // D = op(A) * op(B), all N x N row-major; op = transpose when the flag is set.
 template <bool TA, bool TB>
@@ -928,6 +1164,22 @@ cudaError_t dct_grad_rows(const DctPlan& p, const float* A, const float* B, floa
                           cudaStream_t st) {
   if (!p.fft) return cudaErrorInvalidValue;
 #define GP_CALL(L) launch_grad_rows<L>(p, A, B, gx, gy, phi, st)
+  GP_FFT_DISPATCH(p.N, GP_CALL)
+#undef GP_CALL
+}
+
+cudaError_t dct_emd_step_fwd(const DctPlan& p, const float* gq, const float* sin_, const float* pin, const float* g,
+                             float* sout, float* pout, float* out, const EmdParams& P, cudaStream_t st) {
+  if (!p.fft || P.N != p.N) return cudaErrorInvalidValue;
+#define GP_CALL(L) launch_emd_step_fwd<L>(p, gq, sin_, pin, g, sout, pout, out, P, st)
+  GP_FFT_DISPATCH(p.N, GP_CALL)
+#undef GP_CALL
+}
+
+cudaError_t dct_rof_step_fwd(const DctPlan& p, const float* gu, const float* pin, const float* I, float* pout,
+                             float* out, const RofParams& P, cudaStream_t st) {
+  if (!p.fft || P.N != p.N) return cudaErrorInvalidValue;
+#define GP_CALL(L) launch_rof_step_fwd<L>(p, gu, pin, I, pout, out, P, st)
   GP_FFT_DISPATCH(p.N, GP_CALL)
 #undef GP_CALL
 }

@@ -66,6 +66,17 @@ cudaError_t dct_grad_cols(const DctPlan& p, const float* in, float* A, float* B,
                           cudaStream_t st);
 cudaError_t dct_grad_rows(const DctPlan& p, const float* A, const float* B, float* gx, float* gy, float* phi,
                           cudaStream_t st);
+// One non-gap iteration's stencil (k_emd_fused / k_rof_fused arithmetic)
+// fused with the forward row pass of the next solve: writes s', p' (EMD) or
+// p' (ROF) and, instead of the right-hand side itself, its row spectra `out`
+// in the interleaved layout of pass 0.  Fast sizes only; all pointers
+// 16-byte aligned.
+struct EmdParams;
+struct RofParams;
+cudaError_t dct_emd_step_fwd(const DctPlan& p, const float* gq, const float* sin_, const float* pin, const float* g,
+                             float* sout, float* pout, float* out, const EmdParams& P, cudaStream_t st);
+cudaError_t dct_rof_step_fwd(const DctPlan& p, const float* gu, const float* pin, const float* I, float* pout,
+                             float* out, const RofParams& P, cudaStream_t st);
 // Build C (and C^T) for a plan that lacks them (tensor-core path).
 cudaError_t dct_plan_dense(DctPlan& p);
 // Split-precision (hi + lo BF16) tensor-core form, N % 128 == 0: four tcgen05

@@ -66,18 +66,6 @@ __device__ __forceinline__ void load_row(float (&w)[V + 2], const float* __restr
   w[V + 1] = j0 + V < N ? r[j0 + V] : 0.f;
 }
 
-__device__ __forceinline__ void proj2(float qx, float qy, float& px, float& py) {
-  const float n2 = qx * qx + qy * qy;
-  if (n2 > 1.f) {
-    const float s = rsqrtf(n2);
-    px = qx * s;
-    py = qy * s;
-  } else {
-    px = qx;
-    py = qy;
-  }
-}
-
 // Block reduction of NQ doubles; op bit q set = max, else sum.  Thread 0 writes
 // the block's partials to part[block * NQ + q].
 template <int NQ>

@@ -19,6 +19,20 @@ struct EmdParams {
   float tau, sigma;
 };
 
+// Pointwise projection of the dual variable onto the unit disc (the
+// proximal step of the dual's constraint |p| <= 1, sections 3.1 / 3.2).
+__device__ __forceinline__ void proj2(float qx, float qy, float& px, float& py) {
+  const float n2 = qx * qx + qy * qy;
+  if (n2 > 1.f) {
+    const float s = rsqrtf(n2);
+    px = qx * s;
+    py = qy * s;
+  } else {
+    px = qx;
+    py = qy;
+  }
+}
+
 // rb: row-block height of the fused kernels (4, 8, 16 or 32; anything else -> 16)
 dim3 fused_grid(int N, int V, int rb);
 int reduce_blocks_1d(size_t n);
