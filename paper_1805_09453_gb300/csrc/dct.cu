@@ -28,6 +28,7 @@
 // potential loses about log2(N) bits).
 //
 // Dense path (any N): four FP32 GEMMs with the orthonormal DCT-II matrix.
+#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <math.h>
 
 #include <vector>
@@ -885,6 +886,190 @@ __global__ void __launch_bounds__((PAR ? 3 : 1) * FftCfg<LOG2N>::TPF, (LOG2N == 
   }
 }
 
+// ------------------------------------- column pass, gradient, bulk tensor copies
+// The interleaved spectra seen as a 3-D tensor {4 rows, N columns, N/4 row
+// blocks} (strides 16 B and 16N B): a column pair is 32 B per row block, so a
+// thread-per-row-block load or store touches one cache line per lane (32
+// lines per warp instruction).  Here the tensor-memory-access engine moves
+// the column pair in (one box of up to 256 row blocks per copy, counted on an
+// mbarrier) and each synthesis out (staged in the transform buffer, one bulk
+// tensor store per box), and the threads only touch shared memory.
+constexpr uint32_t kTmaWaitLimit = 1u << 22;  // try_wait rounds before a copy is declared lost
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kTmaWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int c0, int c1, int c2, uint32_t src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                   reinterpret_cast<uint64_t>(tm)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(src)
+               : "memory");
+}
+
+// Same computation as k_dct_cols_grad (non-PAR form).  tm_in: box {4, 2, BOXR}
+// over `in`; tm_a: box {4, 2, BOXR} over A; tm_b: box {4, 1, BOXR} over B.
+// A copy that never lands (bounded wait) poisons the column pair with NaN and
+// sets *err, so the solve reports a non-finite iterate instead of hanging.
+template <int LOG2N>
+__global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
+    k_dct_cols_grad_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_a,
+                        const __grid_constant__ CUtensorMap tm_b, const float2* __restrict__ tw,
+                        const float2* __restrict__ wq, const float* __restrict__ mu, float alpha, float sN2,
+                        int* __restrict__ err) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  constexpr int BOXR = N / 4 < 256 ? N / 4 : 256, NBOX = (N / 4) / BOXR;
+  constexpr int RBT = (N / 4) / TPF;  // row blocks per thread
+  extern __shared__ __align__(128) float2 smem_tma[];
+  float2* buf = smem_tma;
+  float2* X = smem_tma + PADN;  // staged column pair, then the gained spectra
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(X + N);
+  float* stage = reinterpret_cast<float*>(buf);
+  const int cp = blockIdx.x, t = threadIdx.x;
+  const float fN = (float)N;
+  const uint32_t bar = smem_addr(mbar);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)(N * 8))
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < NBOX; ++q) tma_load_3d(smem_addr(X) + q * BOXR * 32, &tm_in, 0, 2 * cp, q * BOXR, bar);
+  }
+  StageTw<LOG2N> stw;
+  stw.load(tw, t);
+  float poison = 1.f;
+  if (!mbar_try(bar, 0)) {
+    poison = __int_as_float(0x7fc00000);
+    atomicExch(err, 1);
+  }
+  {
+    const float* Xs = reinterpret_cast<const float*>(X);
+#pragma unroll
+    for (int ii = 0; ii < RBT; ++ii) {
+      const int rb = t + ii * TPF;
+      const float4 a = *reinterpret_cast<const float4*>(Xs + rb * 8);
+      const float4 b = *reinterpret_cast<const float4*>(Xs + rb * 8 + 4);
+      const int n = 4 * rb;
+      buf[padi(mk_pos(n, N))] = make_float2(poison * a.x, poison * b.x);
+      buf[padi(mk_pos(n + 1, N))] = make_float2(poison * a.y, poison * b.y);
+      buf[padi(mk_pos(n + 2, N))] = make_float2(poison * a.z, poison * b.z);
+      buf[padi(mk_pos(n + 3, N))] = make_float2(poison * a.w, poison * b.w);
+    }
+  }
+  __syncthreads();
+  fft_smem_tw<LOG2N, -1, TPF>(buf, t, tw, stw);
+  col_spectrum<N, TPF>(buf, X, cp, t, wq, mu, alpha, sN2);
+  __syncthreads();
+#pragma unroll 1
+  for (int pass = 0; pass < 3; ++pass) {
+#pragma unroll
+    for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
+      if (kk == (N / 2) / TPF && t != 0) break;
+      const int k = t + kk * TPF;
+      const float2 xk = X[k];
+      if (pass == 0) {
+        if (k == 0) {
+          buf[0] = xk;
+        } else if (k == N / 2) {
+          buf[padi(k)] = make_float2(kSqrt2 * xk.x, kSqrt2 * xk.y);
+        } else {
+          const float2 xn = X[N - k];
+          float2 zk, zn;
+          inv_pre(xk.x, xn.x, xk.y, xn.y, __ldg(&wq[k]), zk, zn);
+          buf[padi(k)] = zk;
+          buf[padi(N - k)] = zn;
+        }
+      } else {
+        const float x0 = pass == 1 ? xk.x : xk.y;
+        if (k == 0) {
+          buf[0] = make_float2(0.f, 0.f);
+        } else if (k == N / 2) {
+          buf[padi(k)] = make_float2(-kSqrt2 * x0, kSqrt2 * x0);
+        } else {
+          const float2 xn2 = X[N - k];
+          float2 zk, zn;
+          deriv_pre(x0, pass == 1 ? xn2.x : xn2.y, __ldg(&wq[k]), zk, zn);
+          buf[padi(k)] = zk;
+          buf[padi(N - k)] = zn;
+        }
+      }
+    }
+    __syncthreads();
+    fft_smem_tw<LOG2N, +1, TPF>(buf, t, tw, stw);
+    // this thread's row blocks: read out of the transform buffer, then staged
+    // over it as {row block, column(s), 4 rows} for the tensor store
+    float4 va[RBT], vb[RBT];
+#pragma unroll
+    for (int ii = 0; ii < RBT; ++ii) {
+      const int n = 4 * (t + ii * TPF);
+      const float2 z0 = buf[padi(mk_pos(n, N))], z1 = buf[padi(mk_pos(n + 1, N))];
+      const float2 z2 = buf[padi(mk_pos(n + 2, N))], z3 = buf[padi(mk_pos(n + 3, N))];
+      if (pass == 0) {
+        va[ii] = make_float4(z0.x, z1.x, z2.x, z3.x);
+        vb[ii] = make_float4(z0.y, z1.y, z2.y, z3.y);
+      } else {  // D_y: N (S_c(P) - (-1)^n S_c(Q)), zero-flux slot at n = N-1
+        va[ii] = make_float4(fN * (z0.x - z0.y), fN * (z1.x + z1.y), fN * (z2.x - z2.y),
+                             n + 3 == N - 1 ? 0.f : fN * (z3.x + z3.y));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ii = 0; ii < RBT; ++ii) {
+      const int rb = t + ii * TPF;
+      if (pass == 0) {
+        *reinterpret_cast<float4*>(stage + rb * 8) = va[ii];
+        *reinterpret_cast<float4*>(stage + rb * 8 + 4) = vb[ii];
+      } else {
+        *reinterpret_cast<float4*>(stage + rb * 4) = va[ii];
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+#pragma unroll
+      for (int q = 0; q < NBOX; ++q) {
+        if (pass == 0)
+          tma_store_3d(&tm_a, 0, 2 * cp, q * BOXR, smem_addr(stage) + q * BOXR * 32);
+        else
+          tma_store_3d(&tm_b, 0, 2 * cp + pass - 1, q * BOXR, smem_addr(stage) + q * BOXR * 16);
+      }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the buffer is reused next pass
+    }
+    __syncthreads();
+  }
+  if (t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
 // ------------------------------------------------------ row pass, gradient
 // CTA = one block of 4 rows (two transform slots).  Per slot f (rows
 // r0 = 4 rb + 2f and r0 + 1):
@@ -916,35 +1101,86 @@ __global__ void __launch_bounds__((PAR ? 8 : 2) * FftCfg<LOG2N>::TPF, (LOG2N == 
   for (int pass = p0; pass < (PAR ? p0 + 1 : npass); ++pass) {
     // pass 0: D_x of A row r0; 1: D_x of A row r0+1; 2: plain of B rows r0, r0+1; 3: plain of A rows
     const float* __restrict__ src = (pass == 2 ? B : A) + (size_t)rb * 4 * N;
+    if constexpr (!PAR) {
+      // both slots' pre-steps at once: one float4 (the block's 4 rows at column k) per load
+      float2* b0 = smem;
+      float2* b1 = smem + PADN;
 #pragma unroll
-    for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
-      if (kk == (N / 2) / TPF && t != 0) break;
-      const int k = t + kk * TPF;
-      const float2 xk2 = *reinterpret_cast<const float2*>(src + 4 * k + 2 * f);
-      if (pass < 2) {
-        const float xk = pass == 0 ? xk2.x : xk2.y;
-        if (k == 0) {
-          buf[0] = make_float2(0.f, 0.f);
-        } else if (k == N / 2) {
-          buf[padi(k)] = make_float2(-kSqrt2 * xk, kSqrt2 * xk);
+      for (int kk = 0; kk <= (N / 2) / (2 * TPF); ++kk) {  // k = tid + kk 2TPF covers [0, N/2]
+        if (kk == (N / 2) / (2 * TPF) && threadIdx.x != 0) break;
+        const int k = (int)threadIdx.x + kk * 2 * TPF;
+        const float4 xk = *reinterpret_cast<const float4*>(src + 4 * k);
+        if (pass < 2) {
+          const float a0 = pass == 0 ? xk.x : xk.y, a1 = pass == 0 ? xk.z : xk.w;
+          if (k == 0) {
+            b0[0] = make_float2(0.f, 0.f);
+            b1[0] = make_float2(0.f, 0.f);
+          } else if (k == N / 2) {
+            b0[padi(k)] = make_float2(-kSqrt2 * a0, kSqrt2 * a0);
+            b1[padi(k)] = make_float2(-kSqrt2 * a1, kSqrt2 * a1);
+          } else {
+            const float4 xn = *reinterpret_cast<const float4*>(src + 4 * (N - k));
+            const float2 w = __ldg(&wq[k]);
+            float2 zk, zn;
+            deriv_pre(a0, pass == 0 ? xn.x : xn.y, w, zk, zn);
+            b0[padi(k)] = zk;
+            b0[padi(N - k)] = zn;
+            deriv_pre(a1, pass == 0 ? xn.z : xn.w, w, zk, zn);
+            b1[padi(k)] = zk;
+            b1[padi(N - k)] = zn;
+          }
         } else {
-          const float2 xn2 = *reinterpret_cast<const float2*>(src + 4 * (N - k) + 2 * f);
-          float2 zk, zn;
-          deriv_pre(xk, pass == 0 ? xn2.x : xn2.y, __ldg(&wq[k]), zk, zn);
-          buf[padi(k)] = zk;
-          buf[padi(N - k)] = zn;
+          if (k == 0) {
+            b0[0] = make_float2(xk.x, xk.y);
+            b1[0] = make_float2(xk.z, xk.w);
+          } else if (k == N / 2) {
+            b0[padi(k)] = make_float2(kSqrt2 * xk.x, kSqrt2 * xk.y);
+            b1[padi(k)] = make_float2(kSqrt2 * xk.z, kSqrt2 * xk.w);
+          } else {
+            const float4 xn = *reinterpret_cast<const float4*>(src + 4 * (N - k));
+            const float2 w = __ldg(&wq[k]);
+            float2 zk, zn;
+            inv_pre(xk.x, xn.x, xk.y, xn.y, w, zk, zn);
+            b0[padi(k)] = zk;
+            b0[padi(N - k)] = zn;
+            inv_pre(xk.z, xn.z, xk.w, xn.w, w, zk, zn);
+            b1[padi(k)] = zk;
+            b1[padi(N - k)] = zn;
+          }
         }
-      } else {
-        if (k == 0) {
-          buf[0] = xk2;
-        } else if (k == N / 2) {
-          buf[padi(k)] = make_float2(kSqrt2 * xk2.x, kSqrt2 * xk2.y);
+      }
+    } else {
+      // one slot's pre-step per thread group (each group in its own buffer)
+#pragma unroll
+      for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
+        if (kk == (N / 2) / TPF && t != 0) break;
+        const int k = t + kk * TPF;
+        const float2 xk2 = *reinterpret_cast<const float2*>(src + 4 * k + 2 * f);
+        if (pass < 2) {
+          const float xk = pass == 0 ? xk2.x : xk2.y;
+          if (k == 0) {
+            buf[0] = make_float2(0.f, 0.f);
+          } else if (k == N / 2) {
+            buf[padi(k)] = make_float2(-kSqrt2 * xk, kSqrt2 * xk);
+          } else {
+            const float2 xn2 = *reinterpret_cast<const float2*>(src + 4 * (N - k) + 2 * f);
+            float2 zk, zn;
+            deriv_pre(xk, pass == 0 ? xn2.x : xn2.y, __ldg(&wq[k]), zk, zn);
+            buf[padi(k)] = zk;
+            buf[padi(N - k)] = zn;
+          }
         } else {
-          const float2 xn2 = *reinterpret_cast<const float2*>(src + 4 * (N - k) + 2 * f);
-          float2 zk, zn;
-          inv_pre(xk2.x, xn2.x, xk2.y, xn2.y, __ldg(&wq[k]), zk, zn);
-          buf[padi(k)] = zk;
-          buf[padi(N - k)] = zn;
+          if (k == 0) {
+            buf[0] = xk2;
+          } else if (k == N / 2) {
+            buf[padi(k)] = make_float2(kSqrt2 * xk2.x, kSqrt2 * xk2.y);
+          } else {
+            const float2 xn2 = *reinterpret_cast<const float2*>(src + 4 * (N - k) + 2 * f);
+            float2 zk, zn;
+            inv_pre(xk2.x, xn2.x, xk2.y, xn2.y, __ldg(&wq[k]), zk, zn);
+            buf[padi(k)] = zk;
+            buf[padi(N - k)] = zn;
+          }
         }
       }
     }
@@ -1005,11 +1241,56 @@ cudaError_t launch_fft_pass(const DctPlan& p, int pass, const float* in, float* 
   return cudaGetLastError();
 }
 
+// Tensor map of an interleaved-spectra plane as {4 rows, N columns, N/4 row
+// blocks}, box {4, ncols, min(256, N/4)}; false when the driver's encoder is
+// unavailable or refuses.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+bool encode_b4_map(CUtensorMap* m, const float* base, int N, int ncols) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn || ((uintptr_t)base & 15u)) return false;
+  const cuuint64_t dims[3] = {4, (cuuint64_t)N, (cuuint64_t)(N / 4)};
+  const cuuint64_t strides[2] = {16, (cuuint64_t)N * 16};
+  const cuuint32_t box[3] = {4, (cuuint32_t)ncols, (cuuint32_t)(N / 4 < 256 ? N / 4 : 256)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int LOG2N>
 cudaError_t launch_grad_cols(const DctPlan& p, const float* in, float* A, float* B, float alpha, float scale,
                              cudaStream_t st) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  if constexpr (LOG2N >= 11) {
+    CUtensorMap tm_in, tm_a, tm_b;
+    if (p.err && encode_b4_map(&tm_in, in, N, 2) && encode_b4_map(&tm_a, A, N, 2) && encode_b4_map(&tm_b, B, N, 1)) {
+      const size_t sm = (size_t)(PADN + N) * sizeof(float2) + 16;
+      cudaError_t e;
+      if ((e = set_smem(k_dct_cols_grad_tma<LOG2N>, sm))) return e;
+      const float sN2 = (float)((double)scale / ((double)N * (double)N));
+      k_dct_cols_grad_tma<LOG2N><<<N / 2, TPF, sm, st>>>(tm_in, tm_a, tm_b, p.tw, p.wq, p.mu, alpha, sN2, p.err);
+      return cudaGetLastError();
+    }
+  }
   // small N (one CTA's transform chain is the latency): the three syntheses in
   // parallel groups; named barriers need whole warps per group (TPF >= 32)
   constexpr bool PAR = LOG2N == 9 || LOG2N == 10;
@@ -1198,6 +1479,8 @@ cudaError_t dct_plan_init(DctPlan& p, int N) {
   if ((e = cudaMalloc(&p.mu, sizeof(float) * N))) return e;
   if ((e = cudaMemcpy(p.mu, mu.data(), sizeof(float) * N, cudaMemcpyHostToDevice))) return e;
   if (p.fft) {
+    if ((e = cudaMalloc(&p.err, sizeof(int)))) return e;
+    if ((e = cudaMemset(p.err, 0, sizeof(int)))) return e;
     std::vector<float2> tw(N), wq(N / 2 + 1);
     for (int m = 0; m < N; ++m) tw[m] = make_float2((float)cos(2 * PI * m / N), (float)-sin(2 * PI * m / N));
     for (int k = 0; k <= N / 2; ++k) wq[k] = make_float2((float)cos(PI * k / (2.0 * N)), (float)-sin(PI * k / (2.0 * N)));
@@ -1276,6 +1559,7 @@ void dct_plan_free(DctPlan& p) {
   if (p.CTs) cudaFree(p.CTs);
   if (p.Es) cudaFree(p.Es);
   if (p.ETs) cudaFree(p.ETs);
+  if (p.err) cudaFree(p.err);
   p = DctPlan();
 }
 

@@ -45,6 +45,7 @@ struct DctPlan {
   void* CTs = nullptr;
   void* Es = nullptr;
   void* ETs = nullptr;
+  int* err = nullptr;  // fast sizes: set to 1 by a transform kernel whose bulk copy never landed
 };
 
 // Launchers (dct.cu)
