@@ -419,6 +419,33 @@ __device__ __forceinline__ void rows_fwd_tail(float2* smem, float* __restrict__ 
   }
 }
 
+// The same for a CTA of TPF threads holding one row pair (rows i0, i0 + 1,
+// i0 even) in one buffer: its spectra fill half of each 4-row group.
+template <int LOG2N>
+__device__ __forceinline__ void rows_fwd_tail_pair(float2* buf, float* __restrict__ out, int i0,
+                                                   const float2* __restrict__ tw, const float2* __restrict__ wq) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, TPF = C::TPF;
+  const int t = threadIdx.x;
+  fft_smem<LOG2N, -1, TPF>(buf, t, tw);
+  float* __restrict__ o = out + (size_t)(i0 >> 2) * 4 * N + (i0 & 3);
+#pragma unroll
+  for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {
+    if (kk == (N / 2) / TPF && t != 0) break;
+    const int k = t + kk * TPF;
+    if (k == 0 || k == N / 2) {
+      const float sc = k == 0 ? 1.f : kRsqrt2;
+      const float2 z = buf[padi(k)];
+      *reinterpret_cast<float2*>(o + 4 * k) = make_float2(sc * z.x, sc * z.y);
+    } else {
+      float ak, an, bk, bn;
+      fwd_post(buf[padi(k)], buf[padi(N - k)], __ldg(&wq[k]), ak, an, bk, bn);
+      *reinterpret_cast<float2*>(o + 4 * k) = make_float2(ak, bk);
+      *reinterpret_cast<float2*>(o + 4 * (N - k)) = make_float2(an, bn);
+    }
+  }
+}
+
 // ------------------------------------------------------- row pass, forward
 // CTA = one block of 4 rows (two transforms of two rows each); input
 // row-major, output spectra in the 4-row-interleaved layout.
@@ -446,14 +473,15 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
 // ------------------------------------- stencil fused with the forward row pass
 // One non-gap iteration's pointwise / stencil update (the same arithmetic as
 // k_rof_fused and k_emd_fused, sections 3.1 / 3.2) run by the CTA of the
-// forward row pass of the next solve: the block's 4 rows are updated (dual
+// forward row pass of the next solve: the block's rows are updated (dual
 // and auxiliary variables to HBM), the new right-hand side is scattered in
-// Makhoul order straight into the two transform buffers, and the block then
-// transforms it.  The right-hand side never travels through HBM, and the
+// Makhoul order straight into the transform buffer(s) (one per row pair),
+// and the block then transforms it.  The right-hand side never travels through HBM, and the
 // transform's shared-memory work overlaps other blocks' streaming.  The row
 // above the block is recomputed from its inputs, so blocks are independent.
-// Thread layout: NT = N/8 threads, each owning 4 consecutive columns in two
-// chunks (j0 = 4 tid and j0 + N/2), walking the block's rows downwards.
+// Thread layout: a CTA of RPC rows (2 or 4) has NT = RPC/2 * N/16 threads,
+// each owning 4 consecutive columns in N/(4 NT) chunks (j0 = 4 tid + 4 NT c),
+// walking the block's rows downwards.
 // Requires every pointer 16-byte aligned (state buffers).
 
 __device__ __forceinline__ void ld4(float* d, const float* __restrict__ p) {
@@ -466,17 +494,17 @@ __device__ __forceinline__ void st4(float* __restrict__ p, const float* s) {
 
 // EMD (section 3.2, affine Leray form): with m = s + grad q,
 //   p' = proj(p + sigma m),  s' = m - tau (2 p' - p),  d' = g - div s'.
-template <int LOG2N>
-__global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
+template <int LOG2N, int RPC>
+__global__ void __launch_bounds__(RPC / 2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 8 / RPC : 1))
     k_emd_step_rows_fwd(const float* __restrict__ gq, const float* __restrict__ sin_, const float* __restrict__ pin,
                         const float* __restrict__ g, float* __restrict__ sout, float* __restrict__ pout,
                         float* __restrict__ out, const float2* __restrict__ tw, const float2* __restrict__ wq,
                         EmdParams P) {
   using C = FftCfg<LOG2N>;
-  constexpr int N = C::N, PADN = C::PADN, NT = 2 * C::TPF;
+  constexpr int N = C::N, PADN = C::PADN, NT = RPC / 2 * C::TPF;
   constexpr size_t NN = (size_t)N * N;
   extern __shared__ float2 smem[];
-  const int rb = blockIdx.x, i0 = 4 * rb;
+  const int rb = blockIdx.x, i0 = RPC * rb;
   const float* __restrict__ gx_ = gq;
   const float* __restrict__ gy_ = gq + NN;
   const float* __restrict__ sx_ = sin_;
@@ -505,7 +533,7 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
     }
     float dprev[4];  // d' of the block's even row, written with its odd partner
 #pragma unroll 1
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RPC; ++r) {
       const int i = i0 + r;
       const size_t ro = (size_t)i * N + j0;
       float gx[5], gy[5], sx[5], sy[5], px[5], py[5];  // [0]: column j0 - 1
@@ -553,21 +581,22 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
     }
   }
   __syncthreads();
-  rows_fwd_tail<LOG2N>(smem, out, rb, tw, wq);
+  if constexpr (RPC == 4) rows_fwd_tail<LOG2N>(smem, out, rb, tw, wq);
+  else rows_fwd_tail_pair<LOG2N>(smem, out, i0, tw, wq);
 }
 
 // ROF (section 3.1): p' = proj(p + sigma grad u), pbar = 2 p' - p,
 //   r' = lambda tau I + tau div pbar - div grad u.
-template <int LOG2N>
-__global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
+template <int LOG2N, int RPC>
+__global__ void __launch_bounds__(RPC / 2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 8 / RPC : 1))
     k_rof_step_rows_fwd(const float* __restrict__ gu, const float* __restrict__ pin, const float* __restrict__ I,
                         float* __restrict__ pout, float* __restrict__ out, const float2* __restrict__ tw,
                         const float2* __restrict__ wq, RofParams P) {
   using C = FftCfg<LOG2N>;
-  constexpr int N = C::N, PADN = C::PADN, NT = 2 * C::TPF;
+  constexpr int N = C::N, PADN = C::PADN, NT = RPC / 2 * C::TPF;
   constexpr size_t NN = (size_t)N * N;
   extern __shared__ float2 smem[];
-  const int rb = blockIdx.x, i0 = 4 * rb;
+  const int rb = blockIdx.x, i0 = RPC * rb;
   const float* __restrict__ gx_ = gu;
   const float* __restrict__ gy_ = gu + NN;
   const float* __restrict__ px_ = pin;
@@ -592,7 +621,7 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
     }
     float rprev[4];
 #pragma unroll 1
-    for (int r = 0; r < 4; ++r) {
+    for (int r = 0; r < RPC; ++r) {
       const int i = i0 + r;
       const size_t ro = (size_t)i * N + j0;
       float gx[5], gy[5], px[5], py[5];  // [0]: column j0 - 1
@@ -639,7 +668,8 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
     }
   }
   __syncthreads();
-  rows_fwd_tail<LOG2N>(smem, out, rb, tw, wq);
+  if constexpr (RPC == 4) rows_fwd_tail<LOG2N>(smem, out, rb, tw, wq);
+  else rows_fwd_tail_pair<LOG2N>(smem, out, i0, tw, wq);
 }
 
 // Load the two columns (2cp, 2cp+1) of the interleaved layout into one
@@ -1316,15 +1346,26 @@ cudaError_t launch_grad_rows(const DctPlan& p, const float* A, const float* B, f
   return cudaGetLastError();
 }
 
+// Rows per CTA of the fused step kernels.  EMD: 2 (one transform of TPF
+// threads, four CTAs per SM at N = 4096, so that co-resident CTAs drift out
+// of phase and one's stencil streaming overlaps another's transform; 158 ->
+// 151 us at 4096^2).  ROF, with fewer bytes per point, loses more to the
+// extra recomputed row above each 2-row block than it gains (107 -> 116 us):
+// 4.
+constexpr int kEmdStepRowsPerCta = 2;
+constexpr int kRofStepRowsPerCta = 4;
+
 template <int LOG2N>
 cudaError_t launch_emd_step_fwd(const DctPlan& p, const float* gq, const float* sin_, const float* pin,
                                 const float* g, float* sout, float* pout, float* out, const EmdParams& P,
                                 cudaStream_t st) {
   using C = FftCfg<LOG2N>;
-  const size_t sm = 2 * (size_t)C::PADN * sizeof(float2);
+  constexpr int RPC = kEmdStepRowsPerCta;
+  const size_t sm = RPC / 2 * (size_t)C::PADN * sizeof(float2);
   cudaError_t e;
-  if ((e = set_smem(k_emd_step_rows_fwd<LOG2N>, sm))) return e;
-  k_emd_step_rows_fwd<LOG2N><<<C::N / 4, 2 * C::TPF, sm, st>>>(gq, sin_, pin, g, sout, pout, out, p.tw, p.wq, P);
+  if ((e = set_smem(k_emd_step_rows_fwd<LOG2N, RPC>, sm))) return e;
+  k_emd_step_rows_fwd<LOG2N, RPC>
+      <<<C::N / RPC, RPC / 2 * C::TPF, sm, st>>>(gq, sin_, pin, g, sout, pout, out, p.tw, p.wq, P);
   return cudaGetLastError();
 }
 
@@ -1332,10 +1373,11 @@ template <int LOG2N>
 cudaError_t launch_rof_step_fwd(const DctPlan& p, const float* gu, const float* pin, const float* I, float* pout,
                                 float* out, const RofParams& P, cudaStream_t st) {
   using C = FftCfg<LOG2N>;
-  const size_t sm = 2 * (size_t)C::PADN * sizeof(float2);
+  constexpr int RPC = kRofStepRowsPerCta;
+  const size_t sm = RPC / 2 * (size_t)C::PADN * sizeof(float2);
   cudaError_t e;
-  if ((e = set_smem(k_rof_step_rows_fwd<LOG2N>, sm))) return e;
-  k_rof_step_rows_fwd<LOG2N><<<C::N / 4, 2 * C::TPF, sm, st>>>(gu, pin, I, pout, out, p.tw, p.wq, P);
+  if ((e = set_smem(k_rof_step_rows_fwd<LOG2N, RPC>, sm))) return e;
+  k_rof_step_rows_fwd<LOG2N, RPC><<<C::N / RPC, RPC / 2 * C::TPF, sm, st>>>(gu, pin, I, pout, out, p.tw, p.wq, P);
   return cudaGetLastError();
 }
 
