@@ -961,34 +961,40 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int c0, int 
                : "memory");
 }
 
-// Same computation as k_dct_cols_grad (non-PAR form).  tm_in: box {4, 2, BOXR}
-// over `in`; tm_a: box {4, 2, BOXR} over A; tm_b: box {4, 1, BOXR} over B.
-// A copy that never lands (bounded wait) poisons the column pair with NaN and
-// sets *err, so the solve reports a non-finite iterate instead of hanging.
-template <int LOG2N>
-__global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
+// Same computation as k_dct_cols_grad.  tm_in: box {4, 2, BOXR} over `in`;
+// tm_a: box {4, 2, BOXR} over A; tm_b: box {4, 1, BOXR} over B.  PAR (N = 512,
+// 1024): three groups of TPF threads run the three syntheses at once, each in
+// its own buffer on its own named barrier, each staging and storing its own
+// output.  A copy that never lands (bounded wait) poisons the column pair with
+// NaN and sets *err, so the solve reports a non-finite iterate instead of
+// hanging.
+template <int LOG2N, bool PAR>
+__global__ void __launch_bounds__((PAR ? 3 : 1) * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
     k_dct_cols_grad_tma(const __grid_constant__ CUtensorMap tm_in, const __grid_constant__ CUtensorMap tm_a,
                         const __grid_constant__ CUtensorMap tm_b, const float2* __restrict__ tw,
                         const float2* __restrict__ wq, const float* __restrict__ mu, float alpha, float sN2,
                         int* __restrict__ err) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  constexpr int NG = PAR ? 3 : 1;
   constexpr int BOXR = N / 4 < 256 ? N / 4 : 256, NBOX = (N / 4) / BOXR;
   constexpr int RBT = (N / 4) / TPF;  // row blocks per thread
   extern __shared__ __align__(128) float2 smem_tma[];
-  float2* buf = smem_tma;
-  float2* X = smem_tma + PADN;  // staged column pair, then the gained spectra
+  const int grp = PAR ? (int)threadIdx.x / TPF : 0, t = (int)threadIdx.x % TPF;
+  float2* buf = smem_tma + grp * PADN;
+  float2* X = smem_tma + NG * PADN;  // staged column pair, then the gained spectra
   uint64_t* mbar = reinterpret_cast<uint64_t*>(X + N);
   float* stage = reinterpret_cast<float*>(buf);
-  const int cp = blockIdx.x, t = threadIdx.x;
+  const int cp = blockIdx.x;
   const float fN = (float)N;
   const uint32_t bar = smem_addr(mbar);
-  if (t == 0) {
+  const int gbar = PAR ? grp + 1 : 0;  // this group's barrier
+  if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (t == 0) {
+  if (threadIdx.x == 0) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)(N * 8))
                  : "memory");
 #pragma unroll
@@ -996,12 +1002,12 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
   }
   StageTw<LOG2N> stw;
   stw.load(tw, t);
-  float poison = 1.f;
-  if (!mbar_try(bar, 0)) {
-    poison = __int_as_float(0x7fc00000);
-    atomicExch(err, 1);
-  }
-  {
+  if (grp == 0) {
+    float poison = 1.f;
+    if (!mbar_try(bar, 0)) {
+      poison = __int_as_float(0x7fc00000);
+      atomicExch(err, 1);
+    }
     const float* Xs = reinterpret_cast<const float*>(X);
 #pragma unroll
     for (int ii = 0; ii < RBT; ++ii) {
@@ -1014,13 +1020,13 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
       buf[padi(mk_pos(n + 2, N))] = make_float2(poison * a.z, poison * b.z);
       buf[padi(mk_pos(n + 3, N))] = make_float2(poison * a.w, poison * b.w);
     }
+    gsync(gbar, TPF);
+    fft_smem_tw<LOG2N, -1, TPF>(buf, t, tw, stw, gbar);
+    col_spectrum<N, TPF>(buf, X, cp, t, wq, mu, alpha, sN2);
   }
   __syncthreads();
-  fft_smem_tw<LOG2N, -1, TPF>(buf, t, tw, stw);
-  col_spectrum<N, TPF>(buf, X, cp, t, wq, mu, alpha, sN2);
-  __syncthreads();
 #pragma unroll 1
-  for (int pass = 0; pass < 3; ++pass) {
+  for (int pass = PAR ? grp : 0; pass < (PAR ? grp + 1 : 3); ++pass) {
 #pragma unroll
     for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {  // k = t + kk TPF covers [0, N/2]; k = N/2 only for t = 0
       if (kk == (N / 2) / TPF && t != 0) break;
@@ -1053,8 +1059,8 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
         }
       }
     }
-    __syncthreads();
-    fft_smem_tw<LOG2N, +1, TPF>(buf, t, tw, stw);
+    gsync(gbar, TPF);
+    fft_smem_tw<LOG2N, +1, TPF>(buf, t, tw, stw, gbar);
     // this thread's row blocks: read out of the transform buffer, then staged
     // over it as {row block, column(s), 4 rows} for the tensor store
     float4 va[RBT], vb[RBT];
@@ -1071,7 +1077,7 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
                              n + 3 == N - 1 ? 0.f : fN * (z3.x + z3.y));
       }
     }
-    __syncthreads();
+    gsync(gbar, TPF);
 #pragma unroll
     for (int ii = 0; ii < RBT; ++ii) {
       const int rb = t + ii * TPF;
@@ -1083,7 +1089,7 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    gsync(gbar, TPF);
     if (t == 0) {
 #pragma unroll
       for (int q = 0; q < NBOX; ++q) {
@@ -1095,9 +1101,94 @@ __global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 3 : 1))
       asm volatile("cp.async.bulk.commit_group;" ::: "memory");
       asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the buffer is reused next pass
     }
-    __syncthreads();
+    gsync(gbar, TPF);
   }
   if (t == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Column pass of the plain solve on bulk tensor copies, in place on the
+// interleaved spectra (same computation as k_dct_cols_solve): the column
+// pair arrives staged in the transform buffer, each thread takes its row
+// blocks into registers before the Makhoul scatter overwrites it, and the
+// result leaves the same way through a staging copy and a tensor store.
+// tm: box {4, 2, BOXR} over `data`.
+template <int LOG2N>
+__global__ void __launch_bounds__(FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 4 : 1))
+    k_dct_cols_solve_tma(const __grid_constant__ CUtensorMap tm, const float2* __restrict__ tw,
+                         const float2* __restrict__ wq, const float* __restrict__ mu, float alpha, float sN2,
+                         int* __restrict__ err) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  constexpr int BOXR = N / 4 < 256 ? N / 4 : 256, NBOX = (N / 4) / BOXR;
+  constexpr int RBT = (N / 4) / TPF;
+  extern __shared__ __align__(128) float2 smem_tma[];
+  float2* buf = smem_tma;
+  float* stage = reinterpret_cast<float*>(buf);
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem_tma + PADN);
+  const int cp = blockIdx.x, t = threadIdx.x;
+  const uint32_t bar = smem_addr(mbar);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"((uint32_t)(N * 8))
+                 : "memory");
+#pragma unroll
+    for (int q = 0; q < NBOX; ++q) tma_load_3d(smem_addr(stage) + q * BOXR * 32, &tm, 0, 2 * cp, q * BOXR, bar);
+  }
+  StageTw<LOG2N> stw;
+  stw.load(tw, t);
+  float poison = 1.f;
+  if (!mbar_try(bar, 0)) {
+    poison = __int_as_float(0x7fc00000);
+    atomicExch(err, 1);
+  }
+  float4 va[RBT], vb[RBT];
+#pragma unroll
+  for (int ii = 0; ii < RBT; ++ii) {
+    const int rb = t + ii * TPF;
+    va[ii] = *reinterpret_cast<const float4*>(stage + rb * 8);
+    vb[ii] = *reinterpret_cast<const float4*>(stage + rb * 8 + 4);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ii = 0; ii < RBT; ++ii) {
+    const int n = 4 * (t + ii * TPF);
+    buf[padi(mk_pos(n, N))] = make_float2(poison * va[ii].x, poison * vb[ii].x);
+    buf[padi(mk_pos(n + 1, N))] = make_float2(poison * va[ii].y, poison * vb[ii].y);
+    buf[padi(mk_pos(n + 2, N))] = make_float2(poison * va[ii].z, poison * vb[ii].z);
+    buf[padi(mk_pos(n + 3, N))] = make_float2(poison * va[ii].w, poison * vb[ii].w);
+  }
+  __syncthreads();
+  fft_smem_tw<LOG2N, -1, TPF>(buf, t, tw, stw);
+  col_spectrum<N, TPF>(buf, nullptr, cp, t, wq, mu, alpha, sN2);
+  __syncthreads();
+  fft_smem_tw<LOG2N, +1, TPF>(buf, t, tw, stw);
+#pragma unroll
+  for (int ii = 0; ii < RBT; ++ii) {
+    const int n = 4 * (t + ii * TPF);
+    const float2 z0 = buf[padi(mk_pos(n, N))], z1 = buf[padi(mk_pos(n + 1, N))];
+    const float2 z2 = buf[padi(mk_pos(n + 2, N))], z3 = buf[padi(mk_pos(n + 3, N))];
+    va[ii] = make_float4(z0.x, z1.x, z2.x, z3.x);
+    vb[ii] = make_float4(z0.y, z1.y, z2.y, z3.y);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ii = 0; ii < RBT; ++ii) {
+    const int rb = t + ii * TPF;
+    *reinterpret_cast<float4*>(stage + rb * 8) = va[ii];
+    *reinterpret_cast<float4*>(stage + rb * 8 + 4) = vb[ii];
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int q = 0; q < NBOX; ++q) tma_store_3d(&tm, 0, 2 * cp, q * BOXR, smem_addr(stage) + q * BOXR * 32);
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
 }
 
 // ------------------------------------------------------ row pass, gradient
@@ -1250,27 +1341,6 @@ cudaError_t set_smem(K k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int LOG2N>
-cudaError_t launch_fft_pass(const DctPlan& p, int pass, const float* in, float* out, float alpha, float scale,
-                            cudaStream_t st) {
-  using C = FftCfg<LOG2N>;
-  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
-  const size_t sm1 = (size_t)PADN * sizeof(float2), sm2 = 2 * sm1;
-  cudaError_t e;
-  if (pass == 0) {
-    if ((e = set_smem(k_dct_rows_fwd<LOG2N>, sm2))) return e;
-    k_dct_rows_fwd<LOG2N><<<N / 4, 2 * TPF, sm2, st>>>(in, out, p.tw, p.wq);
-  } else if (pass == 1) {
-    if ((e = set_smem(k_dct_cols_solve<LOG2N>, sm1))) return e;
-    const float sN2 = (float)((double)scale / ((double)N * (double)N));
-    k_dct_cols_solve<LOG2N><<<N / 2, TPF, sm1, st>>>(out, p.tw, p.wq, p.mu, alpha, sN2);
-  } else {
-    if ((e = set_smem(k_dct_rows_inv<LOG2N>, sm2))) return e;
-    k_dct_rows_inv<LOG2N><<<N / 4, 2 * TPF, sm2, st>>>(in, out, p.tw, p.wq);
-  }
-  return cudaGetLastError();
-}
-
 // Tensor map of an interleaved-spectra plane as {4 rows, N columns, N/4 row
 // blocks}, box {4, ncols, min(256, N/4)}; false when the driver's encoder is
 // unavailable or refuses.
@@ -1306,18 +1376,50 @@ bool encode_b4_map(CUtensorMap* m, const float* base, int N, int ncols) {
 }
 
 template <int LOG2N>
+cudaError_t launch_fft_pass(const DctPlan& p, int pass, const float* in, float* out, float alpha, float scale,
+                            cudaStream_t st) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  const size_t sm1 = (size_t)PADN * sizeof(float2), sm2 = 2 * sm1;
+  cudaError_t e;
+  if (pass == 0) {
+    if ((e = set_smem(k_dct_rows_fwd<LOG2N>, sm2))) return e;
+    k_dct_rows_fwd<LOG2N><<<N / 4, 2 * TPF, sm2, st>>>(in, out, p.tw, p.wq);
+  } else if (pass == 1) {
+    const float sN2 = (float)((double)scale / ((double)N * (double)N));
+    if constexpr (LOG2N >= 11) {
+      CUtensorMap tm;
+      if (p.err && encode_b4_map(&tm, out, N, 2)) {
+        const size_t sm = sm1 + 16;
+        if ((e = set_smem(k_dct_cols_solve_tma<LOG2N>, sm))) return e;
+        k_dct_cols_solve_tma<LOG2N><<<N / 2, TPF, sm, st>>>(tm, p.tw, p.wq, p.mu, alpha, sN2, p.err);
+        return cudaGetLastError();
+      }
+    }
+    if ((e = set_smem(k_dct_cols_solve<LOG2N>, sm1))) return e;
+    k_dct_cols_solve<LOG2N><<<N / 2, TPF, sm1, st>>>(out, p.tw, p.wq, p.mu, alpha, sN2);
+  } else {
+    if ((e = set_smem(k_dct_rows_inv<LOG2N>, sm2))) return e;
+    k_dct_rows_inv<LOG2N><<<N / 4, 2 * TPF, sm2, st>>>(in, out, p.tw, p.wq);
+  }
+  return cudaGetLastError();
+}
+
+template <int LOG2N>
 cudaError_t launch_grad_cols(const DctPlan& p, const float* in, float* A, float* B, float alpha, float scale,
                              cudaStream_t st) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
-  if constexpr (LOG2N >= 11) {
+  if constexpr (LOG2N >= 9) {
+    constexpr bool PART = LOG2N == 9 || LOG2N == 10;
     CUtensorMap tm_in, tm_a, tm_b;
     if (p.err && encode_b4_map(&tm_in, in, N, 2) && encode_b4_map(&tm_a, A, N, 2) && encode_b4_map(&tm_b, B, N, 1)) {
-      const size_t sm = (size_t)(PADN + N) * sizeof(float2) + 16;
+      const size_t sm = (size_t)((PART ? 3 : 1) * PADN + N) * sizeof(float2) + 16;
       cudaError_t e;
-      if ((e = set_smem(k_dct_cols_grad_tma<LOG2N>, sm))) return e;
+      if ((e = set_smem(k_dct_cols_grad_tma<LOG2N, PART>, sm))) return e;
       const float sN2 = (float)((double)scale / ((double)N * (double)N));
-      k_dct_cols_grad_tma<LOG2N><<<N / 2, TPF, sm, st>>>(tm_in, tm_a, tm_b, p.tw, p.wq, p.mu, alpha, sN2, p.err);
+      k_dct_cols_grad_tma<LOG2N, PART>
+          <<<N / 2, (PART ? 3 : 1) * TPF, sm, st>>>(tm_in, tm_a, tm_b, p.tw, p.wq, p.mu, alpha, sN2, p.err);
       return cudaGetLastError();
     }
   }

@@ -55,6 +55,21 @@ def test_dct2_poisson_in_place_and_full_size(h):
     assert rel_l2(bd.cpu().numpy(), ref) < 2e-5
 
 
+def test_dct2_poisson_largest_fast_size(h):
+    """8192 x 8192 (the largest fast-transform size; column pass on bulk
+    tensor copies with 8 boxes per column pair) against the FP64 oracle."""
+    from paper_1805_09453_gb300 import gprox
+
+    N = 8192
+    rng = np.random.default_rng(8192)
+    b = rng.normal(size=(N, N)).astype(np.float32)
+    ref = O.helmholtz_solve(b.astype(np.float64), 3.7, 1.0 / N)
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.empty_like(bd)
+    h.check(gprox.dct2_poisson(h, bd, xd, 3.7))
+    assert rel_l2(xd.cpu().numpy(), ref) < 2e-5
+
+
 def test_dct2_poisson_errors(h):
     from paper_1805_09453_gb300 import gprox
 
@@ -67,7 +82,7 @@ def test_dct2_poisson_errors(h):
     assert "device pointer" in h.last_error()
 
 
-@pytest.mark.parametrize("N", [7, 16, 33, 64, 128, 512, 1024, 2048, 4096])
+@pytest.mark.parametrize("N", [7, 16, 33, 64, 128, 512, 1024, 2048, 4096, 8192])
 @pytest.mark.parametrize("alpha", [0.0, 3.7])
 def test_dct2_poisson_grad_matches_oracle(h, N, alpha):
     """Spectral gradient of the solve vs the FP64 oracle's forward differences:
