@@ -72,7 +72,11 @@ typedef enum gp_prec {
 
 typedef struct gp_opts {
   int max_iters;       /* iteration cap (>= 0; default 1000) */
-  int gap_every;       /* duality-gap check every k iterations (>= 1; default 10) */
+  int gap_every;       /* duality-gap check every k iterations (>= 1; default 10); 0: adaptive
+                          (rof_solve / emd_solve with tol_rel_gap > 0): after each check the gap's
+                          decay over the last two checks, fitted as g ~ n^-a, places the next
+                          check halfway to the predicted crossing of tol_rel_gap, in chunks of
+                          10 * 2^j <= 320 iterations; batched solves take 10 */
   double tol_rel_gap;  /* stop once (P - D) / max(|P|,|D|) <= tol; <= 0: run exactly max_iters */
   double tau;          /* primal step; <= 0 selects the paper's rule (ROF section 4.1, EMD tau = 1) */
   double sigma;        /* dual step; <= 0 selects 1 / tau */
@@ -275,6 +279,18 @@ GP_API gp_status gp_autotune(gp_handle h, int N, const char* cache_path, void* s
 GP_API int gp_tuned_row_block(gp_handle h, const char* kernel, int N);
 
 /*
+ * gp_gap_schedule_next: the adaptive gap-check schedule of gap_every == 0 as
+ * a pure function, for callers driving pd_step / gp_state_gap themselves.
+ * Given the previous check (iteration n_prev, relative gap g_prev; n_prev <= 0
+ * if none) and the current one (n, g), returns the number of iterations to
+ * run before the next check: 10 * 2^j <= 320, halfway to the iteration where
+ * the fit g ~ c n^-a through the two checks reaches tol; 10 when there is no
+ * decrease to fit, no previous check, or g <= tol.  Host only, no GPU work.
+ * The paper has no counterpart (it reports gaps per iteration).
+ */
+GP_API int gp_gap_schedule_next(int n_prev, double g_prev, int n, double g, double tol);
+
+/*
  * Launch profiler (tracing).  gp_profile(h, 1) clears the counters and starts
  * recording: every kernel the handle launches is bracketed by CUDA events on
  * its stream (CUDA-graph replay is disabled while recording); gp_profile(h, 0)
@@ -282,8 +298,12 @@ GP_API int gp_tuned_row_block(gp_handle h, const char* kernel, int N);
  * [0, gp_profile_kernels()), its name (static string), the summed device time
  * in ms and the number of kernel launches recorded (it waits for the recorded
  * events).  Classes: dct_rows_fwd, dct_cols_solve, dct_rows_inv (the three
- * passes of the fast cosine solve), dct_dense, rof_fused, emd_fused, reduce,
- * setup.  The paper has no counterpart (it reports wall-clock totals only).
+ * passes of the fast cosine solve), dct_cols_grad, dct_rows_grad (the
+ * gradient form's column and row passes), dct_dense, dct_tc_split,
+ * rof_fused, emd_fused (the stencil steps that write the right-hand side),
+ * reduce, setup, rof_step_fwd, emd_step_fwd (stencil steps fused with the
+ * next forward row pass).  The paper has no counterpart (it reports
+ * wall-clock totals only).
  */
 GP_API gp_status gp_profile(gp_handle h, int enable);
 GP_API int gp_profile_kernels(void);

@@ -707,7 +707,7 @@ struct Timer {
 
 gp_status check_opts(gp_handle h, const gp_opts* o) {
   if (o->max_iters < 0) return fail(h, GP_ERR_ARG, "max_iters < 0");
-  if (o->gap_every < 1) return fail(h, GP_ERR_ARG, "gap_every < 1");
+  if (o->gap_every < 0) return fail(h, GP_ERR_ARG, "gap_every < 0");
   if (o->prec < 0 || o->prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
   if (o->warm_start < 0 || o->warm_start > 1) return fail(h, GP_ERR_ARG, "unknown warm_start");
   return GP_OK;
@@ -739,8 +739,27 @@ struct DivergenceWatch {
   }
 };
 
+// Adaptive gap-check schedule (gap_every == 0 with a positive tolerance).
+// The relative gap's decay between the last two checks is fitted as
+// g ~ c n^-a; the next check goes halfway to the iteration where that fit
+// reaches the tolerance, as a chunk of 10 * 2^j iterations (at most 320), so
+// the checks thin out far from the target and close in on it in halving
+// steps.  Without a decrease to fit, the next check is 10 iterations on.
+constexpr int kAdaptiveMinChunk = 10, kAdaptiveMaxChunk = 320;
+
+int adaptive_chunk(int n_prev, double g_prev, int n, double g, double tol) {
+  if (n_prev <= 0 || n <= n_prev || !(g > tol) || !(g_prev > g) || !(tol > 0)) return kAdaptiveMinChunk;
+  const double a = log(g_prev / g) / log((double)n / n_prev);
+  if (!(a > 0)) return kAdaptiveMinChunk;
+  const double half = 0.5 * (n * pow(g / tol, 1.0 / a) - n);
+  int k = kAdaptiveMinChunk;
+  while (2 * k <= kAdaptiveMaxChunk && 2 * k <= half) k *= 2;
+  return k;
+}
+
 // Chunked solve loop shared by rof_solve / emd_solve: run gap_every
-// iterations (the last one with the fused gap reductions), check, repeat.
+// iterations (the last one with the fused gap reductions), check, repeat;
+// gap_every == 0 takes the adaptive schedule above.
 gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st) {
   gp_handle h = s->h;
   DivergenceWatch watch;
@@ -748,8 +767,11 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
   rep->primal = rep->dual = rep->rel_gap = rep->mass_residual = NAN;
   gp_status r;
   if (o.max_iters == 0 && (r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
+  int k_next = o.gap_every > 0 ? o.gap_every : kAdaptiveMinChunk;
+  int n_prev = -1;
+  double g_prev = 0;
   while (s->n < o.max_iters) {
-    const int k = std::min(o.gap_every, o.max_iters - s->n);
+    const int k = std::min(k_next, o.max_iters - s->n);
     if ((r = run_steps(s, k, o.prec, true, o.use_graph != 0, st)) != GP_OK) return r;
     if ((r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
     if (!isfinite(rep->primal) || !isfinite(rep->dual)) {
@@ -765,6 +787,11 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
       status = GP_ERR_DIVERGED;
       fail(h, status, "relative gap diverged");
       break;
+    }
+    if (o.gap_every == 0) {
+      k_next = adaptive_chunk(n_prev, g_prev, s->n, rep->rel_gap, o.tol_rel_gap);
+      n_prev = s->n;
+      g_prev = rep->rel_gap;
     }
   }
   rep->iters = s->n;
@@ -1167,7 +1194,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
   while (!active.empty()) {
     const int done_iters = h->batch[active[0]]->n;
     if (done_iters >= o.max_iters) break;
-    const int k = std::min(o.gap_every, o.max_iters - done_iters);
+    const int k = std::min(o.gap_every > 0 ? o.gap_every : kAdaptiveMinChunk, o.max_iters - done_iters);
     if (!exec || exec_k != k || first) {
       if (exec) cudaGraphExecDestroy(exec);
       exec = nullptr;
@@ -1374,6 +1401,10 @@ gp_status gp_autotune(gp_handle h, int N, const char* cache_path, void* stream) 
   for (auto& kv : h->cache) drop_graphs(kv.second);
   if (!tune_save(h, cache_path)) return fail(h, GP_ERR_ARG, "cannot write the autotune cache file");
   return GP_OK;
+}
+
+int gp_gap_schedule_next(int n_prev, double g_prev, int n, double g, double tol) {
+  return adaptive_chunk(n_prev, g_prev, n, g, tol);
 }
 
 int gp_tuned_row_block(gp_handle h, const char* kernel, int N) {

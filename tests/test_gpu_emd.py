@@ -176,3 +176,23 @@ def test_gap_before_any_step_leaves_state_intact(h, N):
     h2.check(st)
     h2.close()
     assert torch.equal(m, m2) and rep1["primal"] == rep2["primal"]
+
+
+@pytest.mark.parametrize("N", [128, 512])
+def test_adaptive_gap_checks_stop_where_the_fixed_schedule_does(h, N):
+    """gap_every = 0: the checks thin out far from the tolerance.  Every
+    adaptive check point is a multiple of 10, so the solve stops no earlier
+    than the every-10 schedule's first check below the tolerance, and at most
+    one chunk (<= 320 iterations) later; both certify gap <= 1e-5."""
+    from paper_1805_09453_gb300 import gprox
+
+    f0, f1 = _pair(N, 3)
+    res = {}
+    for ge in (10, 0):
+        m = torch.empty((2, N, N), device="cuda")
+        st, rep = gprox.emd_solve(h, _t(f0), _t(f1), m, None, None,
+                                  gprox.default_opts(max_iters=60000, tol_rel_gap=1e-5, gap_every=ge))
+        assert st == gprox.GP_OK and 0.0 <= rep["rel_gap"] <= 1e-5, (ge, rep)
+        res[ge] = rep["iters"]
+    print(f"EMD {N}^2 to 1e-5: every 10 -> {res[10]} iterations, adaptive -> {res[0]}")
+    assert res[10] <= res[0] <= res[10] + 320
