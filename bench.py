@@ -414,6 +414,24 @@ def run_ours(args):
                                            "status": rep["status_name"], "start": rep["start"],
                                            "mass_residual": rep["mass_residual"], "coarse_factor": 4,
                                            "coarse_tol": 1e-6, "speedup": ttg["emd"]["seconds"] / sec}
+            # the same two EMD solves with the adaptive gap-check schedule (gap_every = 0): checks
+            # thin out far from the tolerance (each check costs a dual-potential solve)
+            oa = gprox.default_opts(max_iters=args.ttg_cap, tol_rel_gap=1e-5, gap_every=0, use_graph=1)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, oa)
+            sec = time.perf_counter() - t0
+            ttg["emd_adaptive_checks"] = {"seconds": sec, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
+                                          "status": rep["status_name"], "speedup": ttg["emd"]["seconds"] / sec}
+            if N % 64 == 0:
+                oca = gprox.default_opts(max_iters=200000, tol_rel_gap=1e-6, gap_every=0, use_graph=1)
+                stream.synchronize()
+                t0 = time.perf_counter()
+                st, rep = gprox.emd_solve_learned(h, base, f0d, f1d, m, None, None, oa, 4, oca)
+                sec = time.perf_counter() - t0
+                ttg["emd_coarse_start_adaptive_checks"] = {
+                    "seconds": sec, "iters": rep["iters"], "rel_gap": rep["rel_gap"], "status": rep["status_name"],
+                    "start": rep["start"], "speedup": ttg["emd"]["seconds"] / sec}
                 base.close()
 
     # batched solve: 64 independent EMD pairs of sizes drawn from {256, 512, 1024, 2048}^2,

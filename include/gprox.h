@@ -73,10 +73,11 @@ typedef enum gp_prec {
 typedef struct gp_opts {
   int max_iters;       /* iteration cap (>= 0; default 1000) */
   int gap_every;       /* duality-gap check every k iterations (>= 1; default 10); 0: adaptive
-                          (rof_solve / emd_solve with tol_rel_gap > 0): after each check the gap's
-                          decay over the last two checks, fitted as g ~ n^-a, places the next
-                          check halfway to the predicted crossing of tol_rel_gap, in chunks of
-                          10 * 2^j <= 320 iterations; batched solves take 10 */
+                          (rof_solve / emd_solve with tol_rel_gap > 0): while the gap is above
+                          3 x tol_rel_gap, its decay over the last two checks, fitted as
+                          g ~ n^-a, places the next check halfway to the predicted crossing, in
+                          chunks of 10 * 2^j <= 320 iterations; within 3 x, every 10 (see
+                          gp_gap_schedule_next); batched solves take 10 */
   double tol_rel_gap;  /* stop once (P - D) / max(|P|,|D|) <= tol; <= 0: run exactly max_iters */
   double tau;          /* primal step; <= 0 selects the paper's rule (ROF section 4.1, EMD tau = 1) */
   double sigma;        /* dual step; <= 0 selects 1 / tau */
@@ -285,7 +286,9 @@ GP_API int gp_tuned_row_block(gp_handle h, const char* kernel, int N);
  * if none) and the current one (n, g), returns the number of iterations to
  * run before the next check: 10 * 2^j <= 320, halfway to the iteration where
  * the fit g ~ c n^-a through the two checks reaches tol; 10 when there is no
- * decrease to fit, no previous check, or g <= tol.  Host only, no GPU work.
+ * decrease to fit, no previous check, or g <= 3 tol (the gap is not
+ * monotone: near the target it dips below tol at isolated checks that sparse
+ * checks would step over).  Host only, no GPU work.
  * The paper has no counterpart (it reports gaps per iteration).
  */
 GP_API int gp_gap_schedule_next(int n_prev, double g_prev, int n, double g, double tol);

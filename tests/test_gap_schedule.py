@@ -1,10 +1,10 @@
 """Host logic of the adaptive gap-check schedule (gap_every = 0), CPU only.
 
-The schedule fits the relative gap's decay between two checks as
-g = c n^-a and runs half the iterations the fit predicts to the tolerance,
-as a chunk of 10 * 2^j <= 320.  Checked against the closed form of that
-rule on exact power laws, its bounds, and the fallbacks (no previous check,
-no decrease, already converged).
+While the relative gap is above 3 x the tolerance, the schedule fits its
+decay between two checks as g = c n^-a and runs half the iterations the fit
+predicts to the tolerance, as a chunk of 10 * 2^j <= 320; within 3 x, and
+in the fallbacks (no previous check, no decrease, converged), 10.  Checked
+against the closed form of that rule on exact power laws and its bounds.
 """
 import math
 
@@ -14,6 +14,8 @@ from paper_1805_09453_gb300 import gprox
 
 
 def _rule(n_prev, g_prev, n, g, tol):
+    if g <= 3 * tol:
+        return 10
     a = math.log(g_prev / g) / math.log(n / n_prev)
     half = 0.5 * (n * (g / tol) ** (1.0 / a) - n)
     k = 10
@@ -39,12 +41,18 @@ def test_far_from_target_takes_the_longest_chunk():
     assert gprox.gap_schedule_next(100, 1e-1, 200, 5e-2, 1e-5) == 320
 
 
-def test_close_to_target_takes_the_shortest_chunk():
-    # g ~ 1/n: from 2e-5 at n = 1000 the tolerance 1e-5 is 1000 iterations away -> half = 500 -> 320;
-    # from 1.1e-5 at n = 1000 it is 100 away -> half = 50 -> 40
-    assert gprox.gap_schedule_next(500, 4e-5, 1000, 2e-5, 1e-5) == 320
-    assert gprox.gap_schedule_next(500, 2.2e-5, 1000, 1.1e-5, 1e-5) == 40
-    assert gprox.gap_schedule_next(990, 1.0101e-5, 1000, 1.0001e-5, 1e-5) == 10
+def test_chunk_halves_towards_the_predicted_crossing():
+    # g ~ 1/n: from 8e-5 at n = 1000 the tolerance 1e-5 is 7000 iterations away -> half 3500 -> 320;
+    # from 4e-5 at n = 1000 it is 3000 away -> half 1500 -> 320; g ~ n^-4 from 4e-5 at n = 1000:
+    # 1000 (4^(1/4) - 1) = 414 away -> half 207 -> 160
+    assert gprox.gap_schedule_next(500, 16e-5, 1000, 8e-5, 1e-5) == 320
+    assert gprox.gap_schedule_next(500, 8e-5, 1000, 4e-5, 1e-5) == 320
+    assert gprox.gap_schedule_next(500, 4e-5 * 16, 1000, 4e-5, 1e-5) == 160
+
+
+def test_within_three_tolerances_checks_every_ten():
+    assert gprox.gap_schedule_next(500, 6e-5, 1000, 3e-5, 1e-5) == 10
+    assert gprox.gap_schedule_next(500, 2.2e-5, 1000, 1.1e-5, 1e-5) == 10
 
 
 @pytest.mark.parametrize("args", [
