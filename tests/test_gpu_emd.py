@@ -180,12 +180,13 @@ def test_gap_before_any_step_leaves_state_intact(h, N):
 
 @pytest.mark.parametrize("N", [128, 512])
 def test_adaptive_gap_checks_stop_where_the_fixed_schedule_does(h, N):
-    """gap_every = 0: the checks thin out far from the tolerance.  Every
-    adaptive check point is a multiple of 10, so the solve stops no earlier
-    than the every-10 schedule's first check below the tolerance; both
-    certify gap <= 1e-5.  The gap is not monotone (it can dip below the
-    tolerance at a check the adaptive schedule steps over), so the later stop
-    is only bounded loosely."""
+    """gap_every = 0: the checks thin out far from the tolerance; both
+    schedules certify gap <= 1e-5 and every adaptive check point is a
+    multiple of 10.  The stops are compared only loosely: the gap is not
+    monotone (near the target it dips below the tolerance at isolated
+    checks, which sparse checks can step over), and the chunk lengths decide
+    which steps run the fused step kernel, whose rounding differs from the
+    unfused one's, so the two trajectories are not identical."""
     from paper_1805_09453_gb300 import gprox
 
     f0, f1 = _pair(N, 3)
@@ -197,4 +198,4 @@ def test_adaptive_gap_checks_stop_where_the_fixed_schedule_does(h, N):
         assert st == gprox.GP_OK and 0.0 <= rep["rel_gap"] <= 1e-5, (ge, rep)
         res[ge] = rep["iters"]
     print(f"EMD {N}^2 to 1e-5: every 10 -> {res[10]} iterations, adaptive -> {res[0]}")
-    assert res[0] % 10 == 0 and res[10] <= res[0] <= 1.25 * res[10] + 320
+    assert res[0] % 10 == 0 and abs(res[0] - res[10]) <= 0.25 * res[10] + 320
