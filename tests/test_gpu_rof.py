@@ -111,7 +111,10 @@ def test_rof_constant_image_and_errors(h):
     assert rep["tau"] == 1.0  # constant image: the rule's tau is 0, 1 is used
     assert torch.allclose(u, I, atol=1e-6)
     assert gprox.rof_solve(h, I, u, None, -1.0)[0] == gprox.GP_ERR_ARG
-    assert gprox.rof_solve(h, I, u, None, 8.0, gprox.default_opts(gap_every=0))[0] == gprox.GP_ERR_ARG
+    assert gprox.rof_solve(h, I, u, None, 8.0, gprox.default_opts(gap_every=-1))[0] == gprox.GP_ERR_ARG
+    # gap_every = 0 selects the adaptive check schedule
+    st, rep = gprox.rof_solve(h, I, u, None, 8.0, gprox.default_opts(max_iters=50, gap_every=0, tol_rel_gap=1e-5))
+    assert st == gprox.GP_OK and rep["iters"] % 10 == 0
     bad = I.clone()
     bad[3, 3] = float("nan")
     st, _ = gprox.rof_solve(h, bad, u, None, 8.0, gprox.default_opts(max_iters=10, tau=1.0))
