@@ -20,12 +20,16 @@
 // shared memory; each thread holds one 16-point butterfly in registers.
 // Between passes the spectra live in a 4-row-interleaved layout so that the
 // row passes (4 rows per CTA) and the column pass (2 columns per CTA) all
-// move contiguous, full-sector blocks.
+// move contiguous, full-sector blocks; at N >= 512 (gradient form) and
+// N >= 2048 (plain solve) the column passes move them with bulk tensor
+// copies.
 //
-// Gradient variant (EMD): the column and last row pass also synthesise the
-// forward differences of the solution directly from its spectrum, so that the
-// gradient keeps FP32 relative precision at any N (differencing an FP32
-// potential loses about log2(N) bits).
+// Gradient variant (ROF and EMD steps): the column and last row pass also
+// synthesise the forward differences of the solution directly from its
+// spectrum, so that the gradient keeps FP32 relative precision at any N
+// (differencing an FP32 potential loses about log2(N) bits).  Inside a chunk
+// of steps the forward row pass of the next solve runs in the same CTAs as
+// the step's stencil (k_rof_step_rows_fwd, k_emd_step_rows_fwd).
 //
 // Dense path (any N): four FP32 GEMMs with the orthonormal DCT-II matrix.
 #include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
@@ -316,8 +320,9 @@ __device__ __forceinline__ int mk_pos(int n, int N) { return (n & 1) ? (N - 1 - 
 // Offset of element (row i, column l) in the 4-row-interleaved layout of the
 // intermediate spectra: each block of 4 rows is stored column by column, 4
 // values per column.  A row pass (4 rows per CTA) then reads or writes one
-// contiguous 16N-byte block, and a column pass (2 columns per CTA) reads 32
-// contiguous bytes per block: every pass is coalesced.
+// contiguous 16N-byte block, and a column pass (2 columns per CTA) moves 32
+// contiguous bytes per block (one cache line per lane for thread loads, so
+// at N >= 512 the column passes hand those to bulk tensor copies).
 __device__ __forceinline__ size_t b4(int i, int l, int N) {
   return (size_t)(i >> 2) * 4 * N + (size_t)l * 4 + (i & 3);
 }
@@ -428,7 +433,7 @@ __device__ __forceinline__ void rows_fwd_tail_pair(float2* buf, float* __restric
   constexpr int N = C::N, TPF = C::TPF;
   const int t = threadIdx.x;
   fft_smem<LOG2N, -1, TPF>(buf, t, tw);
-  float* __restrict__ o = out + (size_t)(i0 >> 2) * 4 * N + (i0 & 3);
+  float* __restrict__ o = out + b4(i0, 0, N);
 #pragma unroll
   for (int kk = 0; kk <= (N / 2) / TPF; ++kk) {
     if (kk == (N / 2) / TPF && t != 0) break;
