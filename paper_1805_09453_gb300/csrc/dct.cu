@@ -197,18 +197,19 @@ __device__ __forceinline__ void fft_stage(float2* buf, const int Ns, const int t
 
 // Length-2^LOG2N complex FFT in shared memory (unnormalised), natural order.
 // DIR = -1: forward e^{-i...}; DIR = +1: inverse without the 1/N factor.
+// bar: 0 = __syncthreads, else the named barrier of this transform's TPF threads.
 template <int LOG2N, int DIR, int TPF>
-__device__ __forceinline__ void fft_smem(float2* buf, int t, const float2* __restrict__ tw) {
+__device__ __forceinline__ void fft_smem(float2* buf, int t, const float2* __restrict__ tw, int bar = 0) {
   constexpr int N = 1 << LOG2N;
   constexpr int S16 = LOG2N / 4;
   constexpr int REM = 1 << (LOG2N % 4);
   int Ns = 1;
 #pragma unroll
   for (int s = 0; s < S16; ++s) {
-    fft_stage<N, 16, DIR, TPF>(buf, Ns, t, tw);
+    fft_stage<N, 16, DIR, TPF>(buf, Ns, t, tw, bar);
     Ns *= 16;
   }
-  if constexpr (REM > 1) fft_stage<N, REM, DIR, TPF>(buf, Ns, t, tw);
+  if constexpr (REM > 1) fft_stage<N, REM, DIR, TPF>(buf, Ns, t, tw, bar);
 }
 
 // Base twiddles (w1, w2, w4, w8 of e^{-2 pi i m / N}) of thread t's butterfly
@@ -401,7 +402,9 @@ __device__ __forceinline__ void rows_fwd_tail(float2* smem, float* __restrict__ 
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
   const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
-  fft_smem<LOG2N, -1, TPF>(smem + f * PADN, t, tw);
+  // each slot's transform on its own barrier; the post-step reads both buffers
+  fft_smem<LOG2N, -1, TPF>(smem + f * PADN, t, tw, TPF >= 32 ? f + 1 : 0);
+  if (TPF >= 32) __syncthreads();
   float* __restrict__ o = out + (size_t)rb * 4 * N;
   const float2* b0 = smem;
   const float2* b1 = smem + PADN;
@@ -818,7 +821,7 @@ __global__ void __launch_bounds__(2 * FftCfg<LOG2N>::TPF, (LOG2N == 12 ? 2 : 1))
   __syncthreads();
   const int f = threadIdx.x / TPF, t = threadIdx.x % TPF;
   float2* buf = smem + f * PADN;
-  fft_smem<LOG2N, +1, TPF>(buf, t, tw);
+  fft_smem<LOG2N, +1, TPF>(buf, t, tw, TPF >= 32 ? f + 1 : 0);  // the post-step reads only this slot's buffer
   float* __restrict__ oa = out + (size_t)(4 * rb + 2 * f) * N;
   float* __restrict__ ob = oa + N;
   #pragma unroll
@@ -1311,7 +1314,10 @@ __global__ void __launch_bounds__((PAR ? 8 : 2) * FftCfg<LOG2N>::TPF, (LOG2N == 
       }
     }
     gsync(bar, (PAR ? 1 : 2) * TPF);
-    fft_smem_tws<LOG2N, +1, TPF>(buf, t, tw, twsm, bar);
+    // the transform and the post-step touch only this slot's buffer: each
+    // slot synchronises on its own barrier (the pre-step above writes both
+    // buffers, so it and the end of the pass stay CTA-wide)
+    fft_smem_tws<LOG2N, +1, TPF>(buf, t, tw, twsm, PAR ? bar : (TPF >= 32 ? f + 1 : 0));
     if (pass < 2) {
       float* __restrict__ o = gx + (size_t)(r0 + pass) * N;
 #pragma unroll
