@@ -348,6 +348,27 @@ __global__ void __launch_bounds__(256) k_emd_dual(const float* __restrict__ phi,
   block_reduce_store<2>(v, 2u, part);
 }
 
+// The same with 128-bit loads (all pointers 16-byte aligned, N^2 % 4 == 0):
+// a quarter of the load instructions for this bandwidth-bound pass.
+__global__ void __launch_bounds__(256) k_emd_dual4(const float4* __restrict__ phi, const float4* __restrict__ gx,
+                                                   const float4* __restrict__ gy, const float4* __restrict__ f0,
+                                                   const float4* __restrict__ f1, size_t n4,
+                                                   double* __restrict__ part) {
+  CSum s;
+  float gmax = 0.f;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n4; idx += (size_t)gridDim.x * blockDim.x) {
+    const float4 p = phi[idx], a = f0[idx], b = f1[idx], x = gx[idx], y = gy[idx];
+    s.add(p.x * (b.x - a.x));
+    s.add(p.y * (b.y - a.y));
+    s.add(p.z * (b.z - a.z));
+    s.add(p.w * (b.w - a.w));
+    gmax = fmaxf(gmax, fmaxf(fmaxf(sqrtf(x.x * x.x + y.x * y.x), sqrtf(x.y * x.y + y.y * y.y)),
+                             fmaxf(sqrtf(x.z * x.z + y.z * y.z), sqrtf(x.w * x.w + y.w * y.w))));
+  }
+  double v[2] = {s.value(), (double)gmax};
+  block_reduce_store<2>(v, 2u, part);
+}
+
 // ROF step-rule statistics: sum |grad I|, sum |grad I|^2, sum I.
 __global__ void __launch_bounds__(256) k_rof_stats(const float* __restrict__ I, int N, float invh,
                                                    double* __restrict__ part) {
@@ -598,7 +619,15 @@ int reduce_blocks_1d(size_t n) { return grid_1d(n, 256) < 1024 ? grid_1d(n, 256)
 
 cudaError_t launch_emd_dual(const float* phi, const float* gphi, const float* f0, const float* f1, int N, double* part,
                             int nblk, cudaStream_t st) {
-  k_emd_dual<<<nblk, 256, 0, st>>>(phi, gphi, f0, f1, N, part);
+  const size_t NN = (size_t)N * N;
+  auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  if (NN % 4 == 0 && a16(phi) && a16(gphi) && a16(f0) && a16(f1)) {
+    k_emd_dual4<<<nblk, 256, 0, st>>>(reinterpret_cast<const float4*>(phi), reinterpret_cast<const float4*>(gphi),
+                                      reinterpret_cast<const float4*>(gphi + NN), reinterpret_cast<const float4*>(f0),
+                                      reinterpret_cast<const float4*>(f1), NN / 4, part);
+  } else {
+    k_emd_dual<<<nblk, 256, 0, st>>>(phi, gphi, f0, f1, N, part);
+  }
   return cudaGetLastError();
 }
 
