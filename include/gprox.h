@@ -280,6 +280,18 @@ GP_API gp_status gp_autotune(gp_handle h, int N, const char* cache_path, void* s
 GP_API int gp_tuned_row_block(gp_handle h, const char* kernel, int N);
 
 /*
+ * gp_rof_image_stats: the image norms the ROF step rules take (section 4.1;
+ * the rof_solve rule, and the rules of the paper's disc experiments), as FP64
+ * reductions on the GPU: out[0] = ||I||_TV = h^2 sum |grad I| (isotropic,
+ * forward differences), out[1] = ||grad I||_L2 = (h^2 sum |grad I|^2)^(1/2),
+ * out[2] = ||I - mean(I)||^2_L2 = h^2 sum (I - mean)^2, h = 1/N.  I: device
+ * pointer, N x N row-major FP32, read only; out: host array of 3 doubles.
+ * Synchronises the stream.  Errors: GP_ERR_ARG (bad pointer or N),
+ * GP_ERR_CUDA.
+ */
+GP_API gp_status gp_rof_image_stats(gp_handle h, const float* I, int N, double* out, void* stream);
+
+/*
  * gp_gap_schedule_next: the adaptive gap-check schedule of gap_every == 0 as
  * a pure function, for callers driving pd_step / gp_state_gap themselves.
  * Given the previous check (iteration n_prev, relative gap g_prev; n_prev <= 0

@@ -674,8 +674,9 @@ gp_status check_mass(gp_handle h, const double ms[3]) {
 }
 
 // ROF step rule (sections 3.1 and 4.1).
-gp_status rof_rule(gp_handle h, const float* I, int N, double lambda, const gp_opts& o, double* tau_out,
-                   cudaStream_t st) {
+// Image norms of the ROF step rule (section 4.1), FP64 reductions on the GPU:
+// out[0] = ||I||_TV = h^2 sum |grad I|, out[1] = ||grad I||_L2, out[2] = ||I - mean I||^2_L2.
+gp_status rof_image_stats(gp_handle h, const float* I, int N, double out[3], cudaStream_t st) {
   const size_t NN = (size_t)N * N;
   const int nb = reduce_blocks_1d(NN);
   gp_status r = ensure_part(h, (size_t)nb * 3);
@@ -685,13 +686,22 @@ gp_status rof_rule(gp_handle h, const float* I, int N, double lambda, const gp_o
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 3, 0u, h->dres, st); }));
   if ((r = fetch(h, 3, st)) != GP_OK) return r;
   const double h2 = 1.0 / ((double)N * N);
-  const double tv = h2 * h->hres[0];
-  const double grad_l2 = sqrt(h2 * h->hres[1]);
+  out[0] = h2 * h->hres[0];
+  out[1] = sqrt(h2 * h->hres[1]);
   const double mean = h->hres[2] / (double)NN;
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_sq_dev(I, NN, (float)mean, h->part, nb, st); }));
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 1, 0u, h->dres, st); }));
   if ((r = fetch(h, 1, st)) != GP_OK) return r;
-  const double fid = 0.5 * lambda * h2 * h->hres[0];
+  out[2] = h2 * h->hres[0];
+  return GP_OK;
+}
+
+gp_status rof_rule(gp_handle h, const float* I, int N, double lambda, const gp_opts& o, double* tau_out,
+                   cudaStream_t st) {
+  double stats[3];
+  gp_status r = rof_image_stats(h, I, N, stats, st);
+  if (r != GP_OK) return r;
+  const double tv = stats[0], grad_l2 = stats[1], fid = 0.5 * lambda * stats[2];
   if (!isfinite(tv) || !isfinite(fid)) return fail(h, GP_ERR_NONFINITE, "non-finite image");
   const double eps = o.eps > 0 ? o.eps : 1e-3;
   double tau = fmin(sqrt(lambda) * fmin(tv, fid) / sqrt(eps), grad_l2);
@@ -1406,6 +1416,18 @@ gp_status gp_autotune(gp_handle h, int N, const char* cache_path, void* stream) 
   for (auto& kv : h->cache) drop_graphs(kv.second);
   if (!tune_save(h, cache_path)) return fail(h, GP_ERR_ARG, "cannot write the autotune cache file");
   return GP_OK;
+}
+
+gp_status gp_rof_image_stats(gp_handle h, const float* I, int N, double* out, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
+  if (!out) return fail(h, GP_ERR_ARG, "out is NULL");
+  gp_status r = check_ptr(h, I, "I");
+  if (r != GP_OK) return r;
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  return rof_image_stats(h, I, N, out, (cudaStream_t)stream);
 }
 
 int gp_gap_schedule_next(int n_prev, double g_prev, int n, double g, double tol) {

@@ -26,7 +26,7 @@ EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_l
            "dct2_poisson_static", "dct2_poisson_grad", "emd_solve_batched", "gp_autotune", "gp_tuned_row_block",
            "gp_cnn_create", "gp_cnn_destroy", "gp_cnn_last_error", "gp_cnn_num_params", "gp_cnn_get_params",
            "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned",
-           "emd_coarse_start", "gp_gap_schedule_next"]
+           "emd_coarse_start", "gp_gap_schedule_next", "gp_rof_image_stats"]
 
 
 class Opts(C.Structure):
@@ -100,6 +100,7 @@ def lib():
                                     C.POINTER(Report), C.POINTER(i), vp]
     L.emd_coarse_start.argtypes = [vp, vp, vp, i, i, C.POINTER(Opts), vp, C.POINTER(Report), vp]
     L.gp_gap_schedule_next.argtypes = [i, d, i, d, d]
+    L.gp_rof_image_stats.argtypes = [vp, vp, i, C.POINTER(d), vp]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
     for name in EXPORTS:
@@ -283,6 +284,13 @@ def autotune(h: Handle, N: int, cache_path: str | None = None, stream=None) -> i
 
 def tuned_row_block(h: Handle, kernel: str, N: int) -> int:
     return lib().gp_tuned_row_block(h.ptr, kernel.encode(), int(N))
+
+
+def rof_image_stats(h: Handle, I, stream=None):
+    """(||I||_TV, ||grad I||_L2, ||I - mean I||^2_L2), reduced on the GPU."""
+    out = (C.c_double * 3)()
+    h.check(lib().gp_rof_image_stats(h.ptr, _ptr(I), int(I.shape[-1]), out, _stream(stream)))
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def gap_schedule_next(n_prev: int, g_prev: float, n: int, g: float, tol: float) -> int:

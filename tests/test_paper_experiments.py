@@ -1,0 +1,77 @@
+"""Host side of the paper-experiment driver (section 4), CPU only: the step
+rules against the paper's own statements about them, and the inputs.
+
+Section 4.2 states, for the delta-measure rule
+tau = min(sqrt(1/(eps |log eps|)), 2 M^(1/4)): at eps = 1e-2 the first term
+is the smaller on every grid (512^2 .. 4096^2); at 1e-3 it is larger on
+512^2, about equal on 1024^2 and smaller on 2048^2 and 4096^2; at 1e-4 the
+second term is the smaller on every grid.  Those statements hold for M = N,
+the points per side (the reading the driver takes; with M = N^2 points the
+second term would be the larger everywhere at these tolerances), and are the
+pins below.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1805_09453_gb300 import paper_experiments as PE
+from paper_1805_09453_gb300 import synth
+
+SIZES = [512, 1024, 2048, 4096]
+
+
+def _terms(N, eps):
+    return math.sqrt(1.0 / (eps * abs(math.log(eps)))), 2.0 * N ** 0.25
+
+
+def test_delta_rule_eps_1e2_first_term_everywhere():
+    for N in SIZES:
+        a, b = _terms(N, 1e-2)
+        assert a < b and PE.emd_delta_tau(N, 1e-2) == a
+
+
+def test_delta_rule_eps_1e3_crosses_at_1024():
+    a, b = _terms(512, 1e-3)
+    assert a > b and PE.emd_delta_tau(512, 1e-3) == b
+    a, b = _terms(1024, 1e-3)
+    assert abs(a - b) / b < 0.1  # "approximately equal"
+    for N in (2048, 4096):
+        a, b = _terms(N, 1e-3)
+        assert a < b and PE.emd_delta_tau(N, 1e-3) == a
+
+
+def test_delta_rule_eps_1e4_grid_term_everywhere():
+    for N in SIZES:
+        a, b = _terms(N, 1e-4)
+        assert b < a and PE.emd_delta_tau(N, 1e-4) == b
+
+
+@pytest.mark.parametrize("lam,eps", [(10.0, 1e-2), (20.0, 1e-3)])
+def test_rof_rule_forms(lam, eps):
+    stats = (1.5, 30.0, 0.2)
+    free = math.sqrt(lam) * 1.5 / math.sqrt(eps)
+    assert PE.rof_tau(stats, lam, eps, grid_dependent=False) == pytest.approx(free, rel=1e-15)
+    assert PE.rof_tau(stats, lam, eps) == pytest.approx(min(free, 30.0), rel=1e-15)
+
+
+def test_inputs_of_the_experiments():
+    N = 64
+    I = synth.disc_image(N)
+    assert set(np.unique(I)) == {0.0, 1.0}
+    assert abs(I.mean() - math.pi / 16) < 0.01  # disc of radius 1/4
+    f0, f1 = synth.translated_discs(N)
+    assert abs(f0.astype(np.float64).sum() / N ** 2 - 1) < 1e-6 and abs(f1.astype(np.float64).sum() / N ** 2 - 1) < 1e-6
+    # f1 is f0 translated by (1/4, 1/4): N/4 cells along both axes
+    np.testing.assert_array_equal(np.roll(f0, (N // 4, N // 4), axis=(0, 1)), f1)
+    d0, d1 = synth.delta_pair(N)
+    assert np.count_nonzero(d0) == 1 and d0.max() == N * N and np.count_nonzero(d1) == 1
+    np.testing.assert_array_equal(np.roll(d0, (N // 4, N // 4), axis=(0, 1)), d1)
+
+
+def test_paper_tables_are_consistent():
+    for name, t in PE.PAPER_TABLES.items():
+        for N, row in t["iters"].items():
+            assert len(row) == len(t["eps"]), name
+            vals = [v for v in row if v is not None]
+            assert vals == sorted(vals), (name, N)  # tighter tolerance, more iterations
