@@ -6,9 +6,10 @@ tau = min(sqrt(1/(eps |log eps|)), 2 M^(1/4)): at eps = 1e-2 the first term
 is the smaller on every grid (512^2 .. 4096^2); at 1e-3 it is larger on
 512^2, about equal on 1024^2 and smaller on 2048^2 and 4096^2; at 1e-4 the
 second term is the smaller on every grid.  Those statements hold for M = N,
-the points per side (the reading the driver takes; with M = N^2 points the
-second term would be the larger everywhere at these tolerances), and are the
-pins below.
+the points per side, and are the pins of that form of the rule below; with
+M = N^2, the number of grid points the paper's definition names (the
+driver's default, which reproduces the paper's delta table more closely),
+the second term is the larger everywhere at these tolerances.
 """
 import math
 
@@ -28,23 +29,30 @@ def _terms(N, eps):
 def test_delta_rule_eps_1e2_first_term_everywhere():
     for N in SIZES:
         a, b = _terms(N, 1e-2)
-        assert a < b and PE.emd_delta_tau(N, 1e-2) == a
+        assert a < b and PE.emd_delta_tau(N, 1e-2, m_points=False) == a
 
 
 def test_delta_rule_eps_1e3_crosses_at_1024():
     a, b = _terms(512, 1e-3)
-    assert a > b and PE.emd_delta_tau(512, 1e-3) == b
+    assert a > b and PE.emd_delta_tau(512, 1e-3, m_points=False) == b
     a, b = _terms(1024, 1e-3)
     assert abs(a - b) / b < 0.1  # "approximately equal"
     for N in (2048, 4096):
         a, b = _terms(N, 1e-3)
-        assert a < b and PE.emd_delta_tau(N, 1e-3) == a
+        assert a < b and PE.emd_delta_tau(N, 1e-3, m_points=False) == a
 
 
 def test_delta_rule_eps_1e4_grid_term_everywhere():
     for N in SIZES:
         a, b = _terms(N, 1e-4)
-        assert b < a and PE.emd_delta_tau(N, 1e-4) == b
+        assert b < a and PE.emd_delta_tau(N, 1e-4, m_points=False) == b
+
+
+def test_delta_rule_with_grid_points():
+    # M = N^2: 2 M^(1/4) = 2 sqrt(N) >= 45 exceeds sqrt(1/(eps |log eps|)) (<= 33) for eps >= 1e-4
+    for N in SIZES:
+        for eps in (1e-2, 1e-3, 1e-4):
+            assert PE.emd_delta_tau(N, eps) == pytest.approx(math.sqrt(1.0 / (eps * abs(math.log(eps)))))
 
 
 @pytest.mark.parametrize("lam,eps", [(10.0, 1e-2), (20.0, 1e-3)])
