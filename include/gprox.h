@@ -242,6 +242,26 @@ GP_API gp_status gp_state_gap(gp_handle h, gp_state s, gp_report* report, void* 
 GP_API gp_status gp_state_destroy(gp_state s);
 
 /*
+ * Ergodic averages (the iterate averages u^n = (1/n) sum_{k=1..n} u_k,
+ * p^n = (1/n) sum p_k in which the convergence theorems of sections 3.1 / 3.2
+ * are stated).  gp_state_average(h, s, 1, stream) starts (or restarts) the
+ * averages of state s: it allocates 3 (ROF) or 5 (EMD) FP64 planes of running
+ * sums, zeroes them, and every later pd_step adds its iterate; while it is on,
+ * the steps write their right-hand sides (no fused forward row pass).
+ * gp_state_average(h, s, 0, stream) stops and frees the sums.
+ * gp_state_read_average writes the averages of the steps taken since the
+ * start into caller device buffers (either may be NULL): primal (u: N*N, or
+ * m: 2*N*N) and p (2*N*N); *count (may be NULL) receives n.  The primal
+ * average is taken through the solve's linearity: ROF u^n = (lambda tau -
+ * Lap)^{-1} (mean of the right-hand sides), EMD m^n = mean(s) + grad Lap^{-1}
+ * (mean(d)), one solve per read.  Errors: GP_ERR_ARG (no averaged step, bad
+ * pointers).  Not in the paper's experiments (they report the last iterate).
+ */
+GP_API gp_status gp_state_average(gp_handle h, gp_state s, int enable, void* stream);
+GP_API gp_status gp_state_read_average(gp_handle h, gp_state s, float* primal, float* p, long long* count,
+                                       void* stream);
+
+/*
  * dct2_poisson_static: dct2_poisson without any device allocation.  The paper
  * has no counterpart; this entry point serves callers that may not call
  * cudaMalloc -- a host framework that owns all device memory through its own

@@ -111,6 +111,10 @@ struct gp_state_s {
                                      // fused step kernel for the next step of the same chunk
   double* part = nullptr;            // this state's per-block partial sums
   bool vec = false;
+  // ergodic averages (gp_state_average): FP64 running sums of the right-hand
+  // sides (ROF: r; EMD: s (2 planes) and d) and of p over avg_n steps
+  double* avg_sum = nullptr;
+  long long avg_n = 0;
   int rb = 16;                  // row-block height of the fused kernel (autotuned tile shape)
   bool partials_valid = false;  // part holds the fused gap partials of the current iterate
   double mass_den = 0;          // EMD: sum |f0 - f1| (mass-residual normaliser)
@@ -332,6 +336,7 @@ void drop_graphs(gp_state s) {
 void free_state(gp_state s) {
   if (!s) return;
   drop_graphs(s);
+  if (s->avg_sum) cudaFree(s->avg_sum);
   for (void* p : s->allocs) cudaFree(p);
   delete s;
 }
@@ -432,7 +437,7 @@ gp_status rof_setup(gp_state s, const float* I, double lam, double tau, double s
 // chunk (the gap step, when there is one) writes the right-hand side itself,
 // so a chunk always starts and ends with s->r current.
 const DctPlan* fused_step_plan(gp_state s, int prec) {
-  if (prec != GP_PREC_FP32 || !s->rh || !s->vec) return nullptr;
+  if (prec != GP_PREC_FP32 || !s->rh || !s->vec || s->avg_sum) return nullptr;
   auto it = s->h->plans.find(s->N);
   return it != s->h->plans.end() && it->second.fft ? &it->second : nullptr;
 }
@@ -445,6 +450,8 @@ gp_status rof_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
     const bool g = gap_last && (k == n_steps - 1);
     const DctPlan* fp = fused_step_plan(s, prec);  // the plan exists after the first solve
     const bool rows_in = fp && k > 0;
+    if (s->avg_sum)  // u_{n+1} = (lambda tau - Lap)^{-1} r_n is linear in r_n: sum the r_n
+      GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_accumulate(s->avg_sum, s->r, (size_t)N * N, st); }));
     // grad u_{n+1} from the spectrum; u_{n+1} itself only when the step reports the objective
     gp_status r = solve_grad(h, N, rows_in ? s->rh : s->r, s->gu, s->prim, g, s->tmp, s->lam * s->tau, 1.0, prec, st,
                              rows_in);
@@ -460,6 +467,11 @@ gp_status rof_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
                 return launch_rof_fused(s->gu, s->prim, pin, s->Ic, pout, s->r, s->part, P, s->vec, g, s->rb, st);
               }));
     }
+    if (s->avg_sum) {
+      const size_t NN = (size_t)N * N;
+      GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_accumulate(s->avg_sum + NN, pout, 2 * NN, st); }));
+      s->avg_n++;
+    }
     s->cur = 1 - s->cur;
     s->n++;
   }
@@ -473,6 +485,12 @@ gp_status emd_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
   for (int k = 0; k < n_steps; ++k) {
     const DctPlan* fp = fused_step_plan(s, prec);
     const bool rows_in = fp && k > 0;
+    if (s->avg_sum) {  // m_{n+1} = s_n + grad Lap^{-1} d_n is affine in (s_n, d_n): sum both
+      const size_t NN = (size_t)N * N;
+      GP_CUDA(h, plaunch(h, PK_SETUP, st,
+                         [&] { return launch_accumulate(s->avg_sum, s->s[s->cur], 2 * NN, st); }));
+      GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_accumulate(s->avg_sum + 2 * NN, s->r, NN, st); }));
+    }
     // grad q, q = Lap^{-1} d  <=>  (0 - Lap) q = -d
     gp_status r = solve_grad(h, N, rows_in ? s->rh : s->r, s->prim, s->phi, false, s->tmp, 0.0, -1.0, prec, st,
                              rows_in);
@@ -490,6 +508,12 @@ gp_status emd_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
                 return launch_emd_fused(s->prim, s->s[c], s->p[c], s->g, s->s[1 - c], s->p[1 - c], s->r, s->m, s->e,
                                         s->part, P, s->vec, g, s->rb, st);
               }));
+    }
+    if (s->avg_sum) {
+      const size_t NN = (size_t)N * N;
+      GP_CUDA(h, plaunch(h, PK_SETUP, st,
+                         [&] { return launch_accumulate(s->avg_sum + 3 * NN, s->p[1 - c], 2 * NN, st); }));
+      s->avg_n++;
     }
     s->cur = 1 - s->cur;
     s->n++;
@@ -520,6 +544,7 @@ gp_status run_steps(gp_state s, int k, int prec, bool gap_last, bool use_graph, 
     if (r != GP_OK) return r;
     s->partials_valid = gap_last;
     const int cur1 = s->cur, n1 = s->n;
+    const long long avg1 = s->avg_n;
     s->cur = cur0;
     cudaGraph_t g = nullptr;
     GP_CUDA(h, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -529,6 +554,7 @@ gp_status run_steps(gp_state s, int k, int prec, bool gap_last, bool use_graph, 
     cudaError_t e = cudaStreamEndCapture(st, &g);
     s->cur = cur1;
     s->n = n1;
+    s->avg_n = avg1;  // the capture launched nothing
     if (r != GP_OK) {
       if (g) cudaGraphDestroy(g);
       return r;
@@ -544,6 +570,7 @@ gp_status run_steps(gp_state s, int k, int prec, bool gap_last, bool use_graph, 
   GP_CUDA(h, cudaGraphLaunch(it->second, st));
   if (k & 1) s->cur = 1 - s->cur;
   s->n += k;
+  if (s->avg_sum) s->avg_n += k;
   s->partials_valid = gap_last;
   return GP_OK;
 }
@@ -1020,6 +1047,64 @@ gp_status gp_state_read(gp_handle h, gp_state s, float* primal, float* p, void* 
   if (p) {
     if ((r = check_ptr(h, p, "p")) != GP_OK) return r;
     GP_CUDA(h, cudaMemcpyAsync(p, s->p[s->cur], 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  }
+  return GP_OK;
+}
+
+gp_status gp_state_average(gp_handle h, gp_state s, int enable, void* stream) {
+  if (!h || !s || s->h != h) return h ? fail(h, GP_ERR_ARG, "state does not belong to handle") : GP_ERR_ARG;
+  h->err.clear();
+  DeviceGuard g(h->device);
+  drop_graphs(s);  // captured chunks differ with and without the sums
+  if (!enable) {
+    if (s->avg_sum) cudaFree(s->avg_sum);
+    s->avg_sum = nullptr;
+    s->avg_n = 0;
+    return GP_OK;
+  }
+  const size_t NN = (size_t)s->N * s->N;
+  const size_t planes = s->kind == KIND_ROF ? 3 : 5;
+  if (!s->avg_sum) GP_CUDA(h, cudaMalloc(&s->avg_sum, planes * NN * sizeof(double)));
+  GP_CUDA(h, cudaMemsetAsync(s->avg_sum, 0, planes * NN * sizeof(double), (cudaStream_t)stream));
+  s->avg_n = 0;
+  return GP_OK;
+}
+
+gp_status gp_state_read_average(gp_handle h, gp_state s, float* primal, float* p, long long* count,
+                                void* stream) {
+  if (!h || !s || s->h != h) return h ? fail(h, GP_ERR_ARG, "state does not belong to handle") : GP_ERR_ARG;
+  h->err.clear();
+  if (count) *count = s->avg_n;
+  if (!s->avg_sum || s->avg_n == 0) return fail(h, GP_ERR_ARG, "no averaged steps (gp_state_average, then pd_step)");
+  DeviceGuard g(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = s->N;
+  const size_t NN = (size_t)N * N;
+  const double inv = 1.0 / (double)s->avg_n;
+  gp_status r;
+  if (p) {
+    if ((r = check_ptr(h, p, "p")) != GP_OK) return r;
+    const double* ps = s->avg_sum + (s->kind == KIND_ROF ? NN : 3 * NN);
+    GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_scale_sum(ps, p, 2 * NN, inv, st); }));
+  }
+  if (primal) {
+    if ((r = check_ptr(h, primal, "primal")) != GP_OK) return r;
+    if (s->kind == KIND_ROF) {
+      // mean of u_{n+1} = (lambda tau - Lap)^{-1} (mean of r_n), solved into `primal`
+      GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_scale_sum(s->avg_sum, primal, NN, inv, st); }));
+      if ((r = solve_grad(h, N, primal, s->gu, primal, true, s->tmp, s->lam * s->tau, 1.0, GP_PREC_FP32, st)) !=
+          GP_OK)
+        return r;
+    } else {
+      // mean of m_{n+1} = mean(s_n) + grad q, q = Lap^{-1} mean(d_n); `primal` plane 0 holds mean(d_n)
+      // for the solve (plane 1 is scratch), then both planes the flux
+      GP_CUDA(h, plaunch(h, PK_SETUP, st,
+                         [&] { return launch_scale_sum(s->avg_sum + 2 * NN, primal, NN, inv, st); }));
+      if ((r = solve_grad(h, N, primal, s->prim, primal + NN, false, s->tmp, 0.0, -1.0, GP_PREC_FP32, st)) != GP_OK)
+        return r;
+      GP_CUDA(h, plaunch(h, PK_SETUP, st,
+                         [&] { return launch_emd_average_flux(s->avg_sum, s->prim, primal, 2 * NN, inv, st); }));
+    }
   }
   return GP_OK;
 }

@@ -678,6 +678,43 @@ cudaError_t launch_emd_init(const float* m0, const float* pbar, float* p, float*
   return cudaGetLastError();
 }
 
+// Ergodic averages (the iterate averages of the convergence theorems): FP64
+// running sums of FP32 planes, and their readout.
+__global__ void k_accumulate(double* __restrict__ sum, const float* __restrict__ x, size_t n) {
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
+    sum[idx] += (double)x[idx];
+}
+
+// out = sum * scale (FP32)
+__global__ void k_scale_sum(const double* __restrict__ sum, float* __restrict__ out, size_t n, double scale) {
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x)
+    out[idx] = (float)(sum[idx] * scale);
+}
+
+// EMD average flux: m = s_sum * scale + grad q (two planes; the zero slots of
+// s and of the spectral gradient carry over)
+__global__ void k_emd_average_flux(const double* __restrict__ s_sum, const float* __restrict__ gq,
+                                   float* __restrict__ m, size_t n2, double scale) {
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n2; idx += (size_t)gridDim.x * blockDim.x)
+    m[idx] = (float)(s_sum[idx] * scale + (double)gq[idx]);
+}
+
+cudaError_t launch_accumulate(double* sum, const float* x, size_t n, cudaStream_t st) {
+  k_accumulate<<<grid_1d(n, 256), 256, 0, st>>>(sum, x, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_sum(const double* sum, float* out, size_t n, double scale, cudaStream_t st) {
+  k_scale_sum<<<grid_1d(n, 256), 256, 0, st>>>(sum, out, n, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emd_average_flux(const double* s_sum, const float* gq, float* m, size_t n2, double scale,
+                                    cudaStream_t st) {
+  k_emd_average_flux<<<grid_1d(n2, 256), 256, 0, st>>>(s_sum, gq, m, n2, scale);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sub(const float* a, const float* b, float* out, size_t n, cudaStream_t st) {
   k_sub<<<grid_1d(n, 256), 256, 0, st>>>(a, b, out, n);
   return cudaGetLastError();

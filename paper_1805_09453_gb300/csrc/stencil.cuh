@@ -57,6 +57,12 @@ cudaError_t launch_rof_init(const float* I, const float* u, const float* pbar, f
 cudaError_t launch_emd_init(const float* m0, const float* pbar, float* p, float* s, const float* g, float* d,
                             const EmdParams& P, cudaStream_t st);
 cudaError_t launch_sub(const float* a, const float* b, float* out, size_t n, cudaStream_t st);
+// Ergodic averages: sum += x (FP64 sums of FP32 planes); out = sum * scale;
+// EMD flux m = s_sum * scale + grad q over two planes (n2 = 2 N^2).
+cudaError_t launch_accumulate(double* sum, const float* x, size_t n, cudaStream_t st);
+cudaError_t launch_scale_sum(const double* sum, float* out, size_t n, double scale, cudaStream_t st);
+cudaError_t launch_emd_average_flux(const double* s_sum, const float* gq, float* m, size_t n2, double scale,
+                                    cudaStream_t st);
 cudaError_t launch_grad(const float* x, float* g, int N, cudaStream_t st);
 cudaError_t launch_copy_field(const float* a, float* b, int N, cudaStream_t st);
 

@@ -26,7 +26,8 @@ EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_l
            "dct2_poisson_static", "dct2_poisson_grad", "emd_solve_batched", "gp_autotune", "gp_tuned_row_block",
            "gp_cnn_create", "gp_cnn_destroy", "gp_cnn_last_error", "gp_cnn_num_params", "gp_cnn_get_params",
            "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned",
-           "emd_coarse_start", "gp_gap_schedule_next", "gp_rof_image_stats"]
+           "emd_coarse_start", "gp_gap_schedule_next", "gp_rof_image_stats", "gp_state_average",
+           "gp_state_read_average"]
 
 
 class Opts(C.Structure):
@@ -100,6 +101,8 @@ def lib():
                                     C.POINTER(Report), C.POINTER(i), vp]
     L.emd_coarse_start.argtypes = [vp, vp, vp, i, i, C.POINTER(Opts), vp, C.POINTER(Report), vp]
     L.gp_gap_schedule_next.argtypes = [i, d, i, d, d]
+    L.gp_state_average.argtypes = [vp, vp, i, vp]
+    L.gp_state_read_average.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_longlong), vp]
     L.gp_rof_image_stats.argtypes = [vp, vp, i, C.POINTER(d), vp]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
@@ -259,6 +262,21 @@ class State:
         p = torch.empty((2, N, N), device=dev, dtype=torch.float32)
         self.h.check(lib().gp_state_read(self.h.ptr, self._s, _ptr(prim), _ptr(p), _stream(stream)))
         return prim, p
+
+    def average(self, enable: bool = True, stream=None) -> int:
+        """Start (restart) or stop the ergodic averages of this state's iterates."""
+        return self.h.check(lib().gp_state_average(self.h.ptr, self._s, int(bool(enable)), _stream(stream)))
+
+    def read_average(self, stream=None):
+        """(primal average, p average, number of averaged steps)."""
+        N = self.N
+        dev = torch.device("cuda", self.h.device)
+        prim = torch.empty((N, N) if self.kind == "rof" else (2, N, N), device=dev, dtype=torch.float32)
+        p = torch.empty((2, N, N), device=dev, dtype=torch.float32)
+        n = C.c_longlong(0)
+        self.h.check(lib().gp_state_read_average(self.h.ptr, self._s, _ptr(prim), _ptr(p), C.byref(n),
+                                                 _stream(stream)))
+        return prim, p, int(n.value)
 
     def gap(self, stream=None):
         rep = Report()
