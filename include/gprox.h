@@ -225,7 +225,11 @@ GP_API gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, c
  * section-3.2 update m_n - tau (pbar_n - grad Lap^{-1} div pbar_n), and in
  * floating point it keeps solve errors from accumulating in div m.
  * pd_step runs n_steps >= 0 G-prox iterations (section 3, Algorithm 2) with
- * the cosine solve in precision `prec`.  gp_state_read copies the current
+ * the cosine solve in precision `prec`; in FP32 at power-of-two N every step
+ * of a call but the last hands its right-hand side to the next as row
+ * spectra (the stencil runs in the next solve's forward row pass), and the
+ * last step writes it and the gap terms, so calls of any length compose.
+ * gp_state_read copies the current
  * primal (u: N*N, or m: 2*N*N) and p (2*N*N) into caller device buffers
  * (either may be NULL).  gp_state_gap evaluates P, D, gap (and the EMD mass
  * residual) of the current iterate and synchronises `stream`.
