@@ -143,6 +143,31 @@ def test_disc_closed_form_plateaus():
     assert errs[2][0] < errs[0][0] and errs[2][1] < errs[1][1] < errs[0][1]
 
 
+def test_printed_disc_solution_is_the_garbled_one():
+    """Section 4.1 prints the disc's continuum solution (cited fixture
+    tests/golden/section41_disc.json) as (1 - 8/lambda) I + 8 pi/(lambda (16 - pi)).
+    An ROF minimiser keeps the mean of I (the fidelity's optimality condition
+    sums to zero), and the printed form does not; the oracle's converged
+    plateaus at lambda = 20 sit at the two-valued form (reading R12), not at
+    the printed values."""
+    import json
+    import os
+
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "section41_disc.json")))
+    r = g["radius"]
+    area = math.pi * r * r
+    for lam in (10.0, 20.0):
+        inside = (1 - 8 / lam) + 8 * math.pi / (lam * (16 - math.pi))
+        outside = 8 * math.pi / (lam * (16 - math.pi))
+        assert abs(area * inside + (1 - area) * outside - area) > 0.05 * area  # mean off by 10-20 %
+    lam, N = 20.0, 64
+    I = synth.disc_image(N).astype(np.float64)
+    u = O.rof_solve(I, lam, n_iters=3000)["u"]
+    a = 1 - 2 / (lam * r)
+    printed_inside = (1 - 8 / lam) + 8 * math.pi / (lam * (16 - math.pi))
+    assert abs(u[N // 2, N // 2] - a) < 0.02 < abs(u[N // 2, N // 2] - printed_inside)
+
+
 @pytest.mark.parametrize("N", [8, 32])
 def test_step_rule_straight_edge(N):
     lam = 10.0

@@ -11,7 +11,9 @@ M = N^2, the number of grid points the paper's definition names (the
 driver's default, which reproduces the paper's delta table more closely),
 the second term is the larger everywhere at these tolerances.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -75,6 +77,16 @@ def test_inputs_of_the_experiments():
     d0, d1 = synth.delta_pair(N)
     assert np.count_nonzero(d0) == 1 and d0.max() == N * N and np.count_nonzero(d1) == 1
     np.testing.assert_array_equal(np.roll(d0, (N // 4, N // 4), axis=(0, 1)), d1)
+
+
+def test_paper_tables_match_the_cited_fixture():
+    """The driver's copy of the paper's section-4 iteration counts equals the
+    cited fixture tests/golden/section4_iterations.json."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "section4_iterations.json")))
+    assert set(g["tables"]) == set(PE.PAPER_TABLES)
+    for name, t in g["tables"].items():
+        assert t["eps"] == PE.PAPER_TABLES[name]["eps"]
+        assert {int(k): v for k, v in t["iters"].items()} == PE.PAPER_TABLES[name]["iters"], name
 
 
 def test_paper_tables_are_consistent():
