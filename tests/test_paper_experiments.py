@@ -95,3 +95,37 @@ def test_paper_tables_are_consistent():
             assert len(row) == len(t["eps"]), name
             vals = [v for v in row if v is not None]
             assert vals == sorted(vals), (name, N)  # tighter tolerance, more iterations
+
+
+class _FakeState:
+    """Scripted objective sequence: after k steps the primal is P(k), the dual D(k)."""
+
+    def __init__(self, P, D):
+        self.P, self.D, self.k = P, D, 0
+
+    def step(self, n):
+        self.k += n
+
+    def gap(self):
+        return {"primal": self.P(self.k), "dual": self.D(self.k)}
+
+    def close(self):
+        pass
+
+
+def test_protocol_counts_first_iterate_below_each_tolerance(monkeypatch):
+    # F(u_n) - F* = 1/n  ->  first n with 1/n < eps is floor(1/eps) + 1 (tolerances off the reciprocals)
+    monkeypatch.setattr(PE, "_state", lambda *a, **k: _FakeState(lambda n: 2.0 + 1.0 / n, lambda n: 2.0 - 1.0 / n))
+    out, _ = PE.first_below(None, "emd", 8, None, 1.0, 2.0, [0.15, 1.5e-2, 3e-3])
+    assert out == {0.15: 7, 1.5e-2: 67, 3e-3: 334}
+    out, _ = PE.first_below(None, "emd", 8, None, 1.0, 2.0, [1e-4], max_iters=50)
+    assert out == {1e-4: None}
+
+
+def test_ground_truth_certified_by_the_gap(monkeypatch):
+    # gap 2/n: below eps/10 = 1.5e-4 first at n > 13333.3, checked in chunks of 50 -> 13350
+    monkeypatch.setattr(PE, "_state", lambda *a, **k: _FakeState(lambda n: 2.0 + 1.0 / n, lambda n: 2.0 - 1.0 / n))
+    gt = PE.ground_truth(None, "emd", 8, None, 1.0, 1.5e-3)
+    assert gt["certified"] and gt["iters"] == 13350 and abs(gt["F"] - (2.0 + 1.0 / 13350)) < 1e-15
+    gt = PE.ground_truth(None, "emd", 8, None, 1.0, 1e-3, max_iters=1000)
+    assert not gt["certified"] and gt["iters"] == 1000 and abs(gt["F"] - 2.001) < 1e-12  # smallest primal seen
