@@ -32,7 +32,6 @@ import json
 import math
 import time
 
-import numpy as np
 import torch
 
 from . import gprox, synth
