@@ -28,6 +28,10 @@ __all__ = [
     "translated_discs",
     "delta_pair",
     "random_state",
+    "cell_centres3",
+    "ball_image3",
+    "translated_balls3",
+    "gaussian_mixture_pair3",
 ]
 
 
@@ -139,3 +143,50 @@ def random_state(N: int, seed: int, n_fields: int, scale: float = 1.0):
     rng = np.random.default_rng(seed)
     return [np.ascontiguousarray(rng.uniform(-scale, scale, size=(N, N)), dtype=np.float32)
             for _ in range(n_fields)]
+
+
+# ------------------------------------------------------------- 3-D grids
+# N x N x N cell-centred grid on [0,1]^3, arrays indexed (z, y, x), x fastest.
+
+def cell_centres3(N: int):
+    """Return (x, y, z) float64 arrays of shape (N, N, N) holding cell centres."""
+    c = (np.arange(N, dtype=np.float64) + 0.5) / N
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    return x, y, z
+
+
+def ball_image3(N: int, radius: float = 0.25, centre=(0.5, 0.5, 0.5)) -> np.ndarray:
+    """Indicator of a ball (the 3-D counterpart of the section-4.1 disc)."""
+    x, y, z = cell_centres3(N)
+    img = ((x - centre[0]) ** 2 + (y - centre[1]) ** 2 + (z - centre[2]) ** 2 <= radius * radius)
+    return np.ascontiguousarray(img, dtype=np.float32)
+
+
+def translated_balls3(N: int, radius: float = 0.25, c0=(0.375, 0.375, 0.375), c1=(0.625, 0.625, 0.625)):
+    """Uniform unit-mass balls translated by (1/4, 1/4, 1/4), each normalised to h^3 sum f = 1."""
+    x, y, z = cell_centres3(N)
+    out = []
+    for c in (c0, c1):
+        f = ((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2 <= radius * radius).astype(np.float64)
+        f /= f.sum() / N ** 3
+        out.append(np.ascontiguousarray(f, dtype=np.float32))
+    return out[0], out[1]
+
+
+def gaussian_mixture_pair3(N: int, seed: int, n_comp: int = 8, floor: float = 1e-3):
+    """The 3-D form of gaussian_mixture_pair: per component centre ~ U(0.1, 0.9)^3,
+    width ~ U(0.04, 0.12), weight ~ U(0, 1) (drawn in that order, f0's
+    components first), plus the floor, normalised to h^3 sum f = 1."""
+    rng = np.random.default_rng(seed)
+    x, y, z = cell_centres3(N)
+    out = []
+    for _ in range(2):
+        params = [(rng.uniform(0.1, 0.9), rng.uniform(0.1, 0.9), rng.uniform(0.1, 0.9),
+                   rng.uniform(0.04, 0.12), rng.uniform(0.0, 1.0)) for _ in range(n_comp)]
+        f = np.zeros((N, N, N), dtype=np.float64)
+        for cx, cy, cz, sd, w in params:
+            f += w * np.exp(-((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) / (2 * sd * sd)) / (2 * np.pi * sd * sd) ** 1.5
+        f += floor
+        f /= f.sum() / N ** 3
+        out.append(np.ascontiguousarray(f, dtype=np.float32))
+    return out[0], out[1]
