@@ -44,7 +44,7 @@
 extern "C" {
 #endif
 
-#define GP_ABI_VERSION 1
+#define GP_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define GP_API __attribute__((visibility("default")))
@@ -202,13 +202,16 @@ GP_API gp_status emd_solve(gp_handle h, const float* f0, const float* f1, float*
  * checks included; a problem stops at its own tolerance.  Arrays are host
  * arrays of B device pointers; reports[B] receives one report per problem.
  *   B       1..256.  stream must be a non-default stream (graph capture).
+ *   m[b]    out, 2*N[b]*N[b] floats: the last primal iterate of problem b.
+ *   p       NULL, or B device pointers (each 2*N[b]*N[b] floats, out): the
+ *           last dual iterate of each problem.
  *   opts    as emd_solve (warm_start unsupported).
  * Returns GP_OK if every problem met the tolerance, else the first non-OK
  * per-problem status (each report's `status` holds its own).
  */
 GP_API gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const float* const* f1,
-                                   float* const* m, const int* N, const gp_opts* opts, gp_report* reports,
-                                   void* stream);
+                                   float* const* m, float* const* p, const int* N, const gp_opts* opts,
+                                   gp_report* reports, void* stream);
 
 /*
  * Explicit solver states for step-by-step driving (checkpoint / resume, tests,
@@ -283,9 +286,11 @@ GP_API gp_status gp_state_read_average(gp_handle h, gp_state s, float* primal, f
  * All calls share the static arrays: calls that overlap on the GPU (other
  * streams, other host threads) race and give wrong results.  Nothing in the
  * arrays needs to start at zero (each pass writes what the next one reads;
- * the tables are rewritten when N changes).  The first call on a device looks
- * up the arrays' device addresses with that device current and caches them;
- * make that first call before any stream capture.
+ * the tables are rewritten when N changes).  A call made while `stream` is
+ * capturing records the table kernel with the solve, and from then on every
+ * call on that device rewrites the tables as well.  The first call on a
+ * device looks up the arrays' device addresses with that device current and
+ * caches them; make that first call before any stream capture.
  */
 GP_API gp_status dct2_poisson_static(const float* b, float* x, int N, double alpha, void* stream);
 

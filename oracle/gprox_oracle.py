@@ -14,7 +14,7 @@ It is a plain, slow, obviously-correct restatement of the method in float64:
     DCT-II is used as a library primitive for that step);
   * the step-size rules of sections 3.1 / 4.1 (ROF) and 4.2 (EMD).
 
-Readings of points the paper leaves open (each one repeated in the design doc):
+Readings of points the paper leaves open:
   R1  cell-centred N x N grid on [0,1]^2, h = 1/N;
   R2  forward differences for grad with a zero last slot (zero Neumann flux),
       div = -grad^T (backward differences), Laplacian = div grad (5-point

@@ -1224,7 +1224,7 @@ gp_status emd_solve(gp_handle h, const float* f0, const float* f1, float* m, flo
 // chunk.  The graph is re-instantiated when the set of active problems
 // shrinks.
 gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const float* const* f1, float* const* m,
-                            const int* N, const gp_opts* opts, gp_report* reports, void* stream) {
+                            float* const* p_out, const int* N, const gp_opts* opts, gp_report* reports, void* stream) {
   if (!h) return GP_ERR_ARG;
   h->err.clear();
   Timer t;
@@ -1242,7 +1242,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
   for (int b = 0; b < B; ++b) {
     if (N[b] < 1 || N[b] > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
     if ((r = check_ptr(h, f0[b], "f0[b]")) != GP_OK || (r = check_ptr(h, f1[b], "f1[b]")) != GP_OK ||
-        (r = check_ptr(h, m[b], "m[b]")) != GP_OK)
+        (r = check_ptr(h, m[b], "m[b]")) != GP_OK || (p_out && (r = check_ptr(h, p_out[b], "p[b]")) != GP_OK))
       return r;
   }
   const double tau = o.tau > 0 ? o.tau : (o.tau_scale > 0 ? o.tau_scale : 1.0);
@@ -1397,6 +1397,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
     gp_state s = h->batch[b];
     const size_t NN = (size_t)N[b] * N[b];
     GP_CUDA(h, cudaMemcpyAsync(m[b], s->m, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (p_out) GP_CUDA(h, cudaMemcpyAsync(p_out[b], s->p[s->cur], 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
     if (reports[b].status != GP_OK && worst == GP_OK) worst = (gp_status)reports[b].status;
   }
   GP_CUDA(h, cudaStreamSynchronize(st));

@@ -32,13 +32,14 @@
 // the step's stencil (k_rof_step_rows_fwd, k_emd_step_rows_fwd).
 //
 // Dense path (any N): four FP32 GEMMs with the orthonormal DCT-II matrix.
-#include <cuda.h>  // CUtensorMap (the encoder is reached through the runtime's driver entry point)
 #include <math.h>
 
 #include <vector>
 
+#include "fft_common.cuh"
 #include "gp_internal.cuh"
 #include "stencil.cuh"
+#include "tma.cuh"
 
 namespace gp {
 namespace {
@@ -46,65 +47,9 @@ namespace {
 constexpr float kRsqrt2 = 0.70710678118654752440f;
 constexpr float kSqrt2 = 1.41421356237309504880f;
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-
 // Shared-memory padding: one slot per 16 complex values keeps the strided
 // butterfly stores of the first Stockham stage free of bank conflicts.
 __device__ __forceinline__ int padi(int a) { return a + (a >> 4); }
-
-// e^{DIR 2 pi i m / 16} times a, for m known at compile time after unrolling.
-template <int DIR>
-__device__ __forceinline__ float2 mul_root16(float2 a, int m) {
-  m &= 15;
-  if (m == 0) return a;
-  if (m == 8) return make_float2(-a.x, -a.y);
-  if (m == 4) return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
-  if (m == 12) return DIR < 0 ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
-  const float C1 = 0.92387953251128675613f;  // cos(pi/8)
-  const float C2 = 0.70710678118654752440f;  // cos(pi/4)
-  const float C3 = 0.38268343236508977173f;  // cos(3pi/8)
-  const float c[16] = {1.f, C1, C2, C3, 0.f, -C3, -C2, -C1, -1.f, -C1, -C2, -C3, 0.f, C3, C2, C1};
-  const float s[16] = {0.f, C3, C2, C1, 1.f, C1, C2, C3, 0.f, -C3, -C2, -C1, -1.f, -C1, -C2, -C3};
-  return cmul(a, make_float2(c[m], DIR < 0 ? -s[m] : s[m]));
-}
-
-__host__ __device__ constexpr int brev_small(int i, int R) {
-  int r = 0;
-  for (int b = 1; b < R; b <<= 1) r = (r << 1) | ((i & b) ? 1 : 0);
-  return r;
-}
-
-// In-register R-point DFT (R = 2, 4, 8, 16), natural order in and out:
-// iterative radix-2 decimation in time on bit-reversed input.
-template <int R, int DIR>
-__device__ __forceinline__ void dft_reg(float2* v) {
-#pragma unroll
-  for (int i = 0; i < R; ++i) {
-    const int j = brev_small(i, R);
-    if (j > i) {
-      float2 t = v[i];
-      v[i] = v[j];
-      v[j] = t;
-    }
-  }
-#pragma unroll
-  for (int half = 1; half < R; half <<= 1) {
-#pragma unroll
-    for (int i = 0; i < R; i += 2 * half) {
-#pragma unroll
-      for (int k = 0; k < half; ++k) {
-        const float2 b = mul_root16<DIR>(v[i + k + half], k * (8 / half));
-        const float2 a = v[i + k];
-        v[i + k] = cadd(a, b);
-        v[i + k + half] = csub(a, b);
-      }
-    }
-  }
-}
 
 // Twiddles w_r = e^{DIR 2 pi i r m / N}, r < R, from at most four table loads
 // (w1, w2, w4, w8); the others are products of two or three of them.
@@ -932,43 +877,6 @@ __global__ void __launch_bounds__((PAR ? 3 : 1) * FftCfg<LOG2N>::TPF, (LOG2N == 
 // the column pair in (one box of up to 256 row blocks per copy, counted on an
 // mbarrier) and each synthesis out (staged in the transform buffer, one bulk
 // tensor store per box), and the threads only touch shared memory.
-constexpr uint32_t kTmaWaitLimit = 1u << 22;  // try_wait rounds before a copy is declared lost
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  for (uint32_t it = 0; it < kTmaWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int c0, int c1, int c2,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int c0, int c1, int c2, uint32_t src) {
-  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
-                   reinterpret_cast<uint64_t>(tm)),
-               "r"(c0), "r"(c1), "r"(c2), "r"(src)
-               : "memory");
-}
-
 // Same computation as k_dct_cols_grad.  tm_in: box {4, 2, BOXR} over `in`;
 // tm_a: box {4, 2, BOXR} over A; tm_b: box {4, 1, BOXR} over B.  PAR (N = 512,
 // 1024): three groups of TPF threads run the three syntheses at once, each in
@@ -1355,37 +1263,6 @@ cudaError_t set_smem(K k, size_t bytes) {
 // Tensor map of an interleaved-spectra plane as {4 rows, N columns, N/4 row
 // blocks}, box {4, ncols, min(256, N/4)}; false when the driver's encoder is
 // unavailable or refuses.
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled_fn() {
-  static EncodeTiledFn fn = [] {
-    void* f = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess) {
-      cudaGetLastError();
-      f = nullptr;
-    }
-    return reinterpret_cast<EncodeTiledFn>(f);
-  }();
-  return fn;
-}
-
-bool encode_b4_map(CUtensorMap* m, const float* base, int N, int ncols) {
-  EncodeTiledFn fn = encode_tiled_fn();
-  if (!fn || ((uintptr_t)base & 15u)) return false;
-  const cuuint64_t dims[3] = {4, (cuuint64_t)N, (cuuint64_t)(N / 4)};
-  const cuuint64_t strides[2] = {16, (cuuint64_t)N * 16};
-  const cuuint32_t box[3] = {4, (cuuint32_t)ncols, (cuuint32_t)(N / 4 < 256 ? N / 4 : 256)};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
 template <int LOG2N>
 cudaError_t launch_fft_pass(const DctPlan& p, int pass, const float* in, float* out, float alpha, float scale,
                             cudaStream_t st) {
@@ -1549,6 +1426,37 @@ __global__ void k_spec_scale_dense(float* __restrict__ X, const float* __restric
 }
 
 }  // namespace
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      f = nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+bool encode_b4_map(CUtensorMap* m, const float* base, int N, int ncols) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn || ((uintptr_t)base & 15u)) return false;
+  const cuuint64_t dims[3] = {4, (cuuint64_t)N, (cuuint64_t)(N / 4)};
+  const cuuint64_t strides[2] = {16, (cuuint64_t)N * 16};
+  const cuuint32_t box[3] = {4, (cuuint32_t)ncols, (cuuint32_t)(N / 4 < 256 ? N / 4 : 256)};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp, float alpha,
                                  float scale, cudaStream_t st) {

@@ -18,6 +18,10 @@
 //    streams, or different host threads) race and give wrong results.  No part
 //    of the scratch needs to start at zero: every pass writes the whole region
 //    a later pass reads; the tables are rewritten whenever N changes.
+//  * a call made while its stream is capturing records the table kernel with
+//    the solve, and from then on every call on that device rewrites the
+//    tables too: a recorded call may later rewrite them at any time, so the
+//    size they hold is no longer known on the host.
 //  * the first call on a device looks up the arrays' device addresses
 //    (cudaGetSymbolAddress, with that device current) and caches them; make
 //    that first call before any stream capture.
@@ -41,7 +45,8 @@ static __device__ __align__(256) float g_mu[kStaticMaxN];
 
 struct DeviceArrays {
   bool ready = false;
-  int table_n = 0;  // size the tables currently hold (0: none)
+  int table_n = 0;        // size the tables currently hold (0: none)
+  bool tables_shared = false;  // a stream capture recorded a table kernel: sizes no longer tracked
   float* scratch = nullptr;
   float2* tw = nullptr;
   float2* wq = nullptr;
@@ -114,10 +119,14 @@ extern "C" GP_API gp_status dct2_poisson_static(const float* b, float* x, int N,
     D.ready = true;
   }
   cudaStream_t st = (cudaStream_t)stream;
-  if (D.table_n != N) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess)
+    return set_err(GP_ERR_CUDA, "cudaStreamIsCapturing: %s", cudaGetErrorString(e));
+  if (cs != cudaStreamCaptureStatusNone) D.tables_shared = true;
+  if (D.tables_shared || D.table_n != N) {
     k_static_tables<<<(N + 255) / 256, 256, 0, st>>>(D.tw, D.wq, D.mu, N);
     if ((e = cudaGetLastError()) != cudaSuccess) return set_err(GP_ERR_CUDA, "table kernel: %s", cudaGetErrorString(e));
-    D.table_n = N;
+    D.table_n = D.tables_shared ? 0 : N;
   }
   gp::DctPlan p;
   p.N = N;

@@ -19,6 +19,7 @@ GP_OK, GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_MAXITER, GP_ERR_NONFINITE, GP_ERR_DIVERGE
 STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_CUDA", 3: "GP_ERR_MAXITER", 4: "GP_ERR_NONFINITE",
                 5: "GP_ERR_DIVERGED", 6: "GP_ERR_MASS", 7: "GP_ERR_UNSUPPORTED"}
 PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
+ABI_VERSION = 2  # GP_ABI_VERSION of include/gprox.h that these signatures follow
 
 EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_last_error", "dct2_poisson",
            "rof_solve", "emd_solve", "gp_state_create_rof", "gp_state_create_emd", "pd_step", "gp_state_read",
@@ -63,6 +64,8 @@ def lib():
     L = C.CDLL(_LIB_PATH)
     vp, i, d = C.c_void_p, C.c_int, C.c_double
     L.gp_abi_version.restype = i
+    if L.gp_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"{_LIB_PATH} has ABI {L.gp_abi_version()}, the binding expects {ABI_VERSION}: rebuild it")
     L.gp_default_opts.argtypes = [C.POINTER(Opts)]
     L.gp_create.argtypes = [C.POINTER(vp), i]
     L.gp_destroy.argtypes = [vp]
@@ -82,8 +85,8 @@ def lib():
     L.gp_autotune.argtypes = [vp, i, C.c_char_p, vp]
     L.gp_tuned_row_block.argtypes = [vp, C.c_char_p, i]
     L.gp_tuned_row_block.restype = i
-    L.emd_solve_batched.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(i),
-                                    C.POINTER(Opts), C.POINTER(Report), vp]
+    L.emd_solve_batched.argtypes = [vp, i, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                    C.POINTER(i), C.POINTER(Opts), C.POINTER(Report), vp]
     L.gp_profile.argtypes = [vp, i]
     L.gp_cnn_create.argtypes = [vp, i, i, C.c_ulonglong, C.POINTER(vp)]
     L.gp_cnn_destroy.argtypes = [vp]
@@ -122,6 +125,27 @@ def _ptr(t):
     if t.dtype != torch.float32 or not t.is_contiguous():
         raise TypeError("expected a contiguous float32 tensor")
     return C.c_void_p(t.data_ptr())
+
+
+def _side(t, name="array"):
+    """Grid side N of an (N, N) tensor (ValueError for any other shape)."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if t.dim() != 2 or t.shape[0] != t.shape[1]:
+        raise ValueError(f"{name}: expected an (N, N) grid, got shape {tuple(t.shape)}")
+    return int(t.shape[-1])
+
+
+def _shape(t, shape, name):
+    """Require t (if given) to have exactly `shape`: the library reads and
+    writes N*N (or 2*N*N) floats through the pointer, so a smaller tensor
+    would be overrun."""
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
 
 
 def _stream(stream):
@@ -178,21 +202,25 @@ class Handle:
 
 def dct2_poisson(h: Handle, b, x, alpha: float, prec="fp32", stream=None) -> int:
     """x = (alpha - Lap)^{-1} b (Neumann) -- see include/gprox.h."""
-    N = b.shape[-1]
+    N = _side(b, "b")
+    _shape(x, (N, N), "x")
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     return lib().dct2_poisson(h.ptr, _ptr(b), _ptr(x), int(N), float(alpha), p, _stream(stream))
 
 
 def dct2_poisson_grad(h: Handle, b, g, alpha: float, prec="fp32", stream=None) -> int:
     """g (2, N, N) = forward-difference gradient of (alpha - Lap)^{-1} b -- see include/gprox.h."""
-    N = b.shape[-1]
+    N = _side(b, "b")
+    _shape(g, (2, N, N), "g")
     p = PREC[prec] if isinstance(prec, str) else int(prec)
     return lib().dct2_poisson_grad(h.ptr, _ptr(b), _ptr(g), int(N), float(alpha), p, _stream(stream))
 
 
 def dct2_poisson_static(b, x, alpha: float, stream=None) -> int:
     """dct2_poisson without device allocation (static scratch, N <= 1024) -- see include/gprox.h."""
-    return lib().dct2_poisson_static(_ptr(b), _ptr(x), int(b.shape[-1]), float(alpha), _stream(stream))
+    N = _side(b, "b")
+    _shape(x, (N, N), "x")
+    return lib().dct2_poisson_static(_ptr(b), _ptr(x), N, float(alpha), _stream(stream))
 
 
 def static_last_error() -> str:
@@ -202,31 +230,50 @@ def static_last_error() -> str:
 
 def rof_solve(h: Handle, I, u, p=None, lam: float = 8.0, opts: Opts | None = None, stream=None):
     """ROF G-prox PDHG solve; returns (status, report dict)."""
+    N = _side(I, "I")
+    _shape(u, (N, N), "u")
+    _shape(p, (2, N, N), "p")
     rep = Report()
-    st = lib().rof_solve(h.ptr, _ptr(I), _ptr(u), _ptr(p), int(I.shape[-1]), float(lam),
+    st = lib().rof_solve(h.ptr, _ptr(I), _ptr(u), _ptr(p), N, float(lam),
                          C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
     return st, rep.as_dict()
 
 
 def emd_solve(h: Handle, f0, f1, m, p=None, phi=None, opts: Opts | None = None, stream=None):
     """L1 EMD G-prox PDHG solve; returns (status, report dict)."""
+    N = _side(f0, "f0")
+    _shape(f1, (N, N), "f1")
+    _shape(m, (2, N, N), "m")
+    _shape(p, (2, N, N), "p")
+    _shape(phi, (N, N), "phi")
     rep = Report()
-    st = lib().emd_solve(h.ptr, _ptr(f0), _ptr(f1), _ptr(m), _ptr(p), _ptr(phi), int(f0.shape[-1]),
+    st = lib().emd_solve(h.ptr, _ptr(f0), _ptr(f1), _ptr(m), _ptr(p), _ptr(phi), N,
                          C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
     return st, rep.as_dict()
 
 
-def emd_solve_batched(h: Handle, f0s, f1s, ms, opts: Opts | None = None, stream=None):
+def emd_solve_batched(h: Handle, f0s, f1s, ms, opts: Opts | None = None, stream=None, ps=None):
     """Batched EMD solve of independent problems; returns (status, [report dicts]).
+    ms[b] (and ps[b] when ps is given) receive each problem's last m (and p).
 
     `stream` (or the current torch stream) must not be the default stream."""
     B = len(f0s)
+    if len(f1s) != B or len(ms) != B or (ps is not None and len(ps) != B):
+        raise ValueError("f0s, f1s, ms (and ps) must have one entry per problem")
+    sides = []
+    for b in range(B):
+        N = _side(f0s[b], f"f0s[{b}]")
+        _shape(f1s[b], (N, N), f"f1s[{b}]")
+        _shape(ms[b], (2, N, N), f"ms[{b}]")
+        if ps is not None:
+            _shape(ps[b], (2, N, N), f"ps[{b}]")
+        sides.append(N)
     P = C.c_void_p * B
     reps = (Report * B)()
-    Ns = (C.c_int * B)(*[int(f.shape[-1]) for f in f0s])
+    Ns = (C.c_int * B)(*sides)
     st = lib().emd_solve_batched(h.ptr, B, P(*[_ptr(x) for x in f0s]), P(*[_ptr(x) for x in f1s]),
-                                 P(*[_ptr(x) for x in ms]), Ns, C.byref(opts) if opts is not None else None,
-                                 reps, _stream(stream))
+                                 P(*[_ptr(x) for x in ms]), P(*[_ptr(x) for x in ps]) if ps is not None else None,
+                                 Ns, C.byref(opts) if opts is not None else None, reps, _stream(stream))
     return st, [r.as_dict() for r in reps]
 
 
@@ -241,6 +288,11 @@ class State:
         self._s = C.c_void_p()
         sigma = 1.0 / tau if sigma is None else sigma
         self._keep = (I, f0, f1)  # inputs must outlive the state
+        for t, nm in ((I, "I"), (f0, "f0"), (f1, "f1")):
+            _shape(t, (N, N), nm)
+        for t, nm in ((p0, "p0"), (pbar0, "pbar0")):
+            _shape(t, (2, N, N), nm)
+        _shape(primal0, (N, N) if kind == "rof" else (2, N, N), "primal0")
         if kind == "rof":
             st = lib().gp_state_create_rof(h.ptr, C.byref(self._s), _ptr(I), int(N), float(lam), float(tau),
                                            float(sigma), _ptr(primal0), _ptr(p0), _ptr(pbar0), _stream(stream))
@@ -307,7 +359,7 @@ def tuned_row_block(h: Handle, kernel: str, N: int) -> int:
 def rof_image_stats(h: Handle, I, stream=None):
     """(||I||_TV, ||grad I||_L2, ||I - mean I||^2_L2), reduced on the GPU."""
     out = (C.c_double * 3)()
-    h.check(lib().gp_rof_image_stats(h.ptr, _ptr(I), int(I.shape[-1]), out, _stream(stream)))
+    h.check(lib().gp_rof_image_stats(h.ptr, _ptr(I), _side(I, "I"), out, _stream(stream)))
     return float(out[0]), float(out[1]), float(out[2])
 
 
@@ -336,9 +388,12 @@ def pd_step(state: State, n_steps: int, prec="fp32", stream=None) -> int:
     return state.step(n_steps, prec, stream)
 
 
-def _ptr_array(ts):
+def _ptr_array(ts, shape=None, name="arrays"):
     if ts is None:
         return None
+    if shape is not None:
+        for b, t in enumerate(ts):
+            _shape(t, shape, f"{name}[{b}]")
     P = C.c_void_p * len(ts)
     return P(*[_ptr(t) for t in ts])
 
@@ -385,17 +440,23 @@ class Cnn:
 
     def forward(self, f0s, f1s, priors=None, stream=None):
         """phi (B, N, N), mean-free, for lists of (N, N) device tensors (priors: list or None)."""
-        B, N = len(f0s), int(f0s[0].shape[-1])
+        B, N = len(f0s), _side(f0s[0], "f0s[0]")
+        if len(f1s) != B or (priors is not None and len(priors) != B):
+            raise ValueError("f0s, f1s (and priors) must have one entry per sample")
         phi = torch.empty((B, N, N), device=f0s[0].device, dtype=torch.float32)
-        self.check(lib().gp_cnn_forward(self._n, B, _ptr_array(f0s), _ptr_array(f1s), _ptr_array(priors), N,
-                                        _ptr(phi), _stream(stream)))
+        self.check(lib().gp_cnn_forward(self._n, B, _ptr_array(f0s, (N, N), "f0s"), _ptr_array(f1s, (N, N), "f1s"),
+                                        _ptr_array(priors, (N, N), "priors"), N, _ptr(phi), _stream(stream)))
         return phi
 
     def loss_grad(self, f0s, f1s, targets, priors=None, want_grad=False, want_loss=True, stream=None):
         """Forward + loss + backward; returns (loss or None, gradient (numpy) or None)."""
         import numpy as np
 
-        B, N = len(f0s), int(f0s[0].shape[-1])
+        B, N = len(f0s), _side(f0s[0], "f0s[0]")
+        if len(f1s) != B or len(targets) != B or (priors is not None and len(priors) != B):
+            raise ValueError("f0s, f1s, targets (and priors) must have one entry per sample")
+        for nm, ts in (("f0s", f0s), ("f1s", f1s), ("targets", targets), ("priors", priors)):
+            _ptr_array(ts, (N, N), nm)
         loss = C.c_double(float("nan"))
         g = np.empty(self.num_params, np.float32) if want_grad else None
         self.check(lib().gp_cnn_loss_grad(self._n, B, _ptr_array(f0s), _ptr_array(f1s), _ptr_array(priors),
@@ -422,10 +483,15 @@ def emd_solve_learned(h: Handle, net: Cnn, f0, f1, m, p=None, phi=None, opts: Op
                       coarse_factor: int = 4, coarse_opts: Opts | None = None, stream=None):
     """EMD solve from the best (by the gap at n = 0) of the learned, prior and zero
     starts; returns (status, report dict with 'start': 'zero' | 'learned' | 'prior')."""
+    N = _side(f0, "f0")
+    _shape(f1, (N, N), "f1")
+    _shape(m, (2, N, N), "m")
+    _shape(p, (2, N, N), "p")
+    _shape(phi, (N, N), "phi")
     rep = Report()
     used = C.c_int(0)
     st = lib().emd_solve_learned(h.ptr, net._n, _ptr(f0), _ptr(f1), _ptr(m), _ptr(p), _ptr(phi),
-                                 int(f0.shape[-1]), int(coarse_factor),
+                                 N, int(coarse_factor),
                                  C.byref(coarse_opts) if coarse_opts is not None else None,
                                  C.byref(opts) if opts is not None else None, C.byref(rep), C.byref(used),
                                  _stream(stream))
@@ -437,7 +503,9 @@ def emd_solve_learned(h: Handle, net: Cnn, f0, f1, m, p=None, phi=None, opts: Op
 def emd_coarse_start(h: Handle, f0, f1, factor: int, opts: Opts | None = None, phi=None, stream=None):
     """Potential of the EMD solved on an N/factor grid, interpolated to N x N;
     returns (status, phi, coarse report dict)."""
-    N = int(f0.shape[-1])
+    N = _side(f0, "f0")
+    _shape(f1, (N, N), "f1")
+    _shape(phi, (N, N), "phi")
     if phi is None:
         phi = torch.empty((N, N), device=f0.device, dtype=torch.float32)
     rep = Report()

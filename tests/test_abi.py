@@ -33,7 +33,12 @@ def test_library_exports_every_declared_symbol(libpath):
     for name in _declared():
         assert hasattr(L, name), name
     L.gp_abi_version.restype = ctypes.c_int
-    assert L.gp_abi_version() == 1
+    src = open(os.path.join(ROOT, "include", "gprox.h")).read()
+    want = int(re.search(r"#define GP_ABI_VERSION (\d+)", src).group(1))
+    assert L.gp_abi_version() == want
+    from paper_1805_09453_gb300 import gprox
+
+    assert gprox.ABI_VERSION == want
 
 
 def test_binding_lists_every_symbol():

@@ -233,6 +233,11 @@ def test_trained_network_cuts_iterations(h):
     print(s)
     assert all(r["warm_status"] in ("GP_OK",) for r in rows), rows
     assert s["median_warm_iters"] < 0.8 * s["median_zero_iters"], s
+    # what the network adds over its prior (the coarse-grid start alone, the
+    # same network with its head zeroed): the learned start is chosen for some
+    # pairs and saves iterations over the prior on the median pair
+    assert s["fallback_rate"] < 1.0, s
+    assert s["median_warm_iters"] < s["median_prior_iters"], s
 
 
 def test_coarse_start_at_2048(h):
