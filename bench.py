@@ -47,8 +47,10 @@ BYTES_PER_POINT = {
     "dct_tc_split": 32,    # four GEMMs, each reads two N^2 operands and writes one (contraction-bound)
     "rof_fused": 32,       # read grad u(2), p(2), I; write p(2), r   (gap steps also read u)
     "emd_fused": 48,       # read grad q(2), s(2), p(2), g; write s(2), p(2), d  (gap steps add m(2), e)
-    "rof_step_fwd": 28,    # read grad u(2), p(2), I; write p(2), row spectrum of r
-    "emd_step_fwd": 48,    # read grad q(2), s(2), p(2), g; write s(2), p(2), row spectrum of d
+    # N = 4096: one kernel per non-gap step = the solve's row syntheses + the step + the next
+    # forward row pass (other sizes: the step + the next forward row pass, grad u / grad q read)
+    "rof_step_fwd": 32,    # read A, B (column syntheses), p(2), I; write p(2), row spectrum of r
+    "emd_step_fwd": 48,    # read A, B, s(2), p(2), g; write s(2), p(2), row spectrum of d
 }
 
 # The same per-kernel figures as the scope table of the method counts them
@@ -56,10 +58,12 @@ BYTES_PER_POINT = {
 # pass of the cosine solve 2 words; the ROF stencil step u, p(2), I in and
 # p(2), r out; the EMD stencil step q, m(2), p(2), pbar(2) in and m(2),
 # p(2), pbar(2), d out; a stencil step fused with the next forward row pass
-# counts both.  Per iteration: ROF 13 words = 52 B, EMD 20 words = 80 B.
+# counts all of them (at N = 4096 the step kernel also runs the solve's row
+# syntheses: step + two row passes).  Per iteration: ROF 13 words = 52 B, EMD
+# 20 words = 80 B.
 SCOPE_BYTES_PER_POINT = {
     "dct_rows_fwd": 8, "dct_cols_solve": 8, "dct_rows_inv": 8, "dct_cols_grad": 8, "dct_rows_grad": 8,
-    "rof_fused": 28, "emd_fused": 56, "rof_step_fwd": 36, "emd_step_fwd": 64,
+    "rof_fused": 28, "emd_fused": 56, "rof_step_fwd": 44, "emd_step_fwd": 72,
 }
 SCOPE_BYTES_PER_ITER = {"rof": 52, "emd": 80}
 
@@ -416,7 +420,12 @@ def run_ours(args):
             t0 = time.perf_counter()
             st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, o)
             ttg["emd"] = {"seconds": time.perf_counter() - t0, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
-                          "status": rep["status_name"], "mass_residual": rep["mass_residual"]}
+                          "status": rep["status_name"], "mass_residual": rep["mass_residual"],
+                          "primal": rep["primal"], "primal_feasible": rep["primal_feasible"],
+                          "rel_gap_feasible": rep["rel_gap_feasible"],
+                          "mass_residual_feasible": rep["mass_residual_feasible"],
+                          "certificate": "stops once the corrected flux m + grad Lap^-1((f0-f1) - div m), "
+                                         "feasible to mass_residual_feasible, has rel. gap <= 1e-5"}
             u = torch.empty((N, N), device=dev)
             t0 = time.perf_counter()
             st, rep = gprox.rof_solve(h, Id, u, None, LAMBDA, o)
@@ -436,6 +445,7 @@ def run_ours(args):
                 # the network's output is exactly its prior here, so a start it wins is the prior's
                 start = "prior" if rep["start"] in ("learned", "prior") else rep["start"]
                 ttg["emd_coarse_start"] = {"seconds": sec, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
+                                           "rel_gap_feasible": rep["rel_gap_feasible"],
                                            "status": rep["status_name"], "start": start,
                                            "mass_residual": rep["mass_residual"], "coarse_factor": 4,
                                            "coarse_tol": 1e-6, "speedup": ttg["emd"]["seconds"] / sec}

@@ -94,9 +94,25 @@ typedef struct gp_report {
   double primal;         /* P at the last check: ROF energy or EMD cost sum |m| h^2 */
   double dual;           /* D at the last check (a lower bound on the optimum) */
   double rel_gap;        /* (P - D) / max(|P|, |D|) */
-  double mass_residual;  /* EMD: h^2 sum |div m - (f0 - f1)| / h^2 sum |f0 - f1|; ROF: 0 */
+  double mass_residual;  /* EMD: h^2 sum |div m - (f0 - f1)| / h^2 sum |f0 - f1| (FP32 terms at a
+                            plain check, FP64 at a certified one, see below); ROF: 0 */
   double tau, sigma;     /* step sizes used */
   double seconds;        /* host wall time of the call */
+  /* Feasibility certificate (section 3.2: P(m) bounds the optimum from above
+   * only for an m with div m = f0 - f1 exactly; D bounds it from below for
+   * any p).  EMD: at the final check, and at every check whose rel_gap met
+   * tol_rel_gap, the residual rho = (f0 - f1) - div m of the returned FP32 m
+   * is evaluated in FP64 (mass_residual then reports it), c = Lap^{-1} rho is
+   * solved, and m~ = m + grad c is the corrected, feasible flux:
+   *   primal_feasible        = h^2 sum |m~|  (>= the optimum)
+   *   rel_gap_feasible       = (primal_feasible - D) / max(|primal_feasible|, |D|)
+   *   mass_residual_feasible = h^2 sum |div m~ - (f0 - f1)| / h^2 sum |f0 - f1|
+   * and a solve with tol_rel_gap > 0 returns GP_OK only once
+   * rel_gap_feasible <= tol_rel_gap (so the optimum lies within that of
+   * primal_feasible).  ROF (unconstrained): primal, rel_gap and 0. */
+  double primal_feasible;
+  double rel_gap_feasible;
+  double mass_residual_feasible;
 } gp_report;
 
 typedef struct gp_handle_s* gp_handle;
@@ -175,6 +191,28 @@ GP_API gp_status dct2_poisson_grad(gp_handle h, const float* b, float* g, int N,
  */
 GP_API gp_status rof_solve(gp_handle h, const float* I, float* u, float* p, int N, double lambda,
                     const gp_opts* opts, gp_report* report, void* stream);
+
+/*
+ * rof_solve_cp2: the comparison method of section 4.1 (Tables 4-5), the
+ * accelerated primal-dual hybrid gradient iteration ("CP2") for the same ROF
+ * problem as rof_solve.  It takes no linear solve: per iteration
+ *   p_{n+1} = proj(p_n + sigma_n grad ubar_n),
+ *   u_{n+1} = (u_n + tau_n div p_{n+1} + tau_n lambda I) / (1 + tau_n lambda),
+ *   ubar_{n+1} = u_{n+1} + theta_n (u_{n+1} - u_n),
+ *   theta_n = 1/sqrt(1 + 2 lambda tau_n), tau_{n+1} = theta_n tau_n, sigma_{n+1} = sigma_n / theta_n,
+ * exploiting the lambda-strong convexity of the fidelity term; it needs many
+ * more iterations than G-prox PDHG, increasingly so as the grid refines.
+ *   I, u, p  as rof_solve (u out; p may be NULL; warm_start: u and p in/out).
+ *   opts     max_iters, tol_rel_gap, gap_every (0: 10), warm_start as
+ *            rof_solve; tau / sigma > 0 set tau_0 / sigma_0, else both are
+ *            1/sqrt(||Lap||) (section 4.1), tau_0 times / sigma_0 divided by
+ *            tau_scale when that is > 0.  prec and use_graph are ignored.
+ * The report's tau / sigma are the last step sizes; the gap is the ROF gap
+ * of rof_solve.  N in [2, 8192].  Uses (and resets) the handle's cached ROF
+ * buffers of size N.
+ */
+GP_API gp_status rof_solve_cp2(gp_handle h, const float* I, float* u, float* p, int N, double lambda,
+                               const gp_opts* opts, gp_report* report, void* stream);
 
 /*
  * emd_solve: L1 earth mover's distance min sum_x |m(x)| h^2 s.t. div m = f0 - f1

@@ -62,12 +62,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)
-        if res.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")
-        return obj
+        return obj, cmd, res
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
-        objs = list(ex.map(compile_one, sources()))
+        results = list(ex.map(compile_one, sources()))
+    objs = []
+    for obj, cmd, res in results:
+        if res.returncode != 0:
+            # a compiler that crashed (rather than reporting errors) gets one more
+            # try on its own, without the other translation units running beside it
+            if "error" not in (res.stdout + res.stderr):
+                res = subprocess.run(cmd, capture_output=True, text=True)
+            if res.returncode != 0:
+                raise RuntimeError(f"nvcc failed on {cmd[-3]}:\n{res.stdout}\n{res.stderr}")
+        objs.append(obj)
     tmp = LIB + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     res = subprocess.run(cmd, capture_output=True, text=True)

@@ -35,14 +35,16 @@ enum {
   PK_SETUP,
   PK_ROF_STEP_FWD,
   PK_EMD_STEP_FWD,
+  PK_CP2_DUAL,
+  PK_CP2_PRIMAL,
   PK_COUNT
 };
 static const char* kProfNames[PK_COUNT] = {"dct_rows_fwd", "dct_cols_solve", "dct_rows_inv", "dct_cols_grad",
                                            "dct_rows_grad", "dct_dense",     "dct_tc_split", "rof_fused",
                                            "emd_fused",     "reduce",        "setup",         "rof_step_fwd",
-                                           "emd_step_fwd"};
+                                           "emd_step_fwd",  "cp2_dual",      "cp2_primal"};
 // Kernel launches behind one recorded launch of a class.
-static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 4, 1, 1, 1, 1, 1, 1};
+static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 4, 1, 1, 1, 1, 1, 1, 1, 1};
 
 struct Profiler {
   bool on = false;
@@ -277,8 +279,10 @@ gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, 
   if (p->fft && prec == GP_PREC_FP32) {
     float* A = tmp;
     float* B = tmp + NN;
-    if (!b_rows)
-      GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return dct_fft_pass(*p, 0, b, A, a, sc, st); }));
+    if (!b_rows)  // N = 4096: pair-interleaved spectra for the register-resident passes
+      GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] {
+                return grad4k_supported(*p) ? rows_fwd_4k(*p, b, A, st) : dct_fft_pass(*p, 0, b, A, a, sc, st);
+              }));
     const float* in = b_rows ? b : A;
     GP_CUDA(h, plaunch(h, PK_DCT_COLS_GRAD, st, [&] { return dct_grad_cols(*p, in, A, B, a, sc, st); }));
     GP_CUDA(h, plaunch(h, PK_DCT_ROWS_GRAD, st,
@@ -301,6 +305,7 @@ gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, 
                    want_phi ? 8 : 7));
     return GP_OK;
   }
+  if (!phi) return fail(h, GP_ERR_ARG, "internal: the dense gradient solve needs a plane for the solution");
   if ((s = solve(h, N, b, phi, tmp, alpha, scale, prec, false, st)) != GP_OK) return s;
   GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_grad(phi, g2, N, st); }));  // differences of the solution
   return GP_OK;
@@ -442,10 +447,49 @@ const DctPlan* fused_step_plan(gp_state s, int prec) {
   return it != s->h->plans.end() && it->second.fft ? &it->second : nullptr;
 }
 
+// N = 4096: the plan of the fused row pass (one kernel per non-gap step for
+// the solve's row syntheses, the step and the next forward row pass), else null.
+const DctPlan* step4k_plan(gp_state s, int prec) {
+  if (prec != GP_PREC_FP32 || !s->rh || !s->vec || s->avg_sum) return nullptr;
+  const DctPlan* p = nullptr;
+  if (get_plan(s->h, s->N, &p) != GP_OK) return nullptr;
+  return grad4k_supported(*p) ? p : nullptr;
+}
+
 gp_status rof_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cudaStream_t st) {
   gp_handle h = s->h;
   const int N = s->N;
   RofParams P{N, (float)N, (float)((double)N * N), (float)(s->lam * s->tau), (float)s->tau, (float)s->sigma};
+  if (const DctPlan* p4 = step4k_plan(s, prec)) {
+    // per step: the column pass of the solve, then either the fused row pass
+    // (rows of the solve + step + next forward rows) or, on the last step of
+    // the call, the gradient row pass and the unfused step (r and gap terms)
+    const size_t NN = (size_t)N * N;
+    float* A = s->tmp;
+    float* B = s->tmp + NN;
+    const float a = (float)(s->lam * s->tau);
+    for (int k = 0; k < n_steps; ++k) {
+      const bool last = k == n_steps - 1, g = gap_last && last;
+      if (k == 0) GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return rows_fwd_4k(*p4, s->r, A, st); }));
+      GP_CUDA(h, plaunch(h, PK_DCT_COLS_GRAD, st,
+                         [&] { return grad_cols_4k(*p4, k == 0 ? A : s->rh, A, B, a, 1.f, st); }));
+      float* pin = s->p[s->cur];
+      float* pout = s->p[1 - s->cur];
+      if (!last) {
+        GP_CUDA(h, plaunch(h, PK_ROF_STEP_FWD, st,
+                           [&] { return rof_rows_step_4k(*p4, A, B, pin, s->Ic, pout, s->rh, P, st); }));
+      } else {
+        GP_CUDA(h, plaunch(h, PK_DCT_ROWS_GRAD, st,
+                           [&] { return grad_rows_4k(*p4, A, B, s->gu, s->gu + NN, g ? s->prim : nullptr, st); }));
+        GP_CUDA(h, plaunch(h, PK_ROF_FUSED, st, [&] {
+                  return launch_rof_fused(s->gu, s->prim, pin, s->Ic, pout, s->r, s->part, P, s->vec, g, s->rb, st);
+                }));
+      }
+      s->cur = 1 - s->cur;
+      s->n++;
+    }
+    return GP_OK;
+  }
   for (int k = 0; k < n_steps; ++k) {
     const bool g = gap_last && (k == n_steps - 1);
     const DctPlan* fp = fused_step_plan(s, prec);  // the plan exists after the first solve
@@ -482,6 +526,34 @@ gp_status emd_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
   gp_handle h = s->h;
   const int N = s->N;
   EmdParams P{N, (float)N, (float)s->tau, (float)s->sigma};
+  if (const DctPlan* p4 = step4k_plan(s, prec)) {  // as in rof_steps_direct
+    const size_t NN = (size_t)N * N;
+    float* A = s->tmp;
+    float* B = s->tmp + NN;
+    for (int k = 0; k < n_steps; ++k) {
+      const bool last = k == n_steps - 1, g = gap_last && last;
+      const int c = s->cur;
+      // grad q, q = Lap^{-1} d  <=>  (0 - Lap) q = -d
+      if (k == 0) GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return rows_fwd_4k(*p4, s->r, A, st); }));
+      GP_CUDA(h, plaunch(h, PK_DCT_COLS_GRAD, st,
+                         [&] { return grad_cols_4k(*p4, k == 0 ? A : s->rh, A, B, 0.f, -1.f, st); }));
+      if (!last) {
+        GP_CUDA(h, plaunch(h, PK_EMD_STEP_FWD, st, [&] {
+                  return emd_rows_step_4k(*p4, A, B, s->s[c], s->p[c], s->g, s->s[1 - c], s->p[1 - c], s->rh, P, st);
+                }));
+      } else {
+        GP_CUDA(h, plaunch(h, PK_DCT_ROWS_GRAD, st,
+                           [&] { return grad_rows_4k(*p4, A, B, s->prim, s->prim + NN, nullptr, st); }));
+        GP_CUDA(h, plaunch(h, PK_EMD_FUSED, st, [&] {
+                  return launch_emd_fused(s->prim, s->s[c], s->p[c], s->g, s->s[1 - c], s->p[1 - c], s->r, s->m, s->e,
+                                          s->part, P, s->vec, g, s->rb, st);
+                }));
+      }
+      s->cur = 1 - s->cur;
+      s->n++;
+    }
+    return GP_OK;
+  }
   for (int k = 0; k < n_steps; ++k) {
     const DctPlan* fp = fused_step_plan(s, prec);
     const bool rows_in = fp && k > 0;
@@ -662,10 +734,50 @@ void state_gap_finish(gp_state s, const double* v, gp_report* rep) {
   if (s->kind == KIND_ROF) {
     finish_report(rep, h2 * (v[0] + 0.5 * s->lam * v[1]), -h2 * v[2] - h2 * v[3] / (2.0 * s->lam));
     rep->mass_residual = 0.0;
+    rep->primal_feasible = rep->primal;  // no constraint on u: every iterate is feasible
+    rep->rel_gap_feasible = rep->rel_gap;
+    rep->mass_residual_feasible = 0.0;
   } else {
     finish_report(rep, h2 * v[0], h2 * v[2] / fmax(1.0, v[3]));
     rep->mass_residual = s->mass_den > 0 ? v[1] / s->mass_den : v[1];
+    rep->primal_feasible = rep->rel_gap_feasible = rep->mass_residual_feasible = NAN;  // not certified yet
   }
+}
+
+// EMD feasibility certificate of the current m (after state_gap filled P, D):
+// D bounds the optimum from below for any p, P(m) from above only for a
+// feasible m (section 3.2's constraint div m = f0 - f1), and an FP32 m is
+// feasible only up to its rounding times 1/h.  The residual rho of the stored
+// m is taken in FP64, c = Lap^{-1} rho solved (FP32 cosine solve: its relative
+// error multiplies the already small rho), and the corrected flux
+// m~ = m + grad c is feasible up to the residual the correction leaves, which
+// is measured too.  Uses e, prim and tmp, which are free between chunks.
+gp_status emd_certify(gp_state s, gp_report* rep, cudaStream_t st) {
+  gp_handle h = s->h;
+  const int N = s->N;
+  const size_t NN = (size_t)N * N;
+  const int nd = reduce_blocks_1d(NN);
+  gp_status r = ensure_res(h);
+  if (r != GP_OK) return r;
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st,
+                     [&] { return launch_emd_residual64(s->m, s->f0, s->f1, s->e, N, s->part, nd, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nd, 1, 0u, h->dres, st); }));
+  // grad c with Lap c = rho  <=>  (0 - Lap) c = -rho.  Sizes without the fast
+  // transform difference the dense solve's output, which needs a plane: c
+  // goes over rho in e (the dense solve consumes its input first).
+  if ((r = solve_grad(h, N, s->e, s->prim, s->e, false, s->tmp, 0.0, -1.0, GP_PREC_FP32, st)) != GP_OK) return r;
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] {
+            return launch_emd_corrected(s->m, s->prim, s->f0, s->f1, N, s->part + nd, nd, st);
+          }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part + nd, nd, 2, 0u, h->dres + 1, st); }));
+  if ((r = fetch(h, 3, st)) != GP_OK) return r;
+  const double h2 = 1.0 / ((double)N * N), den = s->mass_den > 0 ? s->mass_den : 1.0;
+  rep->mass_residual = h->hres[0] / den;
+  rep->primal_feasible = h2 * h->hres[1];
+  rep->mass_residual_feasible = h->hres[2] / den;
+  const double sc = fmax(fabs(rep->primal_feasible), fabs(rep->dual));
+  rep->rel_gap_feasible = sc > 0 ? (rep->primal_feasible - rep->dual) / sc : 0.0;
+  return GP_OK;
 }
 
 gp_status state_gap(gp_state s, gp_report* rep, int prec, cudaStream_t st) {
@@ -807,6 +919,9 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
   DivergenceWatch watch;
   gp_status status = o.tol_rel_gap > 0 ? GP_ERR_MAXITER : GP_OK;
   rep->primal = rep->dual = rep->rel_gap = rep->mass_residual = NAN;
+  rep->primal_feasible = rep->rel_gap_feasible = rep->mass_residual_feasible = NAN;
+  const bool emd = s->kind == KIND_EMD;
+  bool certified = false;  // the report's certificate belongs to the current iterate
   gp_status r;
   if (o.max_iters == 0 && (r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
   int k_next = o.gap_every > 0 ? o.gap_every : kAdaptiveMinChunk;
@@ -816,14 +931,22 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
     const int k = std::min(k_next, o.max_iters - s->n);
     if ((r = run_steps(s, k, o.prec, true, o.use_graph != 0, st)) != GP_OK) return r;
     if ((r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
+    certified = false;
     if (!isfinite(rep->primal) || !isfinite(rep->dual)) {
       status = GP_ERR_NONFINITE;
       fail(h, status, "non-finite objective: the iteration broke down");
       break;
     }
     if (o.tol_rel_gap > 0 && rep->rel_gap <= o.tol_rel_gap) {
-      status = GP_OK;
-      break;
+      // EMD: stop only on the gap of the corrected, feasible flux
+      if (emd) {
+        if ((r = emd_certify(s, rep, st)) != GP_OK) return r;
+        certified = true;
+      }
+      if (!emd || rep->rel_gap_feasible <= o.tol_rel_gap) {
+        status = GP_OK;
+        break;
+      }
     }
     if (watch.update(rep->rel_gap)) {
       status = GP_ERR_DIVERGED;
@@ -836,6 +959,9 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
       g_prev = rep->rel_gap;
     }
   }
+  if (emd && !certified && status != GP_ERR_NONFINITE && isfinite(rep->dual) &&
+      (r = emd_certify(s, rep, st)) != GP_OK)
+    return r;
   rep->iters = s->n;
   rep->tau = s->tau;
   rep->sigma = s->sigma;
@@ -1172,6 +1298,102 @@ gp_status rof_solve(gp_handle h, const float* I, float* u, float* p, int N, doub
   return status;
 }
 
+gp_status rof_solve_cp2(gp_handle h, const float* I, float* u, float* p, int N, double lambda, const gp_opts* opts,
+                        gp_report* report, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  Timer t;
+  gp_opts o;
+  gp_default_opts(&o);
+  if (opts) o = *opts;
+  gp_report rep;
+  memset(&rep, 0, sizeof(rep));
+  gp_status r = check_opts(h, &o);
+  if (r != GP_OK) return r;
+  if (N < 2 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [2, 8192]");
+  if (!(lambda > 0) || !isfinite(lambda)) return fail(h, GP_ERR_ARG, "lambda must be finite and > 0");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  if ((r = check_ptr(h, I, "I")) != GP_OK) return r;
+  if ((r = check_ptr(h, u, "u")) != GP_OK) return r;
+  if (p && (r = check_ptr(h, p, "p")) != GP_OK) return r;
+  if (o.warm_start && !p) return fail(h, GP_ERR_ARG, "warm_start needs p");
+  cudaStream_t st = (cudaStream_t)stream;
+  gp_state s = cached_state(h, KIND_ROF, N, &r);  // its planes: u (prim), ubar (gu), p (p[0]), partials
+  if (!s) return r;
+  const size_t NN = (size_t)N * N;
+  float* us = s->prim;
+  float* ub = s->gu;
+  float* ps = s->p[0];
+  if (o.warm_start) {
+    GP_CUDA(h, cudaMemcpyAsync(us, u, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    GP_CUDA(h, cudaMemcpyAsync(ps, p, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  } else {
+    GP_CUDA(h, cudaMemsetAsync(us, 0, NN * sizeof(float), st));
+    GP_CUDA(h, cudaMemsetAsync(ps, 0, 2 * NN * sizeof(float), st));
+  }
+  GP_CUDA(h, cudaMemcpyAsync(ub, us, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  // section 4.1: tau0 = sigma0 = 1 / sqrt(||Lap||), ||Lap|| = 2 mu_{N-1} = (8 / h^2) sin^2(pi (N-1) / 2N)
+  const double PI = 3.14159265358979323846;
+  const double sn = sin(PI * (N - 1) / (2.0 * N));
+  const double t0 = 1.0 / sqrt(8.0 * (double)N * N * sn * sn);
+  const double ts = o.tau_scale > 0 ? o.tau_scale : 1.0;
+  double tau = o.tau > 0 ? o.tau : t0 * ts, sigma = o.sigma > 0 ? o.sigma : t0 / ts;
+  const int every = o.gap_every > 0 ? o.gap_every : 10;
+  const int nb = reduce_blocks_1d(NN);
+  if ((r = ensure_res(h)) != GP_OK) return r;
+  gp_status status = o.tol_rel_gap > 0 ? GP_ERR_MAXITER : GP_OK;
+  rep.primal = rep.dual = rep.rel_gap = NAN;
+  const double h2 = 1.0 / ((double)N * N);
+  auto gap = [&]() -> gp_status {
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_rof_gap(us, ps, I, N, s->part, nb, st); }));
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 4, 0u, h->dres, st); }));
+    gp_status q = fetch(h, 4, st);
+    if (q != GP_OK) return q;
+    const double* v = h->hres;
+    finish_report(&rep, h2 * (v[0] + 0.5 * lambda * v[1]), -h2 * v[2] - h2 * v[3] / (2.0 * lambda));
+    return GP_OK;
+  };
+  int n = 0;
+  if (o.max_iters == 0 && (r = gap()) != GP_OK) return r;
+  while (n < o.max_iters) {
+    const int k = std::min(every, o.max_iters - n);
+    for (int q = 0; q < k; ++q) {
+      const double theta = 1.0 / sqrt(1.0 + 2.0 * lambda * tau);
+      GP_CUDA(h, plaunch(h, PK_CP2_DUAL, st, [&] { return launch_cp2_dual(ub, ps, N, (float)sigma, st); }));
+      GP_CUDA(h, plaunch(h, PK_CP2_PRIMAL, st,
+                         [&] { return launch_cp2_primal(us, ub, ps, I, N, tau, lambda, theta, st); }));
+      tau *= theta;
+      sigma /= theta;
+    }
+    n += k;
+    if ((r = gap()) != GP_OK) return r;
+    if (!isfinite(rep.primal) || !isfinite(rep.dual)) {
+      status = fail(h, GP_ERR_NONFINITE, "non-finite objective: the iteration broke down");
+      break;
+    }
+    if (o.tol_rel_gap > 0 && rep.rel_gap <= o.tol_rel_gap) {
+      status = GP_OK;
+      break;
+    }
+  }
+  rep.iters = n;
+  rep.tau = tau;
+  rep.sigma = sigma;
+  rep.status = status;
+  rep.mass_residual = 0.0;
+  rep.primal_feasible = rep.primal;  // no constraint on u
+  rep.rel_gap_feasible = rep.rel_gap;
+  rep.mass_residual_feasible = 0.0;
+  GP_CUDA(h, cudaMemcpyAsync(u, us, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  if (p) GP_CUDA(h, cudaMemcpyAsync(p, ps, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(h, cudaStreamSynchronize(st));
+  s->partials_valid = false;  // the state's partials now hold CP2's gap terms
+  rep.seconds = t.s();
+  if (report) *report = rep;
+  return status;
+}
+
 gp_status emd_solve(gp_handle h, const float* f0, const float* f1, float* m, float* p, float* phi, int N,
                     const gp_opts* opts, gp_report* report, void* stream) {
   if (!h) return GP_ERR_ARG;
@@ -1288,6 +1510,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
   std::vector<int> active;
   for (int b = 0; b < B; ++b) active.push_back(b);
   std::vector<DivergenceWatch> watch(B);
+  std::vector<char> certified(B, 0);  // problem b's report holds the certificate of its current iterate
   cudaGraphExec_t exec = nullptr;
   int exec_k = -1;
   bool first = true;
@@ -1367,6 +1590,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
       gp_state s = h->batch[b];
       gp_report& rep = reports[b];
       state_gap_finish(s, h->bres_h + 4 * b, &rep);
+      certified[b] = false;
       rep.iters = s->n;
       rep.tau = s->tau;
       rep.sigma = s->sigma;
@@ -1375,9 +1599,13 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
       if (!isfinite(rep.primal) || !isfinite(rep.dual)) {
         rep.status = GP_ERR_NONFINITE;
         stop = true;
-      } else if (o.tol_rel_gap > 0 && rep.rel_gap <= o.tol_rel_gap) {
-        rep.status = GP_OK;
+      } else if (o.tol_rel_gap > 0 && rep.rel_gap <= o.tol_rel_gap &&
+                 (certified[b] = true, (r = emd_certify(s, &rep, st)) == GP_OK) &&
+                 rep.rel_gap_feasible <= o.tol_rel_gap) {
+        rep.status = GP_OK;  // the corrected, feasible flux's gap met the tolerance too
         stop = true;
+      } else if (r != GP_OK) {
+        return r;
       } else if (watch[b].update(rep.rel_gap)) {
         rep.status = GP_ERR_DIVERGED;
         stop = true;
@@ -1392,6 +1620,12 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
     active.swap(still);
   }
   if (exec) cudaGraphExecDestroy(exec);
+  for (int b = 0; b < B; ++b) {  // every report carries the certificate of the returned iterate
+    gp_state s = h->batch[b];
+    if (!certified[b] && reports[b].status != GP_ERR_NONFINITE && isfinite(reports[b].dual) &&
+        (r = emd_certify(s, &reports[b], st)) != GP_OK)
+      return r;
+  }
   gp_status worst = GP_OK;
   for (int b = 0; b < B; ++b) {
     gp_state s = h->batch[b];

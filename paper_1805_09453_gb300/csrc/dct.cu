@@ -1298,6 +1298,7 @@ cudaError_t launch_grad_cols(const DctPlan& p, const float* in, float* A, float*
                              cudaStream_t st) {
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  if constexpr (LOG2N == 12) return grad_cols_4k(p, in, A, B, alpha, scale, st);  // pair-interleaved spectra
   if constexpr (LOG2N >= 9) {
     constexpr bool PART = LOG2N == 9 || LOG2N == 10;
     CUtensorMap tm_in, tm_a, tm_b;
@@ -1328,6 +1329,7 @@ cudaError_t launch_grad_rows(const DctPlan& p, const float* A, const float* B, f
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
   constexpr bool PAR = LOG2N == 9 || LOG2N == 10;  // as in the column pass
+  if constexpr (LOG2N == 12) return grad_rows_4k(p, A, B, gx, gy, phi, st);
   const int groups = PAR ? 2 * (phi ? 4 : 3) : 2;
   const size_t sm = ((size_t)groups * PADN + stage_tw_entries<LOG2N>()) * sizeof(float2);
   cudaError_t e;
@@ -1458,6 +1460,18 @@ bool encode_b4_map(CUtensorMap* m, const float* base, int N, int ncols) {
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool encode_pairs_map(CUtensorMap* m, const float* base, int N) {
+  EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn || ((uintptr_t)base & 15u) || N < 512) return false;
+  const cuuint64_t dims[3] = {4, (cuuint64_t)N / 2, (cuuint64_t)N / 2};
+  const cuuint64_t strides[2] = {16, (cuuint64_t)N * 8};
+  const cuuint32_t box[3] = {4, 1, 256};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp, float alpha,
                                  float scale, cudaStream_t st) {
   const int N = p.N;
@@ -1514,7 +1528,7 @@ cudaError_t dct_grad_rows(const DctPlan& p, const float* A, const float* B, floa
 
 cudaError_t dct_emd_step_fwd(const DctPlan& p, const float* gq, const float* sin_, const float* pin, const float* g,
                              float* sout, float* pout, float* out, const EmdParams& P, cudaStream_t st) {
-  if (!p.fft || P.N != p.N) return cudaErrorInvalidValue;
+  if (!p.fft || P.N != p.N || grad4k_supported(p)) return cudaErrorInvalidValue;  // 4096: emd_rows_step_4k
 #define GP_CALL(L) launch_emd_step_fwd<L>(p, gq, sin_, pin, g, sout, pout, out, P, st)
   GP_FFT_DISPATCH(p.N, GP_CALL)
 #undef GP_CALL
@@ -1522,7 +1536,7 @@ cudaError_t dct_emd_step_fwd(const DctPlan& p, const float* gq, const float* sin
 
 cudaError_t dct_rof_step_fwd(const DctPlan& p, const float* gu, const float* pin, const float* I, float* pout,
                              float* out, const RofParams& P, cudaStream_t st) {
-  if (!p.fft || P.N != p.N) return cudaErrorInvalidValue;
+  if (!p.fft || P.N != p.N || grad4k_supported(p)) return cudaErrorInvalidValue;  // 4096: rof_rows_step_4k
 #define GP_CALL(L) launch_rof_step_fwd<L>(p, gu, pin, I, pout, out, P, st)
   GP_FFT_DISPATCH(p.N, GP_CALL)
 #undef GP_CALL

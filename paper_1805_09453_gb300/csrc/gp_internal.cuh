@@ -67,6 +67,29 @@ cudaError_t dct_grad_cols(const DctPlan& p, const float* in, float* A, float* B,
                           cudaStream_t st);
 cudaError_t dct_grad_rows(const DctPlan& p, const float* A, const float* B, float* gx, float* gy, float* phi,
                           cudaStream_t st);
+// At N = 4096 (fftreg.cu) the gradient solve runs register-resident
+// transforms on pair-interleaved spectra (rows 2q, 2q + 1 as N float2 per row
+// pair) instead of the 4-row layout: its forward row pass is rows_fwd_4k
+// (not dct_fft_pass 0), and dct_grad_cols / dct_grad_rows take and give that
+// layout; cudaErrorNotSupported (nothing launched) for other plans or when
+// the column pass's tensor maps cannot be made.
+bool grad4k_supported(const DctPlan& p);
+cudaError_t rows_fwd_4k(const DctPlan& p, const float* in, float* out, cudaStream_t st);
+cudaError_t grad_cols_4k(const DctPlan& p, const float* in, float* A, float* B, float alpha, float scale,
+                         cudaStream_t st);
+cudaError_t grad_rows_4k(const DctPlan& p, const float* A, const float* B, float* gx, float* gy, float* phi,
+                         cudaStream_t st);
+// One non-gap step fused with its solve's row syntheses and the next solve's
+// forward row pass (A, B: the column pass's outputs; out: the next row
+// spectra, pair-interleaved).  ROF: p_in, I -> p_out; EMD: s_in, p_in, g ->
+// s_out, p_out.  All pointers 16-byte aligned.
+struct EmdParams;
+struct RofParams;
+cudaError_t rof_rows_step_4k(const DctPlan& p, const float* A, const float* B, const float* pin, const float* I,
+                             float* pout, float* out, const RofParams& P, cudaStream_t st);
+cudaError_t emd_rows_step_4k(const DctPlan& p, const float* A, const float* B, const float* sin_, const float* pin,
+                             const float* g, float* sout, float* pout, float* out, const EmdParams& P,
+                             cudaStream_t st);
 // One non-gap iteration's stencil (k_emd_fused / k_rof_fused arithmetic)
 // fused with the forward row pass of the next solve: writes s', p' (EMD) or
 // p' (ROF) and, instead of the right-hand side itself, its row spectra `out`

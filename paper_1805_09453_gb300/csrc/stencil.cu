@@ -544,6 +544,53 @@ __global__ void __launch_bounds__(256) k_emd_primal(const float* __restrict__ m,
   block_reduce_store<2>(v, 0u, part);
 }
 
+// Feasibility certificate of an EMD flux (the constraint div m = f0 - f1 of
+// section 3.2).  rho = (f0 - f1) - div m, evaluated in FP64 from the stored
+// FP32 arrays (so it is the exact residual of the m a caller receives, not
+// one blurred by FP32 cancellation in the divergence), is written as FP32 for
+// the correcting solve; sum |rho| is reduced in FP64.
+__global__ void __launch_bounds__(256) k_emd_residual64(const float* __restrict__ m, const float* __restrict__ f0,
+                                                        const float* __restrict__ f1, float* __restrict__ rho,
+                                                        int N, double invh, double* __restrict__ part) {
+  double a = 0.0;
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const double mx = j < N - 1 ? (double)m[idx] : 0.0, my = i < N - 1 ? (double)m[NN + idx] : 0.0;
+    const double mxl = j > 0 ? (double)m[idx - 1] : 0.0, myu = i > 0 ? (double)m[NN + idx - N] : 0.0;
+    const double r = ((double)f0[idx] - (double)f1[idx]) - ((mx - mxl) + (my - myu)) * invh;
+    rho[idx] = (float)r;
+    a += fabs(r);
+  }
+  double v[1] = {a};
+  block_reduce_store<1>(v, 0u, part);
+}
+
+// The corrected flux m~ = m + grad c (grad c: two planes with zero slots, from
+// the spectral gradient of c = Lap^{-1} rho): sum |m~| (FP32 terms, compensated
+// sums: the objective has no 1/h amplification) and the residual left after
+// the correction, sum |(f0 - f1) - div m~|, in FP64.
+__global__ void __launch_bounds__(256) k_emd_corrected(const float* __restrict__ m, const float* __restrict__ gc,
+                                                       const float* __restrict__ f0, const float* __restrict__ f1,
+                                                       int N, double invh, double* __restrict__ part) {
+  CSum a;
+  double b = 0.0;
+  const size_t NN = (size_t)N * N;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    const bool xr = j < N - 1, yd = i < N - 1, xl = j > 0, yu = i > 0;
+    const double mx = xr ? (double)m[idx] + (double)gc[idx] : 0.0;
+    const double my = yd ? (double)m[NN + idx] + (double)gc[NN + idx] : 0.0;
+    const double mxl = xl ? (double)m[idx - 1] + (double)gc[idx - 1] : 0.0;
+    const double myu = yu ? (double)m[NN + idx - N] + (double)gc[NN + idx - N] : 0.0;
+    const float fx = (float)mx, fy = (float)my;
+    a.add(sqrtf(fx * fx + fy * fy));
+    b += fabs(((double)f0[idx] - (double)f1[idx]) - ((mx - mxl) + (my - myu)) * invh);
+  }
+  double v[2] = {a.value(), b};
+  block_reduce_store<2>(v, 0u, part);
+}
+
 // sum f0, sum f1, sum |f0 - f1|
 __global__ void __launch_bounds__(256) k_mass_stats(const float* __restrict__ f0, const float* __restrict__ f1,
                                                     size_t NN, double* __restrict__ part) {
@@ -650,6 +697,18 @@ cudaError_t launch_rof_gap(const float* u, const float* p, const float* I, int N
 cudaError_t launch_emd_primal(const float* m, const float* p, const float* f0, const float* f1, float* e, int N,
                               double* part, int nblk, cudaStream_t st) {
   k_emd_primal<<<nblk, 256, 0, st>>>(m, p, f0, f1, e, N, (float)N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emd_residual64(const float* m, const float* f0, const float* f1, float* rho, int N, double* part,
+                                 int nblk, cudaStream_t st) {
+  k_emd_residual64<<<nblk, 256, 0, st>>>(m, f0, f1, rho, N, (double)N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emd_corrected(const float* m, const float* gc, const float* f0, const float* f1, int N,
+                                 double* part, int nblk, cudaStream_t st) {
+  k_emd_corrected<<<nblk, 256, 0, st>>>(m, gc, f0, f1, N, (double)N, part);
   return cudaGetLastError();
 }
 

@@ -50,6 +50,12 @@ cudaError_t launch_rof_gap(const float* u, const float* p, const float* I, int N
                            cudaStream_t st);
 cudaError_t launch_emd_primal(const float* m, const float* p, const float* f0, const float* f1, float* e, int N,
                               double* part, int nblk, cudaStream_t st);
+// EMD feasibility certificate: rho = (f0 - f1) - div m (FP64, stored FP32) and
+// sum |rho|; then sum |m + grad c| and sum |(f0 - f1) - div(m + grad c)|.
+cudaError_t launch_emd_residual64(const float* m, const float* f0, const float* f1, float* rho, int N, double* part,
+                                 int nblk, cudaStream_t st);
+cudaError_t launch_emd_corrected(const float* m, const float* gc, const float* f0, const float* f1, int N,
+                                 double* part, int nblk, cudaStream_t st);
 cudaError_t launch_mass_stats(const float* f0, const float* f1, size_t NN, double* part, int nblk, cudaStream_t st);
 cudaError_t launch_final_reduce(const double* part, int nblk, int nq, unsigned maxmask, double* out, cudaStream_t st);
 cudaError_t launch_rof_init(const float* I, const float* u, const float* pbar, float* p, float* r, const RofParams& P,
@@ -64,6 +70,11 @@ cudaError_t launch_scale_sum(const double* sum, float* out, size_t n, double sca
 cudaError_t launch_emd_average_flux(const double* s_sum, const float* gq, float* m, size_t n2, double scale,
                                     cudaStream_t st);
 cudaError_t launch_grad(const float* x, float* g, int N, cudaStream_t st);
+// CP2 (cp2.cu): p = proj(p + sigma grad ubar); then u' = (u + tau div p + tau lambda I) / (1 + tau lambda),
+// ubar = u' + theta (u' - u), u = u'.
+cudaError_t launch_cp2_dual(const float* ubar, float* p, int N, float sigma, cudaStream_t st);
+cudaError_t launch_cp2_primal(float* u, float* ubar, const float* p, const float* I, int N, double tau, double lambda,
+                              double theta, cudaStream_t st);
 cudaError_t launch_copy_field(const float* a, float* b, int N, cudaStream_t st);
 
 }  // namespace gp

@@ -13,6 +13,11 @@ namespace gp {
 // driver's encoder is unavailable or refuses, or base is not 16-byte aligned.
 bool encode_b4_map(CUtensorMap* m, const float* base, int N, int ncols);
 
+// Tensor map of a pair-interleaved plane (rows 2q, 2q + 1 stored as N float2
+// per row pair) seen as {4 floats, N/2 column pairs, N/2 row pairs} (strides
+// 16 B and 8N B), box {4, 1, 256}; false as encode_b4_map.
+bool encode_pairs_map(CUtensorMap* m, const float* base, int N);
+
 namespace {
 
 constexpr uint32_t kTmaWaitLimit = 1u << 22;  // try_wait rounds before a copy is declared lost

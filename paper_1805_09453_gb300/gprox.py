@@ -28,7 +28,7 @@ EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_l
            "gp_cnn_create", "gp_cnn_destroy", "gp_cnn_last_error", "gp_cnn_num_params", "gp_cnn_get_params",
            "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned",
            "emd_coarse_start", "gp_gap_schedule_next", "gp_rof_image_stats", "gp_state_average",
-           "gp_state_read_average"]
+           "gp_state_read_average", "rof_solve_cp2"]
 
 
 class Opts(C.Structure):
@@ -40,7 +40,8 @@ class Opts(C.Structure):
 class Report(C.Structure):
     _fields_ = [("iters", C.c_int), ("status", C.c_int), ("primal", C.c_double), ("dual", C.c_double),
                 ("rel_gap", C.c_double), ("mass_residual", C.c_double), ("tau", C.c_double),
-                ("sigma", C.c_double), ("seconds", C.c_double)]
+                ("sigma", C.c_double), ("seconds", C.c_double), ("primal_feasible", C.c_double),
+                ("rel_gap_feasible", C.c_double), ("mass_residual_feasible", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -73,6 +74,7 @@ def lib():
     L.gp_last_error.restype = C.c_char_p
     L.dct2_poisson.argtypes = [vp, vp, vp, i, d, i, vp]
     L.rof_solve.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(Opts), C.POINTER(Report), vp]
+    L.rof_solve_cp2.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(Opts), C.POINTER(Report), vp]
     L.emd_solve.argtypes = [vp, vp, vp, vp, vp, vp, i, C.POINTER(Opts), C.POINTER(Report), vp]
     L.gp_state_create_rof.argtypes = [vp, C.POINTER(vp), vp, i, d, d, d, vp, vp, vp, vp]
     L.gp_state_create_emd.argtypes = [vp, C.POINTER(vp), vp, vp, i, d, d, vp, vp, vp, vp]
@@ -236,6 +238,17 @@ def rof_solve(h: Handle, I, u, p=None, lam: float = 8.0, opts: Opts | None = Non
     rep = Report()
     st = lib().rof_solve(h.ptr, _ptr(I), _ptr(u), _ptr(p), N, float(lam),
                          C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
+    return st, rep.as_dict()
+
+
+def rof_solve_cp2(h: Handle, I, u, p=None, lam: float = 8.0, opts: Opts | None = None, stream=None):
+    """ROF by the accelerated PDHG comparison method (CP2) of section 4.1; returns (status, report dict)."""
+    N = _side(I, "I")
+    _shape(u, (N, N), "u")
+    _shape(p, (2, N, N), "p")
+    rep = Report()
+    st = lib().rof_solve_cp2(h.ptr, _ptr(I), _ptr(u), _ptr(p), N, float(lam),
+                             C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
     return st, rep.as_dict()
 
 

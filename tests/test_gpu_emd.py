@@ -228,3 +228,43 @@ def test_unaligned_densities_give_the_same_solve(h):
     assert torch.equal(ma, mb)
     assert ra["primal"] == rb["primal"] and ra["mass_residual"] == rb["mass_residual"]
     assert abs(ra["dual"] - rb["dual"]) <= 1e-6 * abs(ra["dual"]), (ra["dual"], rb["dual"])
+
+
+def test_emd_feasible_certificate_brackets_the_optimum(h):
+    """The corrected flux m + grad Lap^{-1}((f0 - f1) - div m) is feasible, so
+    its cost is an upper bound on the optimum and D a lower one: against the
+    FP64 oracle's optimum (a run to gap 1e-7), D <= OPT <= primal_feasible, and
+    the solve returned GP_OK only once that bracket was within 1e-5."""
+    from paper_1805_09453_gb300 import gprox
+
+    N = 64
+    f0, f1 = _pair(N, 1)
+    m = torch.empty((2, N, N), device="cuda")
+    st, rep = gprox.emd_solve(h, _t(f0), _t(f1), m, opts=gprox.default_opts(max_iters=20000, tol_rel_gap=1e-5))
+    assert st == gprox.GP_OK and rep["rel_gap_feasible"] <= 1e-5, rep
+    ref = O.emd_solve(f0, f1, tol=1e-7, max_iters=100000)
+    assert rep["dual"] <= ref["primal"] * (1 + 1e-7)
+    assert rep["primal_feasible"] >= ref["dual"] * (1 - 1e-7)
+    assert rep["primal_feasible"] - ref["primal"] <= 1.01e-5 * rep["primal_feasible"]
+    # the correction removes the FP32 residual down to the solve's own error
+    assert rep["mass_residual_feasible"] < 1e-3 * rep["mass_residual"] + 1e-12, rep
+    # the residual reported at a certified check is the FP64 residual of the returned m
+    assert abs(rep["mass_residual"] - O.emd_mass_residual(*m.cpu().numpy(), f0, f1)) <= 1e-6 * rep["mass_residual"]
+
+
+def test_emd_1024_to_gap_certified(h):
+    """The 1024^2 Gaussian-mixture workload to relative gap 1e-5: the stop is
+    certified by the corrected flux (feasible to 1e-6), whose cost is within
+    the gap of the FP32 flux's."""
+    from paper_1805_09453_gb300 import gprox
+
+    N = 1024
+    f0, f1 = _pair(N, 1)
+    m = torch.empty((2, N, N), device="cuda")
+    st, rep = gprox.emd_solve(h, _t(f0), _t(f1), m, opts=gprox.default_opts(max_iters=40000, tol_rel_gap=1e-5))
+    print(rep)
+    assert st == gprox.GP_OK
+    assert rep["rel_gap"] <= 1e-5 and rep["rel_gap_feasible"] <= 1e-5
+    assert rep["dual"] <= rep["primal_feasible"]
+    assert rep["mass_residual_feasible"] < 1e-6
+    assert abs(rep["primal_feasible"] - rep["primal"]) <= 1e-5 * rep["primal"]
