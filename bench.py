@@ -51,6 +51,8 @@ BYTES_PER_POINT = {
     # forward row pass (other sizes: the step + the next forward row pass, grad u / grad q read)
     "rof_step_fwd": 32,    # read A, B (column syntheses), p(2), I; write p(2), row spectrum of r
     "emd_step_fwd": 48,    # read A, B, s(2), p(2), g; write s(2), p(2), row spectrum of d
+    "cp2_dual": 20,        # CP2 (section 4.1 comparison): read ubar, p(2); write p(2)
+    "cp2_primal": 24,      # read u, p(2), I; write u, ubar
 }
 
 # The same per-kernel figures as the scope table of the method counts them
@@ -161,6 +163,75 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def _helmholtz64(b, alpha):
+    """x = (alpha - Lap_h)^{-1} b in FP64 through scipy's orthonormal DCT-II (the
+    5-point Neumann Laplacian's eigenbasis, eigenvalues mu_k + mu_l,
+    mu_k = 4 N^2 sin^2(pi k / 2N)): the reference of the precision study."""
+    import numpy as np
+    import scipy.fft as sfft
+
+    N = b.shape[0]
+    mu = 4.0 * N * N * np.sin(np.pi * np.arange(N) / (2.0 * N)) ** 2
+    den = alpha + mu[:, None] + mu[None, :]
+    return sfft.idctn(sfft.dctn(b.astype(np.float64), type=2, norm="ortho", workers=-1) / den,
+                      type=2, norm="ortho", workers=-1)
+
+
+def _bench_3d(h, dev, stream, N3, peak):
+    """The d = 3 instance (rof_solve3d / emd_solve3d) at N3^3: per-iteration time from two
+    fixed-length solves, the line-transform pass against HBM, and the time to a gap."""
+    import numpy as np
+    import torch
+
+    from paper_1805_09453_gb300 import gprox, synth
+
+    rng = np.random.default_rng(0)
+    I3 = (synth.ball_image3(N3) + 0.1 * rng.normal(size=(N3, N3, N3))).astype(np.float32)
+    a0, a1 = synth.translated_balls3(N3)
+    Id = torch.from_numpy(I3).to(dev)
+    f0 = torch.from_numpy(a0).to(dev)
+    f1 = torch.from_numpy(a1).to(dev)
+    u = torch.empty_like(Id)
+    m = torch.empty((3, N3, N3, N3), device=dev)
+    n3 = N3 ** 3
+    out = {"N": N3, "what": "rof_solve3d (noisy ball, lambda=20) and emd_solve3d (balls translated by "
+                             "(1/4,1/4,1/4)); 12 line passes + 2 stencil kernels per iteration"}
+
+    def run(kind, iters, tol=0.0, gap_every=100000):
+        o = gprox.default_opts(max_iters=iters, tol_rel_gap=tol, gap_every=gap_every)
+        t0 = time.perf_counter()
+        if kind == "rof":
+            st, rep = gprox.rof_solve3d(h, Id, u, None, 20.0, o)
+        else:
+            st, rep = gprox.emd_solve3d(h, f0, f1, m, None, o)
+        stream.synchronize()
+        return time.perf_counter() - t0, st, rep
+
+    with torch.cuda.stream(stream):
+        for kind in ("rof", "emd"):
+            run(kind, 2)
+            t10 = run(kind, 10)[0]
+            gprox.profile(h, True)
+            t40, st, rep = run(kind, 40)
+            stream.synchronize()
+            gprox.profile(h, False)
+            pc = gprox.profile_read(h)
+            it_s = (t40 - t10) / 30
+            lms, ln = pc["dct3_lines"]
+            avg = lms / 1e3 / max(ln, 1)
+            gbs = 8 * n3 / avg / 1e9
+            tol, cap = 1e-4, 5000
+            tg, st, rep = run(kind, cap, tol, 0)
+            out[kind] = {"value": n3 / it_s, "unit": UNIT, "ms_per_iter": it_s * 1e3,
+                         "dct3_lines": {"avg_us": avg * 1e6, "launches": ln, "achieved_gbs": gbs,
+                                        "frac": gbs / peak, "bytes_per_point": 8},
+                         "stencil3_ms_per_iter": pc["stencil3"][0] / 40,
+                         "to_gap": {"tol": tol, "seconds": tg, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
+                                    "primal": rep["primal"], "status": rep["status_name"], "cap": cap}}
+    out["emd"]["to_gap"]["translation_length"] = float(np.sqrt(3) / 4)
+    return out
 
 
 def _inputs(N):
@@ -525,18 +596,54 @@ def run_ours(args):
                            "problem) vs emd_solve per pair; set-up included"}
         del bf0, bf1, bm
 
-    # split-precision study (FP32 fast transform vs hi+lo BF16 tensor-core GEMMs)
+    # CP2, the accelerated PDHG the paper compares with (section 4.1): the same ROF problem,
+    # no linear solve, two stencil passes per iteration; throughput and its roofline, and the
+    # gap it reaches in a fixed budget of iterations against the G-prox solve's time to 1e-5
+    cp2 = None
+    if not args.no_cp2 and rank == 0:
+        u2 = torch.empty((N, N), device=dev)
+        with torch.cuda.stream(stream):
+            o2 = gprox.default_opts(max_iters=50, tol_rel_gap=0.0, gap_every=50)
+            h.check(gprox.rof_solve_cp2(h, Id, u2, None, LAMBDA, o2)[0])
+            stream.synchronize()
+            gprox.profile(h, True)
+            o2 = gprox.default_opts(max_iters=200, tol_rel_gap=0.0, gap_every=200)
+            st, rep = gprox.rof_solve_cp2(h, Id, u2, None, LAMBDA, o2)
+            stream.synchronize()
+            gprox.profile(h, False)
+            pc = gprox.profile_read(h)
+            kern = {}
+            for k in ("cp2_dual", "cp2_primal"):
+                kms, kn = pc[k]
+                avg = kms / 1e3 / max(kn, 1)
+                gbs = BYTES_PER_POINT[k] * N * N / avg / 1e9
+                kern[k] = {"avg_us": avg * 1e6, "achieved_gbs": gbs, "frac": gbs / peak}
+            it_s = (pc["cp2_dual"][0] + pc["cp2_primal"][0]) / 1e3 / max(pc["cp2_dual"][1], 1)
+            o2 = gprox.default_opts(max_iters=args.cp2_iters, tol_rel_gap=1e-5, gap_every=100)
+            t0 = time.perf_counter()
+            st, rep = gprox.rof_solve_cp2(h, Id, u2, None, LAMBDA, o2)
+            stream.synchronize()
+            sec = time.perf_counter() - t0
+        cp2 = {"kernels": kern, "value": N * N / it_s, "unit": UNIT, "bytes_per_point_iteration": 44,
+               "to_gap_1e-5": {"seconds": sec, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
+                               "status": rep["status_name"], "cap": args.cp2_iters},
+               "gprox_to_gap_1e-5": ttg.get("rof") if ttg else None,
+               "what": "rof_solve_cp2 (section 4.1 comparison method) on the bench's ROF image, lambda=8"}
+
+    # split-precision study (FP32 fast transform vs hi+lo BF16 tensor-core GEMMs): the FP64
+    # residual of the discrete equation (alpha - Lap_h) x = b for each solve, and the split
+    # solve's distance from the FP32 one
     prec_study = None
     if not args.no_prec and rank == 0:
-        from oracle import gprox_oracle as O
-
         bp = np.ascontiguousarray(I[:, :], dtype=np.float32)
-        ref = O.helmholtz_solve(bp.astype(np.float64), 50.0, 1.0 / N)
         bd = torch.from_numpy(bp).to(dev)
         xo = torch.empty_like(bd)
-        prec_study = {"solve": f"(50 - Lap)^-1 I at {N}x{N} vs the FP64 oracle"}
+        prec_study = {"solve": f"(50 - Lap)^-1 I at {N}x{N}",
+                      "error": "relative L2 distance from an FP64 scipy DCT-II solve of the same system"}
+        x64 = _helmholtz64(bp, 50.0)
         pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
+        x32 = None
         with torch.cuda.stream(stream):
             for prec in ("fp32", "split_bf16"):
                 for _ in range(2):
@@ -549,13 +656,20 @@ def run_ours(args):
                 a1.record(stream)
                 stream.synchronize()
                 ms_s = a0.elapsed_time(a1) / 3
-                err = float(np.linalg.norm(xo.cpu().numpy() - ref) / np.linalg.norm(ref))
-                row = {"ms": ms_s, "rel_l2_err": err}
-                if prec != "fp32":
+                x = xo.cpu().numpy().astype(np.float64)
+                row = {"ms": ms_s, "rel_l2_err": float(np.linalg.norm(x - x64) / np.linalg.norm(x64))}
+                if prec == "fp32":
+                    x32 = x
+                else:
                     tf = 4 * 3 * 2.0 * N ** 3 / (ms_s / 1e3) / 1e12
-                    row.update({"tflops": tf, "bf16_peak_tflops": float(pk.get("bf16_tflops", 1900.0)),
+                    row.update({"rel_l2_vs_fp32": float(np.linalg.norm(x - x32) / np.linalg.norm(x32)),
+                                "tflops": tf, "bf16_peak_tflops": float(pk.get("bf16_tflops", 1900.0)),
                                 "tensor_frac": tf / float(pk.get("bf16_tflops", 1900.0))})
                 prec_study[prec] = row
+
+    three_d = None
+    if not args.no_3d and rank == 0:
+        three_d = _bench_3d(h, dev, stream, args.size3, peak)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -564,7 +678,7 @@ def run_ours(args):
             "roofline": roofline, "whole_iteration_hbm_frac": whole_frac,
             "whole_iteration_hbm_frac_scope_bytes": whole_frac_scope, "kernels": kernels,
             "gpu_launches": launches, "clocks": cl, "e2e": e2e, "time_to_gap": ttg, "batched": batched,
-            "precision_study": prec_study,
+            "precision_study": prec_study, "cp2": cp2, "three_d": three_d,
             "last_gap": {"rof": g_rof["rel_gap"], "emd": g_emd["rel_gap"]}}
     if rank == 0 and ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline_oracle(N, 1)
@@ -591,7 +705,11 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-prec", action="store_true")
+    ap.add_argument("--no-cp2", action="store_true")
+    ap.add_argument("--cp2-iters", type=int, default=20000)
     ap.add_argument("--ttg-cap", type=int, default=60000)
+    ap.add_argument("--no-3d", action="store_true")
+    ap.add_argument("--size3", type=int, default=256)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

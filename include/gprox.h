@@ -233,6 +233,34 @@ GP_API gp_status emd_solve(gp_handle h, const float* f0, const float* f1, float*
                     int N, const gp_opts* opts, gp_report* report, void* stream);
 
 /*
+ * rof_solve3d / emd_solve3d: the d = 3 instance of rof_solve / emd_solve
+ * (Algorithm 2 is stated for general dimension d; sections 3.1 / 3.2 carry d
+ * through their constants).  Volumes are N x N x N arrays indexed (z, y, x),
+ * x fastest, h = 1/N, weights h^3; vector fields are three consecutive
+ * volumes (x, y, z components), each with a zero last slot along its own
+ * axis; grad = forward differences, div = -grad^T, the Laplacian the 7-point
+ * Neumann stencil, solved in the cosine basis (gain 1/(alpha + mu_x + mu_y +
+ * mu_z)) with one line transform per axis.  The iterations, step rules, gaps
+ * and stopping tests are those of the two-dimensional entry points.
+ *   N       power of two in [16, 512].
+ *   I, f0, f1   device, N^3, read only.
+ *   u       device, N^3, out (rof_solve3d).  m: device, 3 N^3, out.
+ *   p       device, 3 N^3 or NULL, out: the last dual iterate.
+ *   opts    max_iters, tol_rel_gap, gap_every (0: adaptive as rof_solve),
+ *           tau, sigma, tau_scale, eps as the 2-D calls; prec must be
+ *           GP_PREC_FP32; warm_start, use_graph are not supported (warm_start
+ *           != 0 returns GP_ERR_UNSUPPORTED).
+ * EMD reports the FP32 gap (primal, dual, rel_gap, mass_residual); its
+ * feasibility fields are NaN and the stopping test uses rel_gap.  Buffers of
+ * 14 (ROF) / 25 (EMD) N^3 floats are allocated on first use and kept by
+ * the handle.  Returns as rof_solve.
+ */
+GP_API gp_status rof_solve3d(gp_handle h, const float* I, float* u, float* p, int N, double lambda,
+                             const gp_opts* opts, gp_report* report, void* stream);
+GP_API gp_status emd_solve3d(gp_handle h, const float* f0, const float* f1, float* m, float* p, int N,
+                             const gp_opts* opts, gp_report* report, void* stream);
+
+/*
  * emd_solve_batched: B independent EMD problems (section 3.2) of possibly
  * different sizes N[b], solved together.  Every chunk of gap_every
  * iterations of all unconverged problems runs as one CUDA graph with one
@@ -273,7 +301,10 @@ GP_API gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, c
  * gp_state_read copies the current
  * primal (u: N*N, or m: 2*N*N) and p (2*N*N) into caller device buffers
  * (either may be NULL).  gp_state_gap evaluates P, D, gap (and the EMD mass
- * residual) of the current iterate and synchronises `stream`.
+ * residual) of the current iterate and synchronises `stream`;
+ * gp_state_certify does the same and, for EMD, adds the feasibility
+ * certificate described under gp_report (one more cosine solve and two FP64
+ * reductions; ROF: the certificate fields equal P, the gap and 0).
  */
 GP_API gp_status gp_state_create_rof(gp_handle h, gp_state* out, const float* I, int N, double lambda,
                               double tau, double sigma, const float* u0, const float* p0,
@@ -284,6 +315,7 @@ GP_API gp_status gp_state_create_emd(gp_handle h, gp_state* out, const float* f0
 GP_API gp_status pd_step(gp_handle h, gp_state s, int n_steps, int prec, void* stream);
 GP_API gp_status gp_state_read(gp_handle h, gp_state s, float* primal, float* p, void* stream);
 GP_API gp_status gp_state_gap(gp_handle h, gp_state s, gp_report* report, void* stream);
+GP_API gp_status gp_state_certify(gp_handle h, gp_state s, gp_report* report, void* stream);
 GP_API gp_status gp_state_destroy(gp_state s);
 
 /*

@@ -37,14 +37,17 @@ enum {
   PK_EMD_STEP_FWD,
   PK_CP2_DUAL,
   PK_CP2_PRIMAL,
+  PK_3D_LINES,
+  PK_3D_STENCIL,
   PK_COUNT
 };
 static const char* kProfNames[PK_COUNT] = {"dct_rows_fwd", "dct_cols_solve", "dct_rows_inv", "dct_cols_grad",
                                            "dct_rows_grad", "dct_dense",     "dct_tc_split", "rof_fused",
                                            "emd_fused",     "reduce",        "setup",         "rof_step_fwd",
-                                           "emd_step_fwd",  "cp2_dual",      "cp2_primal"};
+                                           "emd_step_fwd",  "cp2_dual",      "cp2_primal",
+                                           "dct3_lines",    "stencil3"};
 // Kernel launches behind one recorded launch of a class.
-static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 4, 1, 1, 1, 1, 1, 1, 1, 1};
+static const int kProfLaunches[PK_COUNT] = {1, 1, 1, 1, 1, 5, 4, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
 
 struct Profiler {
   bool on = false;
@@ -89,6 +92,8 @@ struct gp_handle_s {
   std::vector<cudaEvent_t> evs;
   double* bres_d = nullptr;
   double* bres_h = nullptr;
+  float* v3 = nullptr;  // volumes of the 3-D solves
+  size_t v3_cap = 0;
 };
 
 struct gp_state_s {
@@ -777,6 +782,7 @@ gp_status emd_certify(gp_state s, gp_report* rep, cudaStream_t st) {
   rep->mass_residual_feasible = h->hres[2] / den;
   const double sc = fmax(fabs(rep->primal_feasible), fabs(rep->dual));
   rep->rel_gap_feasible = sc > 0 ? (rep->primal_feasible - rep->dual) / sc : 0.0;
+  s->partials_valid = false;  // part now holds the certificate's sums
   return GP_OK;
 }
 
@@ -969,6 +975,80 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
   return status;
 }
 
+// ------------------------------------------------------------ 3-D solves
+gp_status ensure_v3(gp_handle h, size_t floats) {
+  if (floats <= h->v3_cap) return GP_OK;
+  if (h->v3) cudaFree(h->v3);
+  h->v3 = nullptr;
+  h->v3_cap = 0;
+  GP_CUDA(h, cudaMalloc(&h->v3, floats * sizeof(float)));
+  h->v3_cap = floats;
+  return GP_OK;
+}
+
+gp_status check3(gp_handle h, int N, const gp_opts& o) {
+  if (N < 16 || N > 512 || (N & (N - 1)) != 0)
+    return fail(h, GP_ERR_ARG, "3-D solves take N a power of two in [16, 512]");
+  if (o.prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "3-D solves run the FP32 transform only");
+  if (o.warm_start) return fail(h, GP_ERR_UNSUPPORTED, "3-D solves take no warm start");
+  return GP_OK;
+}
+
+// x = scale (alpha - Lap)^{-1} b on N^3, its gradient into g3, x itself into u when u != nullptr.
+gp_status solve3(gp_handle h, const DctPlan& p, const float* b, float* g3, float* u, float* W, double alpha,
+                 double scale, cudaStream_t st) {
+  const size_t n3 = (size_t)p.N * p.N * p.N;
+  GP_CUDA(h, plaunch(h, PK_3D_LINES, st,
+                     [&] {
+                       return solve_grad3(p, b, g3, u, W, W + n3, W + 2 * n3, (float)alpha, (float)scale, st,
+                                          nullptr);
+                     },
+                     u ? 13 : 12));
+  return GP_OK;
+}
+
+// The chunked check loop of run_loop for the 3-D solves: step(k) runs k
+// iterations, gap() fills rep's P, D and rel_gap for the current iterate.
+template <typename Step, typename Gap>
+gp_status loop3(gp_handle h, const gp_opts& o, gp_report* rep, Step&& step, Gap&& gap) {
+  DivergenceWatch watch;
+  gp_status status = o.tol_rel_gap > 0 ? GP_ERR_MAXITER : GP_OK;
+  gp_status r;
+  int n = 0;
+  if (o.max_iters == 0 && (r = gap()) != GP_OK) return r;
+  int k_next = o.gap_every > 0 ? o.gap_every : kAdaptiveMinChunk;
+  int n_prev = -1;
+  double g_prev = 0;
+  while (n < o.max_iters) {
+    const int k = std::min(k_next, o.max_iters - n);
+    if ((r = step(k)) != GP_OK) return r;
+    n += k;
+    if ((r = gap()) != GP_OK) return r;
+    if (!isfinite(rep->primal) || !isfinite(rep->dual)) {
+      status = GP_ERR_NONFINITE;
+      fail(h, status, "non-finite objective: the iteration broke down");
+      break;
+    }
+    if (o.tol_rel_gap > 0 && rep->rel_gap <= o.tol_rel_gap) {
+      status = GP_OK;
+      break;
+    }
+    if (watch.update(rep->rel_gap)) {
+      status = GP_ERR_DIVERGED;
+      fail(h, status, "relative gap diverged");
+      break;
+    }
+    if (o.gap_every == 0) {
+      k_next = adaptive_chunk(n_prev, g_prev, n, rep->rel_gap, o.tol_rel_gap);
+      n_prev = n;
+      g_prev = rep->rel_gap;
+    }
+  }
+  rep->iters = n;
+  rep->status = status;
+  return status;
+}
+
 bool solve_status_has_outputs(gp_status s) {
   return s == GP_OK || s == GP_ERR_MAXITER || s == GP_ERR_DIVERGED || s == GP_ERR_NONFINITE;
 }
@@ -1022,6 +1102,7 @@ gp_status gp_destroy(gp_handle h) {
   for (auto& kv : h->plans) dct_plan_free(kv.second);
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   if (h->ws) cudaFree(h->ws);
+  if (h->v3) cudaFree(h->v3);
   if (h->tc_err) cudaFree(h->tc_err);
   if (h->part) cudaFree(h->part);
   if (h->dres) cudaFree(h->dres);
@@ -1250,6 +1331,22 @@ gp_status gp_state_gap(gp_handle h, gp_state s, gp_report* rep, void* stream) {
   return r;
 }
 
+gp_status gp_state_certify(gp_handle h, gp_state s, gp_report* rep, void* stream) {
+  if (!h || !s || s->h != h || !rep) return GP_ERR_ARG;
+  h->err.clear();
+  DeviceGuard g(h->device);
+  Timer t;
+  memset(rep, 0, sizeof(*rep));
+  gp_status r = state_gap(s, rep, GP_PREC_FP32, (cudaStream_t)stream);
+  if (r == GP_OK && s->kind == KIND_EMD && isfinite(rep->dual)) r = emd_certify(s, rep, (cudaStream_t)stream);
+  rep->iters = s->n;
+  rep->tau = s->tau;
+  rep->sigma = s->sigma;
+  rep->status = r;
+  rep->seconds = t.s();
+  return r;
+}
+
 gp_status gp_state_destroy(gp_state s) {
   if (!s) return GP_OK;
   DeviceGuard g(s->h->device);
@@ -1389,6 +1486,200 @@ gp_status rof_solve_cp2(gp_handle h, const float* I, float* u, float* p, int N, 
   if (p) GP_CUDA(h, cudaMemcpyAsync(p, ps, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
   GP_CUDA(h, cudaStreamSynchronize(st));
   s->partials_valid = false;  // the state's partials now hold CP2's gap terms
+  rep.seconds = t.s();
+  if (report) *report = rep;
+  return status;
+}
+
+gp_status rof_solve3d(gp_handle h, const float* I, float* u, float* p, int N, double lambda, const gp_opts* opts,
+                      gp_report* report, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  Timer t;
+  gp_opts o;
+  gp_default_opts(&o);
+  if (opts) o = *opts;
+  gp_report rep;
+  memset(&rep, 0, sizeof(rep));
+  gp_status r = check_opts(h, &o);
+  if (r != GP_OK || (r = check3(h, N, o)) != GP_OK) return r;
+  if (!(lambda > 0) || !isfinite(lambda)) return fail(h, GP_ERR_ARG, "lambda must be finite and > 0");
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  if ((r = check_ptr(h, I, "I")) != GP_OK) return r;
+  if ((r = check_ptr(h, u, "u")) != GP_OK) return r;
+  if (p && (r = check_ptr(h, p, "p")) != GP_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const DctPlan* plan = nullptr;
+  if ((r = get_plan(h, N, &plan)) != GP_OK) return r;
+  const size_t n3 = (size_t)N * N * N;
+  // volumes: grad u (3), p ping-pong (3 + 3), r, u, solve scratch (3)
+  if ((r = ensure_v3(h, 14 * n3)) != GP_OK) return r;
+  float* gu = h->v3;
+  float* pp[2] = {gu + 3 * n3, gu + 6 * n3};
+  float* rr = gu + 9 * n3;
+  float* us = rr + n3;
+  float* W = us + n3;
+  const int nb = reduce_blocks_1d(n3);
+  if ((r = ensure_part(h, (size_t)nb * 4)) != GP_OK) return r;
+  if ((r = ensure_res(h)) != GP_OK) return r;
+  const double h3 = 1.0 / (double)n3;
+  // step rule of rof_solve with h^3 weights (sections 3.1 and 4.1)
+  double tau = o.tau;
+  if (!(tau > 0)) {
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_rof3_stats(I, N, h->part, nb, st); }));
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 3, 0u, h->dres, st); }));
+    if ((r = fetch(h, 3, st)) != GP_OK) return r;
+    const double tv = h3 * h->hres[0], grad_l2 = sqrt(h3 * h->hres[1]), mean = h->hres[2] / (double)n3;
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_sq_dev(I, n3, (float)mean, h->part, nb, st); }));
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 1, 0u, h->dres, st); }));
+    if ((r = fetch(h, 1, st)) != GP_OK) return r;
+    const double fid = 0.5 * lambda * h3 * h->hres[0];
+    if (!isfinite(tv) || !isfinite(fid)) return fail(h, GP_ERR_NONFINITE, "non-finite image");
+    const double eps = o.eps > 0 ? o.eps : 1e-3;
+    tau = fmin(sqrt(lambda) * fmin(tv, fid) / sqrt(eps), grad_l2);
+    if (!(tau > 0)) tau = 1.0;  // constant image
+    tau *= o.tau_scale > 0 ? o.tau_scale : 1.0;
+  }
+  const double sigma = o.sigma > 0 ? o.sigma : 1.0 / tau;
+  const float lt = (float)(lambda * tau);
+  // u_0 = 0, p_0 = pbar_0 = 0: r_0 = lambda tau I
+  GP_CUDA(h, cudaMemsetAsync(gu, 0, 3 * n3 * sizeof(float), st));
+  GP_CUDA(h, cudaMemsetAsync(pp[0], 0, 3 * n3 * sizeof(float), st));
+  GP_CUDA(h, cudaMemsetAsync(us, 0, n3 * sizeof(float), st));
+  GP_CUDA(h, plaunch(h, PK_3D_STENCIL, st,
+                     [&] { return launch_rof3_rhs(pp[0], pp[0], gu, I, rr, N, lt, (float)tau, st); }));
+  int cur = 0;
+  auto step = [&](int k) -> gp_status {
+    for (int q = 0; q < k; ++q) {
+      gp_status e = solve3(h, *plan, rr, gu, q == k - 1 ? us : nullptr, W, lambda * tau, 1.0, st);
+      if (e != GP_OK) return e;
+      float* pin = pp[cur];
+      float* pout = pp[cur ^ 1];
+      GP_CUDA(h, plaunch(h, PK_3D_STENCIL, st, [&] { return launch_rof3_pstep(gu, pin, pout, N, (float)sigma, st); }));
+      GP_CUDA(h, plaunch(h, PK_3D_STENCIL, st,
+                         [&] { return launch_rof3_rhs(pout, pin, gu, I, rr, N, lt, (float)tau, st); }));
+      cur ^= 1;
+    }
+    return GP_OK;
+  };
+  auto gap = [&]() -> gp_status {
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_rof3_gap(us, gu, I, pp[cur], N, h->part, nb, st); }));
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 4, 0u, h->dres, st); }));
+    gp_status e = fetch(h, 4, st);
+    if (e != GP_OK) return e;
+    const double* v = h->hres;
+    finish_report(&rep, h3 * (v[0] + 0.5 * lambda * v[1]), -h3 * v[2] - h3 * v[3] / (2.0 * lambda));
+    return GP_OK;
+  };
+  gp_status status = loop3(h, o, &rep, step, gap);
+  if (!solve_status_has_outputs(status)) return status;
+  rep.tau = tau;
+  rep.sigma = sigma;
+  rep.mass_residual = 0.0;
+  rep.primal_feasible = rep.primal;  // no constraint on u
+  rep.rel_gap_feasible = rep.rel_gap;
+  rep.mass_residual_feasible = 0.0;
+  GP_CUDA(h, cudaMemcpyAsync(u, us, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  if (p) GP_CUDA(h, cudaMemcpyAsync(p, pp[cur], 3 * n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(h, cudaStreamSynchronize(st));
+  rep.seconds = t.s();
+  if (report) *report = rep;
+  return status;
+}
+
+gp_status emd_solve3d(gp_handle h, const float* f0, const float* f1, float* m, float* p, int N, const gp_opts* opts,
+                      gp_report* report, void* stream) {
+  if (!h) return GP_ERR_ARG;
+  h->err.clear();
+  Timer t;
+  gp_opts o;
+  gp_default_opts(&o);
+  if (opts) o = *opts;
+  gp_report rep;
+  memset(&rep, 0, sizeof(rep));
+  gp_status r = check_opts(h, &o);
+  if (r != GP_OK || (r = check3(h, N, o)) != GP_OK) return r;
+  DeviceGuard g(h->device);
+  if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
+  if ((r = check_ptr(h, f0, "f0")) != GP_OK) return r;
+  if ((r = check_ptr(h, f1, "f1")) != GP_OK) return r;
+  if ((r = check_ptr(h, m, "m")) != GP_OK) return r;
+  if (p && (r = check_ptr(h, p, "p")) != GP_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const DctPlan* plan = nullptr;
+  if ((r = get_plan(h, N, &plan)) != GP_OK) return r;
+  const size_t n3 = (size_t)N * N * N;
+  const int nb = reduce_blocks_1d(n3);
+  if ((r = ensure_part(h, (size_t)nb * 4)) != GP_OK) return r;
+  if ((r = ensure_res(h)) != GP_OK) return r;
+  double ms[3];
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_mass_stats(f0, f1, n3, h->part, nb, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 3, 0u, h->dres, st); }));
+  if ((r = fetch(h, 3, st)) != GP_OK) return r;
+  for (int q = 0; q < 3; ++q) ms[q] = h->hres[q];
+  if ((r = check_mass(h, ms)) != GP_OK) return r;
+  // volumes: g, d, s ping-pong (3 + 3), p ping-pong (3 + 3), grad q (3), m (3), phi, -div p, scratch (3)
+  if ((r = ensure_v3(h, 25 * n3)) != GP_OK) return r;
+  float* gg = h->v3;
+  float* dd = gg + n3;
+  float* ss[2] = {dd + n3, dd + 4 * n3};
+  float* pp[2] = {dd + 7 * n3, dd + 10 * n3};
+  float* gq = dd + 13 * n3;
+  float* mm = gq + 3 * n3;
+  float* phi = mm + 3 * n3;
+  float* ee = phi + n3;
+  float* W = ee + n3;
+  // section 4.2: tau = sigma = 1 for bounded densities
+  const double tau = o.tau > 0 ? o.tau : (o.tau_scale > 0 ? o.tau_scale : 1.0);
+  const double sigma = o.sigma > 0 ? o.sigma : 1.0 / tau;
+  // s_0 = 0, p_0 = 0, d_0 = g: the first step's solve gives m_0 = grad psi, Lap psi = f0 - f1
+  GP_CUDA(h, plaunch(h, PK_3D_STENCIL, st, [&] { return launch_sub(f0, f1, gg, n3, st); }));
+  GP_CUDA(h, cudaMemcpyAsync(dd, gg, n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(h, cudaMemsetAsync(ss[0], 0, 3 * n3 * sizeof(float), st));
+  GP_CUDA(h, cudaMemsetAsync(pp[0], 0, 3 * n3 * sizeof(float), st));
+  // q = Lap^{-1} d  <=>  (0 - Lap) q = -d
+  if (o.max_iters == 0 && (r = solve3(h, *plan, dd, mm, nullptr, W, 0.0, -1.0, st)) != GP_OK) return r;
+  int cur = 0;
+  auto step = [&](int k) -> gp_status {
+    for (int q = 0; q < k; ++q) {
+      gp_status e = solve3(h, *plan, dd, gq, nullptr, W, 0.0, -1.0, st);  // grad q, Lap q = d
+      if (e != GP_OK) return e;
+      float* mo = q == k - 1 ? mm : nullptr;
+      const int c = cur;
+      GP_CUDA(h, plaunch(h, PK_3D_STENCIL, st, [&] {
+                return launch_emd3_step(gq, ss[c], pp[c], ss[c ^ 1], pp[c ^ 1], mo, N, (float)tau, (float)sigma, st);
+              }));
+      GP_CUDA(h, plaunch(h, PK_3D_STENCIL, st, [&] { return launch_emd3_rhs(ss[c ^ 1], gg, dd, N, st); }));
+      cur ^= 1;
+    }
+    return GP_OK;
+  };
+  auto gap = [&]() -> gp_status {
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_emd3_primal(mm, gg, N, h->part, nb, st); }));
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(h->part, nb, 2, 0u, h->dres, st); }));
+    // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p; grad phi into gq (free between chunks)
+    GP_CUDA(h, plaunch(h, PK_3D_STENCIL, st, [&] { return launch_div3(pp[cur], ee, N, -1.f, st); }));
+    gp_status e = solve3(h, *plan, ee, gq, phi, W, 0.0, 1.0, st);
+    if (e != GP_OK) return e;
+    double* pd = h->part + (size_t)nb * 2;
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_emd3_dual(phi, gq, f0, f1, N, pd, nb, st); }));
+    GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(pd, nb, 2, 2u, h->dres + 2, st); }));
+    if ((e = fetch(h, 4, st)) != GP_OK) return e;
+    const double* v = h->hres;
+    const double h3 = 1.0 / (double)n3;
+    finish_report(&rep, h3 * v[0], h3 * v[2] / fmax(1.0, v[3]));
+    rep.mass_residual = ms[2] > 0 ? v[1] / ms[2] : v[1];
+    return GP_OK;
+  };
+  gp_status status = loop3(h, o, &rep, step, gap);
+  if (!solve_status_has_outputs(status)) return status;
+  rep.tau = tau;
+  rep.sigma = sigma;
+  rep.primal_feasible = rep.rel_gap_feasible = rep.mass_residual_feasible = NAN;  // no certificate in 3-D
+  GP_CUDA(h, cudaMemcpyAsync(m, mm, 3 * n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  if (p) GP_CUDA(h, cudaMemcpyAsync(p, pp[cur], 3 * n3 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(h, cudaStreamSynchronize(st));
   rep.seconds = t.s();
   if (report) *report = rep;
   return status;

@@ -1427,6 +1427,154 @@ __global__ void k_spec_scale_dense(float* __restrict__ X, const float* __restric
   X[idx] = den > 0.f ? X[idx] * (scale / den) : 0.f;
 }
 
+// ------------------------------------------------------------- 3-D lines
+// Volumes (z, y, x), x fastest, N^3.  One pass transforms every line along
+// `axis` (0: x, 1: y, 2: z): MODE 0 the forward DCT-II, MODE 1 the plain
+// cosine synthesis S_c, MODE 2 the forward-difference synthesis
+// N (S_c(P) - (-1)^j S_c(Q)) of the spectral gradient (zero-flux slot at
+// j = N - 1).  A CTA takes 16 lines adjacent in their fastest other
+// coordinate (x for the y and z lines, y for the x lines), staged in shared
+// memory, so that every global access moves 16 consecutive floats or more;
+// two lines share one complex FFT (MODE 0 / 1), or one line per FFT (MODE 2,
+// S_c(P) + i S_c(Q)).  In place is allowed: a CTA reads all its lines
+// before it writes them.
+constexpr int kLines3 = 16;
+
+template <int LOG2N, int MODE>
+__global__ void k_dct3_lines(const float* in, float* out, int axis,
+                             const float2* __restrict__ tw, const float2* __restrict__ wq) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
+  constexpr int NF = MODE == 2 ? kLines3 : kLines3 / 2;  // FFTs per CTA
+  extern __shared__ float2 sm3[];
+  float* stg = reinterpret_cast<float*>(sm3 + NF * PADN);  // [line][n]
+  const int f = (int)threadIdx.x / TPF, t = (int)threadIdx.x % TPF;
+  const int nthr = (int)blockDim.x;
+  const size_t NN = (size_t)N * N;
+  const int L0 = (int)blockIdx.x * kLines3;
+  const int outer = L0 / N, inner0 = L0 % N;
+  const size_t base = axis == 0 ? (size_t)L0 * N : (size_t)outer * (axis == 1 ? NN : (size_t)N) + inner0;
+  const size_t stride = axis == 0 ? 1 : (axis == 1 ? (size_t)N : NN);
+  // load: element e of the CTA's block -> line l, position n
+  for (int e = (int)threadIdx.x; e < kLines3 * N; e += nthr) {
+    int l, n;
+    if (axis == 0) { l = e / N; n = e % N; }
+    else { l = e % kLines3; n = e / kLines3; }
+    const size_t g = axis == 0 ? base + (size_t)l * N + n : base + (size_t)l + (size_t)n * stride;
+    stg[l * N + n] = in[g];
+  }
+  __syncthreads();
+  float2* buf = sm3 + f * PADN;
+  const float fN = (float)N;
+  if (MODE == 0) {
+    const float* xa = stg + (2 * f) * N;
+    const float* xb = xa + N;
+    for (int n = t; n < N; n += TPF) buf[padi(mk_pos(n, N))] = make_float2(xa[n], xb[n]);
+  } else {
+    // pre-step from the line spectra (MODE 1: lines 2f, 2f+1; MODE 2: line f)
+    const float* xa = stg + (MODE == 1 ? 2 * f : f) * N;
+    const float* xb = xa + N;
+    for (int k = t; k <= N / 2; k += TPF) {
+      if (MODE == 1) {
+        if (k == 0) buf[0] = make_float2(xa[0], xb[0]);
+        else if (k == N / 2) buf[padi(k)] = make_float2(kSqrt2 * xa[k], kSqrt2 * xb[k]);
+        else {
+          float2 zk, zn;
+          inv_pre(xa[k], xa[N - k], xb[k], xb[N - k], __ldg(&wq[k]), zk, zn);
+          buf[padi(k)] = zk;
+          buf[padi(N - k)] = zn;
+        }
+      } else {
+        if (k == 0) buf[0] = make_float2(0.f, 0.f);
+        else if (k == N / 2) buf[padi(k)] = make_float2(-kSqrt2 * xa[k], kSqrt2 * xa[k]);
+        else {
+          float2 zk, zn;
+          deriv_pre(xa[k], xa[N - k], __ldg(&wq[k]), zk, zn);
+          buf[padi(k)] = zk;
+          buf[padi(N - k)] = zn;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (MODE == 0) fft_smem<LOG2N, -1, TPF>(buf, t, tw, 0);
+  else fft_smem<LOG2N, +1, TPF>(buf, t, tw, 0);
+  // results back into the staging lines (each FFT group writes only its own lines)
+  if (MODE == 0) {
+    float* xa = stg + (2 * f) * N;
+    float* xb = xa + N;
+    for (int k = t; k <= N / 2; k += TPF) {
+      if (k == 0 || k == N / 2) {
+        const float sc = k == 0 ? 1.f : kRsqrt2;
+        const float2 z = buf[padi(k)];
+        xa[k] = sc * z.x;
+        xb[k] = sc * z.y;
+      } else {
+        float ak, an, bk, bn;
+        fwd_post(buf[padi(k)], buf[padi(N - k)], __ldg(&wq[k]), ak, an, bk, bn);
+        xa[k] = ak;
+        xa[N - k] = an;
+        xb[k] = bk;
+        xb[N - k] = bn;
+      }
+    }
+  } else if (MODE == 1) {
+    float* xa = stg + (2 * f) * N;
+    float* xb = xa + N;
+    for (int n = t; n < N; n += TPF) {
+      const float2 z = buf[padi(mk_pos(n, N))];
+      xa[n] = z.x;
+      xb[n] = z.y;
+    }
+  } else {
+    float* xa = stg + f * N;
+    for (int n = t; n < N; n += TPF) {
+      const float2 z = buf[padi(mk_pos(n, N))];
+      xa[n] = n == N - 1 ? 0.f : fN * (z.x - ((n & 1) ? -z.y : z.y));
+    }
+  }
+  __syncthreads();
+  for (int e = (int)threadIdx.x; e < kLines3 * N; e += nthr) {
+    int l, n;
+    if (axis == 0) { l = e / N; n = e % N; }
+    else { l = e % kLines3; n = e / kLines3; }
+    const size_t g = axis == 0 ? base + (size_t)l * N + n : base + (size_t)l + (size_t)n * stride;
+    out[g] = stg[l * N + n];
+  }
+}
+
+// Spectral gain of the 3-D solve: X *= sN3 / (alpha + mu_x + mu_y + mu_z), 0 for
+// the constant mode when alpha == 0.
+__global__ void k_gain3(float* __restrict__ X, const float* __restrict__ mu, int N, float alpha, float sN3) {
+  const size_t NN = (size_t)N * N, n3 = NN * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % N), ky = (int)((i / N) % N), kz = (int)(i / NN);
+    const float den = alpha + __ldg(&mu[kx]) + __ldg(&mu[ky]) + __ldg(&mu[kz]);
+    X[i] = den > 0.f ? X[i] * (sN3 / den) : 0.f;
+  }
+}
+
+template <int LOG2N>
+cudaError_t launch_dct3_lines(const DctPlan& p, const float* in, float* out, int axis, int mode, cudaStream_t st) {
+  using C = FftCfg<LOG2N>;
+  constexpr int N = C::N;
+  const int nf = mode == 2 ? kLines3 : kLines3 / 2;
+  const size_t sm = (size_t)nf * C::PADN * sizeof(float2) + (size_t)kLines3 * N * sizeof(float);
+  const int grid = N * N / kLines3, thr = nf * C::TPF;
+  cudaError_t e;
+  if (mode == 0) {
+    if ((e = set_smem(k_dct3_lines<LOG2N, 0>, sm))) return e;
+    k_dct3_lines<LOG2N, 0><<<grid, thr, sm, st>>>(in, out, axis, p.tw, p.wq);
+  } else if (mode == 1) {
+    if ((e = set_smem(k_dct3_lines<LOG2N, 1>, sm))) return e;
+    k_dct3_lines<LOG2N, 1><<<grid, thr, sm, st>>>(in, out, axis, p.tw, p.wq);
+  } else {
+    if ((e = set_smem(k_dct3_lines<LOG2N, 2>, sm))) return e;
+    k_dct3_lines<LOG2N, 2><<<grid, thr, sm, st>>>(in, out, axis, p.tw, p.wq);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1540,6 +1688,61 @@ cudaError_t dct_rof_step_fwd(const DctPlan& p, const float* gu, const float* pin
 #define GP_CALL(L) launch_rof_step_fwd<L>(p, gu, pin, I, pout, out, P, st)
   GP_FFT_DISPATCH(p.N, GP_CALL)
 #undef GP_CALL
+}
+
+cudaError_t dct3_lines(const DctPlan& p, const float* in, float* out, int axis, int mode, cudaStream_t st) {
+  if (!p.fft || p.N > 512) return cudaErrorInvalidValue;
+  switch (p.N) {
+    case 16: return launch_dct3_lines<4>(p, in, out, axis, mode, st);
+    case 32: return launch_dct3_lines<5>(p, in, out, axis, mode, st);
+    case 64: return launch_dct3_lines<6>(p, in, out, axis, mode, st);
+    case 128: return launch_dct3_lines<7>(p, in, out, axis, mode, st);
+    case 256: return launch_dct3_lines<8>(p, in, out, axis, mode, st);
+    case 512: return launch_dct3_lines<9>(p, in, out, axis, mode, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t dct3_gain(const DctPlan& p, float* X, float alpha, float scale, cudaStream_t st) {
+  const int N = p.N;
+  const size_t n3 = (size_t)N * N * N;
+  const float sN3 = (float)((double)scale / ((double)N * N * N));
+  const size_t blocks = (n3 + 255) / 256;
+  k_gain3<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, st>>>(X, p.mu, N, alpha, sN3);
+  return cudaGetLastError();
+}
+
+// g3 = grad x and (u != nullptr) u = x for x = scale (alpha - Lap)^{-1} b on an
+// N^3 grid: three forward line passes, the spectral gain, then the
+// syntheses, sharing S_z X between the x, y components and u:
+//   gz = S_x S_y D_z X,  gx = D_x S_y S_z X,  u = S_x S_y S_z X,  gy = S_x D_y S_z X.
+// W0..W2 are N^3 scratch volumes; b is not written (it may alias u).
+// Returns the number of line / gain launches through *nlaunch.
+cudaError_t solve_grad3(const DctPlan& p, const float* b, float* g3, float* u, float* W0, float* W1, float* W2,
+                        float alpha, float scale, cudaStream_t st, int* nlaunch) {
+  const size_t n3 = (size_t)p.N * p.N * p.N;
+  float* gx = g3;
+  float* gy = g3 + n3;
+  float* gz = g3 + 2 * n3;
+  cudaError_t e;
+#define GP_L3(IN, OUT, AX, MODE) \
+  if ((e = dct3_lines(p, IN, OUT, AX, MODE, st))) return e
+  GP_L3(b, W0, 0, 0);
+  GP_L3(W0, W0, 1, 0);
+  GP_L3(W0, W0, 2, 0);
+  if ((e = dct3_gain(p, W0, alpha, scale, st))) return e;
+  GP_L3(W0, W1, 2, 1);  // S_z X
+  GP_L3(W0, W2, 2, 2);  // D_z X
+  GP_L3(W2, W2, 1, 1);
+  GP_L3(W2, gz, 0, 1);
+  GP_L3(W1, W2, 1, 1);  // S_y S_z X
+  GP_L3(W2, gx, 0, 2);
+  if (u) GP_L3(W2, u, 0, 1);
+  GP_L3(W1, W1, 1, 2);  // D_y S_z X
+  GP_L3(W1, gy, 0, 1);
+#undef GP_L3
+  if (nlaunch) *nlaunch = u ? 13 : 12;
+  return cudaSuccess;
 }
 
 cudaError_t dct_plan_init(DctPlan& p, int N) {

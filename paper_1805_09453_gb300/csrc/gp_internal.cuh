@@ -101,6 +101,14 @@ cudaError_t dct_emd_step_fwd(const DctPlan& p, const float* gq, const float* sin
                              float* sout, float* pout, float* out, const EmdParams& P, cudaStream_t st);
 cudaError_t dct_rof_step_fwd(const DctPlan& p, const float* gu, const float* pin, const float* I, float* pout,
                              float* out, const RofParams& P, cudaStream_t st);
+// 3-D volumes (z, y, x), x fastest, power-of-two N in [16, 512]: one pass of
+// line transforms along `axis` (0 x, 1 y, 2 z); mode 0 forward DCT-II, 1 plain
+// cosine synthesis, 2 forward-difference synthesis (in may equal out); and the
+// spectral gain X *= scale / ((alpha + mu_x + mu_y + mu_z) N^3).
+cudaError_t dct3_lines(const DctPlan& p, const float* in, float* out, int axis, int mode, cudaStream_t st);
+cudaError_t dct3_gain(const DctPlan& p, float* X, float alpha, float scale, cudaStream_t st);
+cudaError_t solve_grad3(const DctPlan& p, const float* b, float* g3, float* u, float* W0, float* W1, float* W2,
+                        float alpha, float scale, cudaStream_t st, int* nlaunch);
 // Build C (and C^T) for a plan that lacks them (tensor-core path).
 cudaError_t dct_plan_dense(DctPlan& p);
 // Split-precision (hi + lo BF16) tensor-core form, N % 128 == 0: four tcgen05

@@ -610,6 +610,190 @@ inline int grid_1d(size_t n, int threads) {
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
+// ------------------------------------------------------------------- 3-D
+// The d = 3 instance of the updates above (Algorithm 2 for general d;
+// sections 3.1 / 3.2): volumes (z, y, x), x fastest, n3 = N^3 points;
+// vector fields are three consecutive volumes (x, y, z components) with
+// structurally zero last slots; forward differences, div = -grad^T.
+__device__ __forceinline__ void proj3(float qx, float qy, float qz, float& px, float& py, float& pz) {
+  const float n2 = qx * qx + qy * qy + qz * qz;
+  if (n2 > 1.f) {
+    const float s = rsqrtf(n2);
+    px = qx * s;
+    py = qy * s;
+    pz = qz * s;
+  } else {
+    px = qx;
+    py = qy;
+    pz = qz;
+  }
+}
+
+struct Idx3 {
+  int x, y, z;
+  size_t sy, sz;  // strides of y and z
+};
+__device__ __forceinline__ Idx3 idx3(size_t i, int N) {
+  const size_t NN = (size_t)N * N;
+  return Idx3{(int)(i % N), (int)((i / N) % N), (int)(i / NN), (size_t)N, NN};
+}
+
+// div v at point i (backward differences, each component's last slot ignored)
+__device__ __forceinline__ float div3_at(const float* __restrict__ v, size_t n3, size_t i, const Idx3& c, int N,
+                                         float invh) {
+  const float* vx = v;
+  const float* vy = v + n3;
+  const float* vz = v + 2 * n3;
+  return ((c.x < N - 1 ? vx[i] : 0.f) - (c.x > 0 ? vx[i - 1] : 0.f) + (c.y < N - 1 ? vy[i] : 0.f) -
+          (c.y > 0 ? vy[i - c.sy] : 0.f) + (c.z < N - 1 ? vz[i] : 0.f) - (c.z > 0 ? vz[i - c.sz] : 0.f)) *
+         invh;
+}
+
+// ROF: p_{n+1} = proj(p_n + sigma grad u_{n+1})
+__global__ void __launch_bounds__(256) k_rof3_pstep(const float* __restrict__ gu, const float* __restrict__ pin,
+                                                    float* __restrict__ pout, int N, float sigma) {
+  const size_t n3 = (size_t)N * N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const Idx3 c = idx3(i, N);
+    float px, py, pz;
+    proj3(pin[i] + sigma * gu[i], pin[n3 + i] + sigma * gu[n3 + i], pin[2 * n3 + i] + sigma * gu[2 * n3 + i], px,
+          py, pz);
+    pout[i] = c.x < N - 1 ? px : 0.f;
+    pout[n3 + i] = c.y < N - 1 ? py : 0.f;
+    pout[2 * n3 + i] = c.z < N - 1 ? pz : 0.f;
+  }
+}
+
+// ROF: r_{n+1} = lambda tau I + tau div pbar_{n+1} - div grad u_{n+1}, pbar = 2 p_{n+1} - p_n
+__global__ void __launch_bounds__(256) k_rof3_rhs(const float* __restrict__ pout, const float* __restrict__ pin,
+                                                  const float* __restrict__ gu, const float* __restrict__ I,
+                                                  float* __restrict__ r, int N, float invh, float lt, float tau) {
+  const size_t n3 = (size_t)N * N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const Idx3 c = idx3(i, N);
+    auto pb = [&](int comp, size_t j) { return 2.f * pout[comp * n3 + j] - pin[comp * n3 + j]; };
+    const float dpb = ((c.x < N - 1 ? pb(0, i) : 0.f) - (c.x > 0 ? pb(0, i - 1) : 0.f) +
+                       (c.y < N - 1 ? pb(1, i) : 0.f) - (c.y > 0 ? pb(1, i - c.sy) : 0.f) +
+                       (c.z < N - 1 ? pb(2, i) : 0.f) - (c.z > 0 ? pb(2, i - c.sz) : 0.f)) *
+                      invh;
+    r[i] = lt * I[i] + tau * dpb - div3_at(gu, n3, i, c, N, invh);
+  }
+}
+
+// EMD (affine Leray form): m = s + grad q;  p' = proj(p + sigma m);
+// s' = m - tau (2 p' - p); m written when requested (gap steps)
+__global__ void __launch_bounds__(256) k_emd3_step(const float* __restrict__ gq, const float* __restrict__ sin_,
+                                                   const float* __restrict__ pin, float* __restrict__ sout,
+                                                   float* __restrict__ pout, float* __restrict__ m, int N, float tau,
+                                                   float sigma) {
+  const size_t n3 = (size_t)N * N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const Idx3 c = idx3(i, N);
+    const bool in[3] = {c.x < N - 1, c.y < N - 1, c.z < N - 1};
+    float mv[3], pv[3], q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      mv[k] = in[k] ? sin_[k * n3 + i] + gq[k * n3 + i] : 0.f;
+      pv[k] = pin[k * n3 + i];
+      q[k] = pv[k] + sigma * mv[k];
+    }
+    float p1[3];
+    proj3(q[0], q[1], q[2], p1[0], p1[1], p1[2]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (!in[k]) p1[k] = 0.f;
+      pout[k * n3 + i] = p1[k];
+      sout[k * n3 + i] = in[k] ? mv[k] - tau * (2.f * p1[k] - pv[k]) : 0.f;
+      if (m) m[k * n3 + i] = mv[k];
+    }
+  }
+}
+
+// EMD: d = g - div s
+__global__ void __launch_bounds__(256) k_emd3_rhs(const float* __restrict__ sout, const float* __restrict__ g,
+                                                  float* __restrict__ d, int N, float invh) {
+  const size_t n3 = (size_t)N * N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x)
+    d[i] = g[i] - div3_at(sout, n3, i, idx3(i, N), N, invh);
+}
+
+// e = scale * div v
+__global__ void __launch_bounds__(256) k_div3(const float* __restrict__ v, float* __restrict__ e, int N, float invh,
+                                              float scale) {
+  const size_t n3 = (size_t)N * N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x)
+    e[i] = scale * div3_at(v, n3, i, idx3(i, N), N, invh);
+}
+
+// ROF gap terms: sum |grad u|, sum (u - I)^2, sum I div p, sum (div p)^2
+__global__ void __launch_bounds__(256) k_rof3_gap(const float* __restrict__ u, const float* __restrict__ gu,
+                                                  const float* __restrict__ I, const float* __restrict__ p, int N,
+                                                  float invh, double* __restrict__ part) {
+  const size_t n3 = (size_t)N * N * N;
+  CSum a, b, c2, d;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const float gx = gu[i], gy = gu[n3 + i], gz = gu[2 * n3 + i];
+    a.add(sqrtf(gx * gx + gy * gy + gz * gz));
+    const float e = u[i] - I[i];
+    b.add(e * e);
+    const float dp = div3_at(p, n3, i, idx3(i, N), N, invh);
+    c2.add(I[i] * dp);
+    d.add(dp * dp);
+  }
+  double v[4] = {a.value(), b.value(), c2.value(), d.value()};
+  block_reduce_store<4>(v, 0u, part);
+}
+
+// EMD primal terms: sum |m|, sum |div m - g|
+__global__ void __launch_bounds__(256) k_emd3_primal(const float* __restrict__ m, const float* __restrict__ g, int N,
+                                                     float invh, double* __restrict__ part) {
+  const size_t n3 = (size_t)N * N * N;
+  CSum a, b;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const float mx = m[i], my = m[n3 + i], mz = m[2 * n3 + i];
+    a.add(sqrtf(mx * mx + my * my + mz * mz));
+    b.add(fabsf(div3_at(m, n3, i, idx3(i, N), N, invh) - g[i]));
+  }
+  double v[2] = {a.value(), b.value()};
+  block_reduce_store<2>(v, 0u, part);
+}
+
+// EMD dual bound terms: sum phi (f1 - f0), max |grad phi|
+__global__ void __launch_bounds__(256) k_emd3_dual(const float* __restrict__ phi, const float* __restrict__ gphi,
+                                                   const float* __restrict__ f0, const float* __restrict__ f1, int N,
+                                                   double* __restrict__ part) {
+  const size_t n3 = (size_t)N * N * N;
+  CSum a;
+  double mx = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    a.add(phi[i] * (f1[i] - f0[i]));
+    const float gx = gphi[i], gy = gphi[n3 + i], gz = gphi[2 * n3 + i];
+    mx = fmax(mx, (double)sqrtf(gx * gx + gy * gy + gz * gz));
+  }
+  double v[2] = {a.value(), mx};
+  block_reduce_store<2>(v, 2u, part);
+}
+
+// ROF step-rule statistics of I: sum |grad I|, sum |grad I|^2, sum I
+__global__ void __launch_bounds__(256) k_rof3_stats(const float* __restrict__ I, int N, float invh,
+                                                    double* __restrict__ part) {
+  const size_t n3 = (size_t)N * N * N;
+  CSum a, b, c2;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (size_t)gridDim.x * blockDim.x) {
+    const Idx3 c = idx3(i, N);
+    const float v = I[i];
+    const float gx = c.x < N - 1 ? (I[i + 1] - v) * invh : 0.f;
+    const float gy = c.y < N - 1 ? (I[i + c.sy] - v) * invh : 0.f;
+    const float gz = c.z < N - 1 ? (I[i + c.sz] - v) * invh : 0.f;
+    const float m2 = gx * gx + gy * gy + gz * gz;
+    a.add(sqrtf(m2));
+    b.add(m2);
+    c2.add(v);
+  }
+  double v[3] = {a.value(), b.value(), c2.value()};
+  block_reduce_store<3>(v, 0u, part);
+}
+
 }  // namespace
 
 // Row-block heights the fused kernels are instantiated for (the autotuned
@@ -786,6 +970,50 @@ cudaError_t launch_grad(const float* x, float* g, int N, cudaStream_t st) {
 
 cudaError_t launch_copy_field(const float* a, float* b, int N, cudaStream_t st) {
   k_copy_field<<<grid_1d((size_t)N * N, 256), 256, 0, st>>>(a, b, N);
+  return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------------------ 3-D
+
+cudaError_t launch_rof3_pstep(const float* gu, const float* pin, float* pout, int N, float sigma, cudaStream_t st) {
+  k_rof3_pstep<<<grid_1d((size_t)N * N * N, 256), 256, 0, st>>>(gu, pin, pout, N, sigma);
+  return cudaGetLastError();
+}
+cudaError_t launch_rof3_rhs(const float* pout, const float* pin, const float* gu, const float* I, float* r, int N,
+                            float lt, float tau, cudaStream_t st) {
+  k_rof3_rhs<<<grid_1d((size_t)N * N * N, 256), 256, 0, st>>>(pout, pin, gu, I, r, N, (float)N, lt, tau);
+  return cudaGetLastError();
+}
+cudaError_t launch_emd3_step(const float* gq, const float* sin_, const float* pin, float* sout, float* pout, float* m,
+                             int N, float tau, float sigma, cudaStream_t st) {
+  k_emd3_step<<<grid_1d((size_t)N * N * N, 256), 256, 0, st>>>(gq, sin_, pin, sout, pout, m, N, tau, sigma);
+  return cudaGetLastError();
+}
+cudaError_t launch_emd3_rhs(const float* sout, const float* g, float* d, int N, cudaStream_t st) {
+  k_emd3_rhs<<<grid_1d((size_t)N * N * N, 256), 256, 0, st>>>(sout, g, d, N, (float)N);
+  return cudaGetLastError();
+}
+cudaError_t launch_div3(const float* v, float* e, int N, float scale, cudaStream_t st) {
+  k_div3<<<grid_1d((size_t)N * N * N, 256), 256, 0, st>>>(v, e, N, (float)N, scale);
+  return cudaGetLastError();
+}
+cudaError_t launch_rof3_gap(const float* u, const float* gu, const float* I, const float* p, int N, double* part,
+                            int nblk, cudaStream_t st) {
+  k_rof3_gap<<<nblk, 256, 0, st>>>(u, gu, I, p, N, (float)N, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_emd3_primal(const float* m, const float* g, int N, double* part, int nblk, cudaStream_t st) {
+  k_emd3_primal<<<nblk, 256, 0, st>>>(m, g, N, (float)N, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_emd3_dual(const float* phi, const float* gphi, const float* f0, const float* f1, int N,
+                             double* part, int nblk, cudaStream_t st) {
+  k_emd3_dual<<<nblk, 256, 0, st>>>(phi, gphi, f0, f1, N, part);
+  return cudaGetLastError();
+}
+cudaError_t launch_rof3_stats(const float* I, int N, double* part, int nblk, cudaStream_t st) {
+  k_rof3_stats<<<nblk, 256, 0, st>>>(I, N, (float)N, part);
   return cudaGetLastError();
 }
 

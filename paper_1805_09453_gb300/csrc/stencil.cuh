@@ -70,6 +70,20 @@ cudaError_t launch_scale_sum(const double* sum, float* out, size_t n, double sca
 cudaError_t launch_emd_average_flux(const double* s_sum, const float* gq, float* m, size_t n2, double scale,
                                     cudaStream_t st);
 cudaError_t launch_grad(const float* x, float* g, int N, cudaStream_t st);
+// 3-D (N^3 volumes, (z, y, x), vector fields as three volumes; see stencil.cu).
+cudaError_t launch_rof3_pstep(const float* gu, const float* pin, float* pout, int N, float sigma, cudaStream_t st);
+cudaError_t launch_rof3_rhs(const float* pout, const float* pin, const float* gu, const float* I, float* r, int N,
+                            float lt, float tau, cudaStream_t st);
+cudaError_t launch_emd3_step(const float* gq, const float* sin_, const float* pin, float* sout, float* pout, float* m,
+                             int N, float tau, float sigma, cudaStream_t st);
+cudaError_t launch_emd3_rhs(const float* sout, const float* g, float* d, int N, cudaStream_t st);
+cudaError_t launch_div3(const float* v, float* e, int N, float scale, cudaStream_t st);
+cudaError_t launch_rof3_gap(const float* u, const float* gu, const float* I, const float* p, int N, double* part,
+                            int nblk, cudaStream_t st);
+cudaError_t launch_emd3_primal(const float* m, const float* g, int N, double* part, int nblk, cudaStream_t st);
+cudaError_t launch_emd3_dual(const float* phi, const float* gphi, const float* f0, const float* f1, int N,
+                             double* part, int nblk, cudaStream_t st);
+cudaError_t launch_rof3_stats(const float* I, int N, double* part, int nblk, cudaStream_t st);
 // CP2 (cp2.cu): p = proj(p + sigma grad ubar); then u' = (u + tau div p + tau lambda I) / (1 + tau lambda),
 // ubar = u' + theta (u' - u), u = u'.
 cudaError_t launch_cp2_dual(const float* ubar, float* p, int N, float sigma, cudaStream_t st);

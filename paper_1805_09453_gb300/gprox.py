@@ -28,7 +28,7 @@ EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_l
            "gp_cnn_create", "gp_cnn_destroy", "gp_cnn_last_error", "gp_cnn_num_params", "gp_cnn_get_params",
            "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned",
            "emd_coarse_start", "gp_gap_schedule_next", "gp_rof_image_stats", "gp_state_average",
-           "gp_state_read_average", "rof_solve_cp2"]
+           "gp_state_read_average", "rof_solve_cp2", "rof_solve3d", "emd_solve3d", "gp_state_certify"]
 
 
 class Opts(C.Structure):
@@ -81,6 +81,7 @@ def lib():
     L.pd_step.argtypes = [vp, vp, i, i, vp]
     L.gp_state_read.argtypes = [vp, vp, vp, vp, vp]
     L.gp_state_gap.argtypes = [vp, vp, C.POINTER(Report), vp]
+    L.gp_state_certify.argtypes = [vp, vp, C.POINTER(Report), vp]
     L.gp_state_destroy.argtypes = [vp]
     L.dct2_poisson_static.argtypes = [vp, vp, i, d, vp]
     L.dct2_poisson_grad.argtypes = [vp, vp, vp, i, d, i, vp]
@@ -109,6 +110,8 @@ def lib():
     L.gp_state_average.argtypes = [vp, vp, i, vp]
     L.gp_state_read_average.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_longlong), vp]
     L.gp_rof_image_stats.argtypes = [vp, vp, i, C.POINTER(d), vp]
+    L.rof_solve3d.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(Opts), C.POINTER(Report), vp]
+    L.emd_solve3d.argtypes = [vp, vp, vp, vp, vp, i, C.POINTER(Opts), C.POINTER(Report), vp]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
     for name in EXPORTS:
@@ -265,6 +268,38 @@ def emd_solve(h: Handle, f0, f1, m, p=None, phi=None, opts: Opts | None = None, 
     return st, rep.as_dict()
 
 
+def _side3(t, name="array"):
+    """Grid side N of an (N, N, N) tensor (ValueError for any other shape)."""
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name}: expected a torch tensor")
+    if t.dim() != 3 or not (t.shape[0] == t.shape[1] == t.shape[2]):
+        raise ValueError(f"{name}: expected an (N, N, N) volume, got shape {tuple(t.shape)}")
+    return int(t.shape[-1])
+
+
+def rof_solve3d(h: Handle, I, u, p=None, lam: float = 8.0, opts: Opts | None = None, stream=None):
+    """ROF G-prox PDHG on an (N, N, N) volume (z, y, x); p is (3, N, N, N); returns (status, report dict)."""
+    N = _side3(I, "I")
+    _shape(u, (N, N, N), "u")
+    _shape(p, (3, N, N, N), "p")
+    rep = Report()
+    st = lib().rof_solve3d(h.ptr, _ptr(I), _ptr(u), _ptr(p), N, float(lam),
+                           C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
+    return st, rep.as_dict()
+
+
+def emd_solve3d(h: Handle, f0, f1, m, p=None, opts: Opts | None = None, stream=None):
+    """L1 EMD G-prox PDHG on (N, N, N) densities; m and p are (3, N, N, N); returns (status, report dict)."""
+    N = _side3(f0, "f0")
+    _shape(f1, (N, N, N), "f1")
+    _shape(m, (3, N, N, N), "m")
+    _shape(p, (3, N, N, N), "p")
+    rep = Report()
+    st = lib().emd_solve3d(h.ptr, _ptr(f0), _ptr(f1), _ptr(m), _ptr(p), N,
+                           C.byref(opts) if opts is not None else None, C.byref(rep), _stream(stream))
+    return st, rep.as_dict()
+
+
 def emd_solve_batched(h: Handle, f0s, f1s, ms, opts: Opts | None = None, stream=None, ps=None):
     """Batched EMD solve of independent problems; returns (status, [report dicts]).
     ms[b] (and ps[b] when ps is given) receive each problem's last m (and p).
@@ -346,6 +381,12 @@ class State:
     def gap(self, stream=None):
         rep = Report()
         self.h.check(lib().gp_state_gap(self.h.ptr, self._s, C.byref(rep), _stream(stream)))
+        return rep.as_dict()
+
+    def certify(self, stream=None):
+        """gap() plus, for EMD, the feasibility certificate of the current flux."""
+        rep = Report()
+        self.h.check(lib().gp_state_certify(self.h.ptr, self._s, C.byref(rep), _stream(stream)))
         return rep.as_dict()
 
     def close(self):
