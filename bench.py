@@ -70,12 +70,14 @@ SCOPE_BYTES_PER_POINT = {
 SCOPE_BYTES_PER_ITER = {"rof": 52, "emd": 80}
 
 # ncu DRAM traffic (read + write bytes per launch) of the dominant kernel at
-# 4096^2, from the committed summary profiles/spectral_and_fused_4096.md; valid
-# only while the source file holding that kernel is unchanged (sha256 prefix).
+# 4096^2 (the column pass k_cols_grad_4k), from the committed summary named in
+# "profile"; valid only while the source file holding that kernel is unchanged
+# (sha256 prefix), else the line reports traffic null.
 NCU_TRAFFIC = {
-    "dct_cols_grad": {"bytes": 167.9e6, "file": "dct.cu", "src": "70ece90912a866bc",
-                      "ncu": {"dram_pct_of_peak": 15.7, "issue_active_pct": 57.8,
-                              "note": "bound by the shared-memory pipe and latency, not DRAM"}},
+    "dct_cols_grad": {"bytes": 148.7e6, "file": "fftreg.cu", "src": "7d76152a3ad6b054",
+                      "profile": "profiles/fftreg_cols_4096.md",
+                      "ncu": {"dram_pct_of_peak": 14.7, "issue_active_pct": 55.6, "fma_pipe_pct": 45.7,
+                              "note": "bound by FP32 issue and the shared-memory exchanges, not DRAM"}},
 }
 
 
@@ -179,7 +181,7 @@ def _helmholtz64(b, alpha):
                       type=2, norm="ortho", workers=-1)
 
 
-def _bench_3d(h, dev, stream, N3, peak):
+def _bench_3d(h, dev, stream, N3, peak, cap3=5000):
     """The d = 3 instance (rof_solve3d / emd_solve3d) at N3^3: per-iteration time from two
     fixed-length solves, the line-transform pass against HBM, and the time to a gap."""
     import numpy as np
@@ -222,7 +224,7 @@ def _bench_3d(h, dev, stream, N3, peak):
             lms, ln = pc["dct3_lines"]
             avg = lms / 1e3 / max(ln, 1)
             gbs = 8 * n3 / avg / 1e9
-            tol, cap = 1e-4, 5000
+            tol, cap = 1e-4, cap3
             tg, st, rep = run(kind, cap, tol, 0)
             out[kind] = {"value": n3 / it_s, "unit": UNIT, "ms_per_iter": it_s * 1e3,
                          "dct3_lines": {"avg_us": avg * 1e6, "launches": ln, "achieved_gbs": gbs,
@@ -400,7 +402,7 @@ def run_ours(args):
                 "frac_scope_bytes": scope_launch / avg_s / 1e9 / peak,
                 "timing": f"CUDA events around every launch over {prof_steps} steps run right after the timed window"}
     if fresh and "ncu" in tr:  # the same capture's view of what bounds the kernel
-        roofline["ncu"] = dict(tr["ncu"], source="profiles/spectral_and_fused_4096.md")
+        roofline["ncu"] = dict(tr["ncu"], source=tr["profile"])
     kernels = {k: {"ms_total": v[0], "launches": v[1], "avg_us": 1e3 * v[0] / v[1]} for k, v in prof.items() if v[1]}
     # kernels launched inside the timed window: the profiled pass runs the same steps (the timed
     # window replays them from CUDA graphs, kernel for kernel)
@@ -480,65 +482,52 @@ def run_ours(args):
                                     "from pinned host inputs, u and m copied back; copies overlapped with the "
                                     "solves through double-buffered device arrays"}
 
-    # time to relative gap 1e-5 (solve calls from device inputs, CUDA graphs on)
+    # time to relative gap 1e-5 (solve calls from device inputs, CUDA graphs on, the adaptive
+    # gap-check schedule: checks thin out far from the tolerance)
     ttg = None
     if not args.no_ttg:
         ttg = {}
+        cert = ("stops once the corrected flux m + grad Lap^-1((f0-f1) - div m), feasible to "
+                "mass_residual_feasible, is within rel. 1e-5 of the best dual bound met (the iterates' p at "
+                "the checks and windowed averages of them)")
+
+        def emd_row(rep, sec):
+            return {"seconds": sec, "iters": rep["iters"], "status": rep["status_name"],
+                    "rel_gap_feasible": rep["rel_gap_feasible"], "primal": rep["primal"],
+                    "primal_feasible": rep["primal_feasible"], "dual": rep["dual"], "rel_gap": rep["rel_gap"],
+                    "mass_residual": rep["mass_residual"], "mass_residual_feasible": rep["mass_residual_feasible"]}
+
         with torch.cuda.stream(stream):
             m = torch.empty((2, N, N), device=dev)
-            o = gprox.default_opts(max_iters=args.ttg_cap, tol_rel_gap=1e-5, use_graph=1)
-            stream.synchronize()
-            t0 = time.perf_counter()
-            st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, o)
-            ttg["emd"] = {"seconds": time.perf_counter() - t0, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
-                          "status": rep["status_name"], "mass_residual": rep["mass_residual"],
-                          "primal": rep["primal"], "primal_feasible": rep["primal_feasible"],
-                          "rel_gap_feasible": rep["rel_gap_feasible"],
-                          "mass_residual_feasible": rep["mass_residual_feasible"],
-                          "certificate": "stops once the corrected flux m + grad Lap^-1((f0-f1) - div m), "
-                                         "feasible to mass_residual_feasible, has rel. gap <= 1e-5"}
+            o = gprox.default_opts(max_iters=args.ttg_cap, tol_rel_gap=1e-5, gap_every=0, use_graph=1)
             u = torch.empty((N, N), device=dev)
+            stream.synchronize()
             t0 = time.perf_counter()
             st, rep = gprox.rof_solve(h, Id, u, None, LAMBDA, o)
             ttg["rof"] = {"seconds": time.perf_counter() - t0, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
                           "status": rep["status_name"], "tau": rep["tau"]}
+            t0 = time.perf_counter()
+            st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, o)
+            ttg["emd"] = dict(emd_row(rep, time.perf_counter() - t0), certificate=cert, cap=args.ttg_cap)
+            o4 = gprox.default_opts(max_iters=args.ttg_cap, tol_rel_gap=1e-4, gap_every=0, use_graph=1)
+            t0 = time.perf_counter()
+            st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, o4)
+            ttg["emd_1e-4"] = emd_row(rep, time.perf_counter() - t0)
             if N % 64 == 0:
                 # warm-started form: the EMD solved 4x coarser to gap 1e-6, interpolated, as the start
                 # (emd_solve_learned with a network whose output is its prior; the duality gap at
                 # n = 0 picks between that start and zero)
                 base = gprox.Cnn(h, 1, seed=0)
                 base.set_params(np.zeros(base.num_params, np.float32))
-                oc = gprox.default_opts(max_iters=200000, tol_rel_gap=1e-6, gap_every=50, use_graph=1)
+                oc = gprox.default_opts(max_iters=200000, tol_rel_gap=1e-6, gap_every=0, use_graph=1)
                 stream.synchronize()
                 t0 = time.perf_counter()
                 st, rep = gprox.emd_solve_learned(h, base, f0d, f1d, m, None, None, o, 4, oc)
                 sec = time.perf_counter() - t0
                 # the network's output is exactly its prior here, so a start it wins is the prior's
                 start = "prior" if rep["start"] in ("learned", "prior") else rep["start"]
-                ttg["emd_coarse_start"] = {"seconds": sec, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
-                                           "rel_gap_feasible": rep["rel_gap_feasible"],
-                                           "status": rep["status_name"], "start": start,
-                                           "mass_residual": rep["mass_residual"], "coarse_factor": 4,
-                                           "coarse_tol": 1e-6, "speedup": ttg["emd"]["seconds"] / sec}
-            # the same two EMD solves with the adaptive gap-check schedule (gap_every = 0): checks
-            # thin out far from the tolerance (each check costs a dual-potential solve)
-            oa = gprox.default_opts(max_iters=args.ttg_cap, tol_rel_gap=1e-5, gap_every=0, use_graph=1)
-            stream.synchronize()
-            t0 = time.perf_counter()
-            st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, oa)
-            sec = time.perf_counter() - t0
-            ttg["emd_adaptive_checks"] = {"seconds": sec, "iters": rep["iters"], "rel_gap": rep["rel_gap"],
-                                          "status": rep["status_name"], "speedup": ttg["emd"]["seconds"] / sec}
-            if N % 64 == 0:
-                oca = gprox.default_opts(max_iters=200000, tol_rel_gap=1e-6, gap_every=0, use_graph=1)
-                stream.synchronize()
-                t0 = time.perf_counter()
-                st, rep = gprox.emd_solve_learned(h, base, f0d, f1d, m, None, None, oa, 4, oca)
-                sec = time.perf_counter() - t0
-                ttg["emd_coarse_start_adaptive_checks"] = {
-                    "seconds": sec, "iters": rep["iters"], "rel_gap": rep["rel_gap"], "status": rep["status_name"],
-                    "start": "prior" if rep["start"] in ("learned", "prior") else rep["start"],
-                    "speedup": ttg["emd"]["seconds"] / sec}
+                ttg["emd_coarse_start"] = dict(emd_row(rep, sec), start=start, coarse_factor=4, coarse_tol=1e-6,
+                                               speedup=ttg["emd"]["seconds"] / sec)
                 base.close()
 
     # batched solve: 64 independent EMD pairs of sizes drawn from {256, 512, 1024, 2048}^2,
@@ -645,7 +634,7 @@ def run_ours(args):
             os.path.join(ROOT, "MEASURED_PEAKS.json")) else {"bf16_tflops": 1900.0}
         x32 = None
         with torch.cuda.stream(stream):
-            for prec in ("fp32", "split_bf16"):
+            for prec in ("fp32", "split_bf16", "split_fp16", "split_bf16_refined", "split_fp16_refined"):
                 for _ in range(2):
                     h.check(gprox.dct2_poisson(h, bd, xo, 50.0, prec=prec))
                 stream.synchronize()
@@ -661,15 +650,27 @@ def run_ours(args):
                 if prec == "fp32":
                     x32 = x
                 else:
-                    tf = 4 * 3 * 2.0 * N ** 3 / (ms_s / 1e3) / 1e12
+                    gemms = 4 * (2 if prec.endswith("refined") else 1)
+                    tf = gemms * 3 * 2.0 * N ** 3 / (ms_s / 1e3) / 1e12
                     row.update({"rel_l2_vs_fp32": float(np.linalg.norm(x - x32) / np.linalg.norm(x32)),
                                 "tflops": tf, "bf16_peak_tflops": float(pk.get("bf16_tflops", 1900.0)),
                                 "tensor_frac": tf / float(pk.get("bf16_tflops", 1900.0))})
                 prec_study[prec] = row
+            # the ROF solve to relative gap 1e-5 with each transform (config 2's time to gap)
+            u3 = torch.empty((N, N), device=dev)
+            ttg_prec = {}
+            for prec in ("fp32", "split_bf16", "split_fp16", "split_bf16_refined", "split_fp16_refined"):
+                o3 = gprox.default_opts(max_iters=3000, tol_rel_gap=1e-5, gap_every=10, prec=prec)
+                t0 = time.perf_counter()
+                st3, r3 = gprox.rof_solve(h, Id, u3, None, LAMBDA, o3)
+                stream.synchronize()
+                ttg_prec[prec] = {"seconds": time.perf_counter() - t0, "iters": r3["iters"],
+                                  "rel_gap": r3["rel_gap"], "primal": r3["primal"], "status": r3["status_name"]}
+            prec_study["rof_time_to_gap_1e-5"] = ttg_prec
 
     three_d = None
     if not args.no_3d and rank == 0:
-        three_d = _bench_3d(h, dev, stream, args.size3, peak)
+        three_d = _bench_3d(h, dev, stream, args.size3, peak, args.ttg3_cap)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -707,9 +708,10 @@ def main():
     ap.add_argument("--no-prec", action="store_true")
     ap.add_argument("--no-cp2", action="store_true")
     ap.add_argument("--cp2-iters", type=int, default=20000)
-    ap.add_argument("--ttg-cap", type=int, default=60000)
+    ap.add_argument("--ttg-cap", type=int, default=100000)
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--size3", type=int, default=256)
+    ap.add_argument("--ttg3-cap", type=int, default=5000, help="iteration cap of the 3-D runs to a gap")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -64,10 +64,22 @@ typedef enum gp_status {
 } gp_status;
 
 /* Arithmetic of the cosine-transform (Helmholtz / Poisson) solve. */
+/* The split modes need N a multiple of 128 (GP_ERR_UNSUPPORTED otherwise).
+ * Each operand x is stored as x_hi + x_lo in two 16-bit formats and a product
+ * A B^T ~ A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T is accumulated in FP32:
+ * BF16 parts carry 16 significant bits; FP16 parts carry 22, each operand
+ * first multiplied by a power of two taken from its largest magnitude so
+ * that it fits FP16's range (exact: the product is divided back).  The
+ * REFINED modes add one step of residual correction to every solve:
+ * r = b - (alpha - Lap) x / scale evaluated in FP64 from the stored x, then
+ * x += solve(r) (two solves per call; an FP32-level result from the BF16
+ * split). */
 typedef enum gp_prec {
-  GP_PREC_FP32 = 0,        /* FP32 fast cosine transform (power-of-two N) or FP32 dense transform */
-  GP_PREC_SPLIT_BF16 = 1,  /* dense transform on tensor cores, hi+lo bf16 split, FP32 accumulate */
-  GP_PREC_SPLIT_FP16 = 2   /* dense transform on tensor cores, hi+lo fp16 split, FP32 accumulate */
+  GP_PREC_FP32 = 0,                /* FP32 fast cosine transform (power-of-two N) or FP32 dense transform */
+  GP_PREC_SPLIT_BF16 = 1,          /* dense transform on tensor cores, hi+lo bf16 split, FP32 accumulate */
+  GP_PREC_SPLIT_FP16 = 2,          /* dense transform on tensor cores, scaled hi+lo fp16 split, FP32 accumulate */
+  GP_PREC_SPLIT_BF16_REFINED = 3,  /* GP_PREC_SPLIT_BF16 plus one residual-correction solve */
+  GP_PREC_SPLIT_FP16_REFINED = 4   /* GP_PREC_SPLIT_FP16 plus one residual-correction solve */
 } gp_prec;
 
 typedef struct gp_opts {
@@ -109,7 +121,14 @@ typedef struct gp_report {
    *   mass_residual_feasible = h^2 sum |div m~ - (f0 - f1)| / h^2 sum |f0 - f1|
    * and a solve with tol_rel_gap > 0 returns GP_OK only once
    * rel_gap_feasible <= tol_rel_gap (so the optimum lies within that of
-   * primal_feasible).  ROF (unconstrained): primal, rel_gap and 0. */
+   * primal_feasible).  In that mode (EMD, tol_rel_gap > 0) `dual` is the best
+   * lower bound met during the solve: the dual value of the iterate's p at
+   * every check and of averages of those p's (a convex combination of
+   * feasible p's is feasible; the averaging window opens once the gap is
+   * within 30 x tol_rel_gap and restarts whenever the iteration count has
+   * doubled since it opened), and rel_gap / rel_gap_feasible use it; the
+   * last iterate's own dual value lags the optimum far more than its primal
+   * does.  ROF (unconstrained): primal, rel_gap and 0. */
   double primal_feasible;
   double rel_gap_feasible;
   double mass_residual_feasible;
@@ -444,6 +463,24 @@ GP_API gp_status emd_coarse_start(gp_handle h, const float* f0, const float* f1,
                                   const gp_opts* opts, float* phi, gp_report* report, void* stream);
 
 /*
+ * rof_coarse_start: a start for the ROF solve from a coarser grid.  I is
+ * restricted to (N/factor)^2 by block means, the coarse problem (the same
+ * continuum energy of section 3.1: the same lambda, h_c = factor / N) is
+ * solved with rof_solve(opts), and u_c and both planes of p_c are
+ * interpolated bilinearly between cell centres as emd_coarse_start does;
+ * the interpolated p is then made feasible (zero structural slots, |p| <= 1).
+ *   I       device, N*N.  u: device N*N out.  p: device 2*N*N out.
+ *   factor  >= 2 with N % factor == 0 and N / factor >= 2.  lambda > 0.
+ *   opts    the coarse solve's options (warm_start must be 0); report (may
+ *           be NULL) receives the coarse solve's report.
+ * Returns the coarse solve's status (GP_ERR_MAXITER still writes u and p).
+ * Allocates 4 (N/factor)^2 floats of scratch for the call; synchronises the
+ * stream.  The paper has no counterpart (it starts from zero).
+ */
+GP_API gp_status rof_coarse_start(gp_handle h, const float* I, int N, int factor, double lambda,
+                                  const gp_opts* opts, float* u, float* p, gp_report* report, void* stream);
+
+/*
  * Learned warm start for the EMD solve (section 4.2's dual potential).  A
  * 4-level encoder-decoder CNN maps (f0, f1, prior) to a potential phi_0; the
  * start is p_0 = proj(grad phi_0) (forward differences, unit-disc
@@ -514,6 +551,25 @@ GP_API gp_status gp_cnn_loss_grad(gp_cnn net, int B, const float* const* f0, con
 GP_API gp_status gp_cnn_adam_step(gp_cnn net, double lr, void* stream);
 GP_API gp_status emd_solve_learned(gp_handle h, gp_cnn net, const float* f0, const float* f1, float* m, float* p,
                                    float* phi, int N, int coarse_factor, const gp_opts* coarse_opts,
+                                   const gp_opts* opts, gp_report* report, int* start_used, void* stream);
+
+/*
+ * rof_solve_learned: the same network as a warm start for rof_solve
+ * (section 3.1; the strong convexity of Corollary 3.4 makes the primal
+ * iterate the quantity a start should approximate).  The inputs per cell
+ * are I - mean(I), 0 and the prior u_prior - mean(I) (rof_coarse_start's u
+ * when coarse_factor >= 2, none when 0), i.e. gp_cnn_forward with
+ * f0 = 8 (I - mean), f1 = -f0; the learned start is u_0 = mean(I) + phi
+ * (a fidelity minimiser keeps the mean), paired with the prior's p (zero
+ * without a prior).  The duality gap at n = 0 picks among the learned start,
+ * the prior alone and zero (*start_used: 0 zero, 1 learned, 2 prior).
+ * Training targets: u* - mean(I) of converged solves (see learn.py).
+ * Arguments as rof_solve (u out, p may be NULL) and emd_solve_learned;
+ * coarse_opts NULL: relative gap 1e-4, at most 100000 iterations.
+ * Allocates 4 N^2 floats of scratch for the call.
+ */
+GP_API gp_status rof_solve_learned(gp_handle h, gp_cnn net, const float* I, float* u, float* p, int N,
+                                   double lambda, int coarse_factor, const gp_opts* coarse_opts,
                                    const gp_opts* opts, gp_report* report, int* start_used, void* stream);
 
 #ifdef __cplusplus

@@ -94,6 +94,9 @@ struct gp_handle_s {
   double* bres_h = nullptr;
   float* v3 = nullptr;  // volumes of the 3-D solves
   size_t v3_cap = 0;
+  float* rf = nullptr;  // scratch of the refined split-precision solves
+  size_t rf_cap = 0;
+  double* rfd = nullptr;  // partial sums and the sum of the split solves' mean removal
 };
 
 struct gp_state_s {
@@ -125,6 +128,10 @@ struct gp_state_s {
   int rb = 16;                  // row-block height of the fused kernel (autotuned tile shape)
   bool partials_valid = false;  // part holds the fused gap partials of the current iterate
   double mass_den = 0;          // EMD: sum |f0 - f1| (mass-residual normaliser)
+  // EMD stopping test: FP64 sum of p over the current averaging window (2 N^2)
+  // and the potential of the window's average (N^2), see run_loop
+  double* pwin = nullptr;
+  float* phiwin = nullptr;
   std::vector<void*> allocs;
   // CUDA graphs of k-step chunks, keyed by (k, cur, prec, gap_last)
   std::map<std::tuple<int, int, int, int>, cudaGraphExec_t> graphs;
@@ -234,6 +241,38 @@ gp_status ensure_res(gp_handle h) {
   return GP_OK;
 }
 
+bool prec_split(int prec) { return prec >= GP_PREC_SPLIT_BF16 && prec <= GP_PREC_SPLIT_FP16_REFINED; }
+bool prec_fp16(int prec) { return prec == GP_PREC_SPLIT_FP16 || prec == GP_PREC_SPLIT_FP16_REFINED; }
+bool prec_refined(int prec) { return prec == GP_PREC_SPLIT_BF16_REFINED || prec == GP_PREC_SPLIT_FP16_REFINED; }
+constexpr int kPrecMax = GP_PREC_SPLIT_FP16_REFINED;
+
+// Scratch of the split solves' refinement and mean removal (handle-owned, grown on demand).
+gp_status ensure_rf(gp_handle h, size_t floats) {
+  if (!h->rfd) GP_CUDA(h, cudaMalloc(&h->rfd, 1040 * sizeof(double)));
+  if (floats <= h->rf_cap) return GP_OK;
+  if (h->rf) cudaFree(h->rf);
+  h->rf = nullptr;
+  h->rf_cap = 0;
+  GP_CUDA(h, cudaMalloc(&h->rf, floats * sizeof(float)));
+  h->rf_cap = floats;
+  return GP_OK;
+}
+
+// The split-precision plan of size N (dense matrices, their split tiles) and
+// the tensor-core timeout flag.
+gp_status tc_prepare(gp_handle h, int N, bool grad, bool f16, cudaStream_t st, DctPlan** out) {
+  DctPlan* pm = &h->plans[N];
+  GP_CUDA(h, dct_plan_dense(*pm));
+  if (grad) GP_CUDA(h, dct_plan_grad_dense(*pm));
+  GP_CUDA(h, dct_plan_tc_split(*pm, st, f16));
+  if (!h->tc_err) {
+    GP_CUDA(h, cudaMalloc(&h->tc_err, sizeof(int)));
+    GP_CUDA(h, cudaMemset(h->tc_err, 0, sizeof(int)));
+  }
+  *out = pm;
+  return GP_OK;
+}
+
 // x = scale (alpha - Lap)^{-1} b with the plan of size N; `tmp` holds 2 N^2.
 gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double alpha, double scale, int prec,
                 bool allow_fast, cudaStream_t st) {
@@ -241,16 +280,36 @@ gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double
   gp_status s = get_plan(h, N, &p);
   if (s != GP_OK) return s;
   const float a = (float)alpha, sc = (float)scale;
-  if (prec == GP_PREC_SPLIT_BF16) {
+  if (prec_split(prec)) {
     if (!tc_solve_supported(N)) return fail(h, GP_ERR_UNSUPPORTED, "split-precision solve needs N a multiple of 128");
-    DctPlan* pm = &h->plans[N];
-    GP_CUDA(h, dct_plan_dense(*pm));
-    GP_CUDA(h, dct_plan_tc_split(*pm, st));
-    if (!h->tc_err) {
-      GP_CUDA(h, cudaMalloc(&h->tc_err, sizeof(int)));
-      GP_CUDA(h, cudaMemset(h->tc_err, 0, sizeof(int)));
+    const bool f16 = prec_fp16(prec);
+    DctPlan* pm = nullptr;
+    if ((s = tc_prepare(h, N, false, f16, st, &pm)) != GP_OK) return s;
+    const int nl = f16 ? 9 : 5;
+    const size_t NN = (size_t)N * N;
+    const float* b0 = b;
+    if ((s = ensure_rf(h, 3 * NN)) != GP_OK) return s;
+    if (alpha == 0.0) {
+      // the constant mode is dropped: remove it before the GEMMs, whose
+      // rounding of a large mean would leak into the other modes
+      GP_CUDA(h, plaunch(h, PK_SETUP, st,
+                         [&] { return launch_center(b, h->rf + 2 * NN, NN, h->rfd + 8, h->rfd, st); }, 3));
+      b0 = h->rf + 2 * NN;
+    } else if (prec_refined(prec) && b == x) {  // the residual needs b after x is written
+      GP_CUDA(h, cudaMemcpyAsync(h->rf + 2 * NN, b, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      b0 = h->rf + 2 * NN;
     }
-    GP_CUDA(h, plaunch(h, PK_DCT_TC, st, [&] { return dct_solve_tc(*pm, b, x, tmp, a, sc, h->tc_err, st); }));
+    GP_CUDA(h, plaunch(h, PK_DCT_TC, st, [&] { return dct_solve_tc(*pm, b0, x, tmp, a, sc, h->tc_err, st, f16); },
+                       nl));
+    if (prec_refined(prec)) {  // r = b - (alpha - Lap) x / scale in FP64; x += solve(r)
+      float* r = h->rf;
+      float* t = h->rf + NN;
+      GP_CUDA(h, plaunch(h, PK_SETUP, st,
+                         [&] { return launch_helmholtz_residual(b0, x, r, N, alpha, 1.0 / scale, st); }));
+      GP_CUDA(h, plaunch(h, PK_DCT_TC, st, [&] { return dct_solve_tc(*pm, r, t, tmp, a, sc, h->tc_err, st, f16); },
+                         nl));
+      GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_add_inplace(x, t, NN, st); }));
+    }
     return GP_OK;
   }
   if (prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
@@ -271,13 +330,16 @@ gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double
 // dense solve's output (phi is then always written).  tmp holds 2 N^2.
 // b_rows: b already holds the row spectra of the right-hand side (the
 // interleaved output of the forward row pass; fast sizes, FP32 only).
+// cscr / cdscr (optional, split modes at alpha == 0): an N^2 plane and 1032
+// doubles of the caller's for the mean removal, so that concurrent solves of
+// different states (batched branches) share no scratch.
 gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, bool want_phi, float* tmp,
-                     double alpha, double scale, int prec, cudaStream_t st, bool b_rows = false) {
+                     double alpha, double scale, int prec, cudaStream_t st, bool b_rows = false,
+                     float* cscr = nullptr, double* cdscr = nullptr) {
   const DctPlan* p = nullptr;
   gp_status s = get_plan(h, N, &p);
   if (s != GP_OK) return s;
-  if (prec != GP_PREC_FP32 && prec != GP_PREC_SPLIT_BF16)
-    return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
+  if (prec != GP_PREC_FP32 && !prec_split(prec)) return fail(h, GP_ERR_ARG, "unknown prec");
   if (b_rows && !(p->fft && prec == GP_PREC_FP32)) return fail(h, GP_ERR_ARG, "row spectra need the FP32 fast path");
   const float a = (float)alpha, sc = (float)scale;
   const size_t NN = (size_t)N * N;
@@ -294,20 +356,55 @@ gp_status solve_grad(gp_handle h, int N, const float* b, float* g2, float* phi, 
                        [&] { return dct_grad_rows(*p, A, B, g2, g2 + NN, want_phi ? phi : nullptr, st); }));
     return GP_OK;
   }
-  if (prec == GP_PREC_SPLIT_BF16 && tc_solve_supported(N)) {
+  if (prec_split(prec) && tc_solve_supported(N)) {
     // tensor-core GEMMs with the gradient synthesised from the spectrum
-    DctPlan* pm = &h->plans[N];
-    GP_CUDA(h, dct_plan_dense(*pm));
-    GP_CUDA(h, dct_plan_grad_dense(*pm));
-    GP_CUDA(h, dct_plan_tc_split(*pm, st));
-    if (!h->tc_err) {
-      GP_CUDA(h, cudaMalloc(&h->tc_err, sizeof(int)));
-      GP_CUDA(h, cudaMemset(h->tc_err, 0, sizeof(int)));
+    const bool f16 = prec_fp16(prec), ref = prec_refined(prec);
+    DctPlan* pm = nullptr;
+    if ((s = tc_prepare(h, N, true, f16, st, &pm)) != GP_OK) return s;
+    auto nl = [&](bool ph) { return f16 ? (ph ? 15 : 14) : (ph ? 8 : 7); };
+    if ((s = ensure_rf(h, 6 * NN)) != GP_OK) return s;
+    const float* b0 = b;
+    if (alpha == 0.0) {  // as in solve(): the dropped constant mode leaves before the GEMMs
+      float* c = cscr ? cscr : h->rf + 5 * NN;
+      double* cd = cdscr ? cdscr : h->rfd;
+      GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_center(b, c, NN, cd + 8, cd, st); }, 3));
+      b0 = c;
+    } else if (ref && (b == g2 || b == g2 + NN || (want_phi && b == phi))) {
+      GP_CUDA(h, cudaMemcpyAsync(h->rf + 5 * NN, b, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      b0 = h->rf + 5 * NN;
     }
+    if (!ref) {
+      GP_CUDA(h, plaunch(
+                     h, PK_DCT_TC, st,
+                     [&] {
+                       return dct_grad_tc(*pm, b0, g2, g2 + NN, want_phi ? phi : nullptr, tmp, a, sc, h->tc_err, st,
+                                          f16);
+                     },
+                     nl(want_phi)));
+      return GP_OK;
+    }
+    // One residual correction.  x0 = S b (the solve), r = b - (alpha - Lap) x0 / scale
+    // in FP64 from the stored x0, then grad x = D x0 + G r and x = x0 + S r: D x0,
+    // the forward differences of the stored x0, is exact up to one rounding of
+    // each difference, and G r, the split gradient of the correction, errs only
+    // relative to the correction.  (G b + G r would keep G's own error on b.)
+    float* x0 = want_phi ? phi : h->rf;
+    float* r = h->rf + NN;
+    float* gg = h->rf + 2 * NN;
+    float* ph1 = h->rf + 4 * NN;
+    GP_CUDA(h, plaunch(h, PK_DCT_TC, st, [&] { return dct_solve_tc(*pm, b0, x0, tmp, a, sc, h->tc_err, st, f16); },
+                       f16 ? 9 : 5));
+    GP_CUDA(h, plaunch(h, PK_SETUP, st,
+                       [&] { return launch_helmholtz_residual(b0, x0, r, N, alpha, 1.0 / scale, st); }));
+    GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_grad(x0, g2, N, st); }));
     GP_CUDA(h, plaunch(
                    h, PK_DCT_TC, st,
-                   [&] { return dct_grad_tc(*pm, b, g2, g2 + NN, want_phi ? phi : nullptr, tmp, a, sc, h->tc_err, st); },
-                   want_phi ? 8 : 7));
+                   [&] {
+                     return dct_grad_tc(*pm, r, gg, gg + NN, want_phi ? ph1 : nullptr, tmp, a, sc, h->tc_err, st, f16);
+                   },
+                   nl(want_phi)));
+    GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_add_inplace(g2, gg, 2 * NN, st); }));
+    if (want_phi) GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_add_inplace(phi, ph1, NN, st); }));
     return GP_OK;
   }
   if (!phi) return fail(h, GP_ERR_ARG, "internal: the dense gradient solve needs a plane for the solution");
@@ -347,6 +444,8 @@ void free_state(gp_state s) {
   if (!s) return;
   drop_graphs(s);
   if (s->avg_sum) cudaFree(s->avg_sum);
+  if (s->pwin) cudaFree(s->pwin);
+  if (s->phiwin) cudaFree(s->phiwin);
   for (void* p : s->allocs) cudaFree(p);
   delete s;
 }
@@ -570,7 +669,7 @@ gp_status emd_steps_direct(gp_state s, int n_steps, int prec, bool gap_last, cud
     }
     // grad q, q = Lap^{-1} d  <=>  (0 - Lap) q = -d
     gp_status r = solve_grad(h, N, rows_in ? s->rh : s->r, s->prim, s->phi, false, s->tmp, 0.0, -1.0, prec, st,
-                             rows_in);
+                             rows_in, s->s[1 - s->cur], s->part);
     if (r != GP_OK) return r;
     const bool g = gap_last && (k == n_steps - 1);
     const int c = s->cur;
@@ -724,7 +823,8 @@ gp_status state_gap_enqueue(gp_state s, double* dst, int prec, cudaStream_t st) 
             }));
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 2, 0u, dst, st); }));
   // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p = e; grad phi into prim (free between steps)
-  gp_status r = solve_grad(h, N, s->e, s->prim, s->phi, true, s->tmp, 0.0, 1.0, prec, st);
+  gp_status r = solve_grad(h, N, s->e, s->prim, s->phi, true, s->tmp, 0.0, 1.0, prec, st, false, s->s[1 - s->cur],
+                           s->part);
   if (r != GP_OK) return r;
   const int nd = reduce_blocks_1d(NN);
   double* pd = s->part + (size_t)nb * 4;
@@ -863,7 +963,7 @@ struct Timer {
 gp_status check_opts(gp_handle h, const gp_opts* o) {
   if (o->max_iters < 0) return fail(h, GP_ERR_ARG, "max_iters < 0");
   if (o->gap_every < 0) return fail(h, GP_ERR_ARG, "gap_every < 0");
-  if (o->prec < 0 || o->prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
+  if (o->prec < 0 || o->prec > kPrecMax) return fail(h, GP_ERR_ARG, "unknown prec");
   if (o->warm_start < 0 || o->warm_start > 1) return fail(h, GP_ERR_ARG, "unknown warm_start");
   return GP_OK;
 }
@@ -917,6 +1017,110 @@ int adaptive_chunk(int n_prev, double g_prev, int n, double g, double tol) {
   return k;
 }
 
+// EMD dual bound of the average of the p's summed in s->pwin (count n): p_bar
+// into prim, e = -div p_bar, phi = Lap^{-1} div p_bar with its gradient (prim),
+// D = h^2 sum phi (f1 - f0) / max(1, max |grad phi|).  A convex combination of
+// feasible p's is feasible, so D bounds the optimum from below.  Uses prim,
+// e, tmp and the partial sums (free between chunks).
+gp_status emd_window_dual(gp_state s, long long n, double* D, cudaStream_t st) {
+  gp_handle h = s->h;
+  const int N = s->N;
+  const size_t NN = (size_t)N * N;
+  const int nd = reduce_blocks_1d(NN);
+  gp_status r = ensure_res(h);
+  if (r != GP_OK) return r;
+  GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_scale_sum(s->pwin, s->prim, 2 * NN, 1.0 / (double)n, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] {
+            return launch_emd_primal(s->m, s->prim, s->f0, s->f1, s->e, N, s->part, nd, st);  // e = -div p_bar
+          }));
+  if ((r = solve_grad(h, N, s->e, s->prim, s->phiwin, true, s->tmp, 0.0, 1.0, GP_PREC_FP32, st)) != GP_OK) return r;
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st,
+                     [&] { return launch_emd_dual(s->phiwin, s->prim, s->f0, s->f1, N, s->part, nd, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nd, 2, 2u, h->dres, st); }));
+  if ((r = fetch(h, 2, st)) != GP_OK) return r;
+  *D = h->hres[0] / ((double)N * N) / fmax(1.0, h->hres[1]);
+  s->partials_valid = false;
+  return GP_OK;
+}
+
+// EMD stopping test with a tolerance (run_loop and the batched loop).  The
+// dual bound is the best one met so far, over the iterates' p at the checks
+// and over averages of those p's (windows that open once the gap is within
+// 30 x tol and restart whenever the iteration count has doubled since their
+// start); each is a lower bound of the optimum, and the last iterate's p
+// lags it.  A candidate (gap with the best bound within 2 x tol: the
+// corrected primal is usually a little below the stored one) is certified
+// at most every 100 iterations unless the plain gap already meets tol; the
+// solve stops once the certified gap does.
+struct EmdStop {
+  double d_best = -INFINITY;
+  int win_start = -1, last_cert = -1000000;
+  long long win_n = 0;
+};
+
+double rel_gap_of(double P, double D) {
+  const double sc = fmax(fabs(P), fabs(D));
+  return sc > 0 ? (P - D) / sc : 0.0;
+}
+
+gp_status emd_close_window(gp_state s, EmdStop& z, cudaStream_t st) {
+  if (z.win_n == 0) return GP_OK;
+  double Dw;
+  gp_status q = emd_window_dual(s, z.win_n, &Dw, st);
+  if (q == GP_OK && Dw > z.d_best) z.d_best = Dw;
+  return q;
+}
+
+// After a plain check filled rep (P, the iterate's D, the plain gap).
+gp_status emd_stop_check(gp_state s, EmdStop& z, double tol, gp_report* rep, cudaStream_t st, bool* certified,
+                         bool* stop) {
+  gp_handle h = s->h;
+  const size_t NN = (size_t)s->N * s->N;
+  gp_status r;
+  *stop = false;
+  if (rep->dual > z.d_best) z.d_best = rep->dual;
+  if (z.win_start < 0 && rep->rel_gap <= 30.0 * tol) z.win_start = s->n;
+  if (z.win_start >= 0) {
+    if (s->n >= 2 * z.win_start && z.win_n > 0) {  // restart the window
+      if ((r = emd_close_window(s, z, st)) != GP_OK) return r;
+      z.win_n = 0;
+      z.win_start = s->n;
+    }
+    if (!s->pwin) GP_CUDA(h, cudaMalloc(&s->pwin, 2 * NN * sizeof(double)));
+    if (!s->phiwin) GP_CUDA(h, cudaMalloc(&s->phiwin, NN * sizeof(float)));
+    if (z.win_n == 0) GP_CUDA(h, cudaMemsetAsync(s->pwin, 0, 2 * NN * sizeof(double), st));
+    GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_accumulate(s->pwin, s->p[s->cur], 2 * NN, st); }));
+    ++z.win_n;
+  }
+  rep->dual = z.d_best;
+  rep->rel_gap = rel_gap_of(rep->primal, z.d_best);
+  if (rep->rel_gap <= 2.0 * tol && (rep->rel_gap <= tol || s->n - z.last_cert >= 100)) {
+    z.last_cert = s->n;
+    if ((r = emd_close_window(s, z, st)) != GP_OK) return r;
+    if ((r = emd_certify(s, rep, st)) != GP_OK) return r;
+    rep->dual = z.d_best;
+    rep->rel_gap = rel_gap_of(rep->primal, z.d_best);
+    rep->rel_gap_feasible = rel_gap_of(rep->primal_feasible, z.d_best);
+    *certified = true;
+    *stop = rep->rel_gap_feasible <= tol;
+  }
+  return GP_OK;
+}
+
+// The certificate of the returned iterate when the last check did not take it.
+gp_status emd_stop_final(gp_state s, EmdStop& z, bool stop_test, gp_report* rep, cudaStream_t st) {
+  gp_status r;
+  if (rep->dual > z.d_best) z.d_best = rep->dual;  // a solve with no check yet (max_iters == 0)
+  if (stop_test && (r = emd_close_window(s, z, st)) != GP_OK) return r;
+  if ((r = emd_certify(s, rep, st)) != GP_OK) return r;
+  if (stop_test) {
+    rep->dual = z.d_best;
+    rep->rel_gap = rel_gap_of(rep->primal, z.d_best);
+    rep->rel_gap_feasible = rel_gap_of(rep->primal_feasible, z.d_best);
+  }
+  return GP_OK;
+}
+
 // Chunked solve loop shared by rof_solve / emd_solve: run gap_every
 // iterations (the last one with the fused gap reductions), check, repeat;
 // gap_every == 0 takes the adaptive schedule above.
@@ -927,7 +1131,9 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
   rep->primal = rep->dual = rep->rel_gap = rep->mass_residual = NAN;
   rep->primal_feasible = rep->rel_gap_feasible = rep->mass_residual_feasible = NAN;
   const bool emd = s->kind == KIND_EMD;
+  const bool stop_test = o.tol_rel_gap > 0;
   bool certified = false;  // the report's certificate belongs to the current iterate
+  EmdStop z;
   gp_status r;
   if (o.max_iters == 0 && (r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
   int k_next = o.gap_every > 0 ? o.gap_every : kAdaptiveMinChunk;
@@ -943,16 +1149,15 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
       fail(h, status, "non-finite objective: the iteration broke down");
       break;
     }
-    if (o.tol_rel_gap > 0 && rep->rel_gap <= o.tol_rel_gap) {
-      // EMD: stop only on the gap of the corrected, feasible flux
-      if (emd) {
-        if ((r = emd_certify(s, rep, st)) != GP_OK) return r;
-        certified = true;
-      }
-      if (!emd || rep->rel_gap_feasible <= o.tol_rel_gap) {
-        status = GP_OK;
-        break;
-      }
+    bool stop = false;
+    if (emd && stop_test) {
+      if ((r = emd_stop_check(s, z, o.tol_rel_gap, rep, st, &certified, &stop)) != GP_OK) return r;
+    } else {
+      stop = stop_test && rep->rel_gap <= o.tol_rel_gap;
+    }
+    if (stop) {
+      status = GP_OK;
+      break;
     }
     if (watch.update(rep->rel_gap)) {
       status = GP_ERR_DIVERGED;
@@ -966,7 +1171,7 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
     }
   }
   if (emd && !certified && status != GP_ERR_NONFINITE && isfinite(rep->dual) &&
-      (r = emd_certify(s, rep, st)) != GP_OK)
+      (r = emd_stop_final(s, z, stop_test, rep, st)) != GP_OK)
     return r;
   rep->iters = s->n;
   rep->tau = s->tau;
@@ -1103,6 +1308,8 @@ gp_status gp_destroy(gp_handle h) {
   for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
   if (h->ws) cudaFree(h->ws);
   if (h->v3) cudaFree(h->v3);
+  if (h->rf) cudaFree(h->rf);
+  if (h->rfd) cudaFree(h->rfd);
   if (h->tc_err) cudaFree(h->tc_err);
   if (h->part) cudaFree(h->part);
   if (h->dres) cudaFree(h->dres);
@@ -1118,7 +1325,7 @@ gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alph
   h->err.clear();
   if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
   if (!(alpha >= 0.0) || !isfinite(alpha)) return fail(h, GP_ERR_ARG, "alpha must be finite and >= 0");
-  if (prec < 0 || prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
+  if (prec < 0 || prec > kPrecMax) return fail(h, GP_ERR_ARG, "unknown prec");
   DeviceGuard g(h->device);
   if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
   gp_status r;
@@ -1127,7 +1334,7 @@ gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alph
   const DctPlan* p = nullptr;
   if ((r = get_plan(h, N, &p)) != GP_OK) return r;
   const bool aligned = aligned16(b) && aligned16(x);
-  if ((p->fft || prec == GP_PREC_SPLIT_BF16) && !aligned)
+  if ((p->fft || prec_split(prec)) && !aligned)
     return fail(h, GP_ERR_ARG, "b and x must be 16-byte aligned for this size / precision");
   const size_t need = 2 * (size_t)N * N;
   if (h->ws_floats < need) {
@@ -1138,7 +1345,7 @@ gp_status dct2_poisson(gp_handle h, const float* b, float* x, int N, double alph
     h->ws_floats = need;
   }
   r = solve(h, N, b, x, h->ws, alpha, 1.0, prec, true, (cudaStream_t)stream);
-  if (r == GP_OK && prec == GP_PREC_SPLIT_BF16) {
+  if (r == GP_OK && prec_split(prec)) {
     // the tensor-core kernels report a timed-out wait through a flag: check it
     int flag = 0;
     GP_CUDA(h, cudaMemcpyAsync(&flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
@@ -1153,7 +1360,7 @@ gp_status dct2_poisson_grad(gp_handle h, const float* b, float* g, int N, double
   h->err.clear();
   if (N < 1 || N > 8192) return fail(h, GP_ERR_ARG, "N out of range [1, 8192]");
   if (!(alpha >= 0.0) || !isfinite(alpha)) return fail(h, GP_ERR_ARG, "alpha must be finite and >= 0");
-  if (prec < 0 || prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
+  if (prec < 0 || prec > kPrecMax) return fail(h, GP_ERR_ARG, "unknown prec");
   DeviceGuard dg(h->device);
   if (!dg.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
   gp_status r;
@@ -1229,7 +1436,7 @@ gp_status pd_step(gp_handle h, gp_state s, int n_steps, int prec, void* stream) 
   if (!h || !s || s->h != h) return h ? fail(h, GP_ERR_ARG, "state does not belong to handle") : GP_ERR_ARG;
   h->err.clear();
   if (n_steps < 0) return fail(h, GP_ERR_ARG, "n_steps < 0");
-  if (prec < 0 || prec > 2) return fail(h, GP_ERR_ARG, "unknown prec");
+  if (prec < 0 || prec > kPrecMax) return fail(h, GP_ERR_ARG, "unknown prec");
   DeviceGuard g(h->device);
   if (n_steps == 0) return GP_OK;
   // The last step of every call also leaves the gap partials (and, for EMD,
@@ -1748,6 +1955,10 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
   if (r != GP_OK) return r;
   if (B < 1 || !f0 || !f1 || !m || !N || !reports) return fail(h, GP_ERR_ARG, "bad batch arguments");
   if (o.warm_start) return fail(h, GP_ERR_ARG, "warm_start is not available for batched solves");
+  // the FP16 split's scale slots and the refinement scratch are per plan and
+  // per handle: concurrent branches would share them
+  if (prec_fp16(o.prec) || prec_refined(o.prec))
+    return fail(h, GP_ERR_UNSUPPORTED, "batched solves take the FP32 or the BF16 split transform");
   DeviceGuard g(h->device);
   if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1802,6 +2013,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
   for (int b = 0; b < B; ++b) active.push_back(b);
   std::vector<DivergenceWatch> watch(B);
   std::vector<char> certified(B, 0);  // problem b's report holds the certificate of its current iterate
+  std::vector<EmdStop> stops(B);
   cudaGraphExec_t exec = nullptr;
   int exec_k = -1;
   bool first = true;
@@ -1886,17 +2098,15 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
       rep.tau = s->tau;
       rep.sigma = s->sigma;
       rep.seconds = t.s();
-      bool stop = false;
+      bool stop = false, met = false, cert = false;
       if (!isfinite(rep.primal) || !isfinite(rep.dual)) {
         rep.status = GP_ERR_NONFINITE;
         stop = true;
-      } else if (o.tol_rel_gap > 0 && rep.rel_gap <= o.tol_rel_gap &&
-                 (certified[b] = true, (r = emd_certify(s, &rep, st)) == GP_OK) &&
-                 rep.rel_gap_feasible <= o.tol_rel_gap) {
-        rep.status = GP_OK;  // the corrected, feasible flux's gap met the tolerance too
-        stop = true;
-      } else if (r != GP_OK) {
+      } else if (o.tol_rel_gap > 0 && (r = emd_stop_check(s, stops[b], o.tol_rel_gap, &rep, st, &cert, &met)) != GP_OK) {
         return r;
+      } else if ((certified[b] = cert, met)) {
+        rep.status = GP_OK;  // the corrected, feasible flux's gap met the tolerance
+        stop = true;
       } else if (watch[b].update(rep.rel_gap)) {
         rep.status = GP_ERR_DIVERGED;
         stop = true;
@@ -1914,7 +2124,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
   for (int b = 0; b < B; ++b) {  // every report carries the certificate of the returned iterate
     gp_state s = h->batch[b];
     if (!certified[b] && reports[b].status != GP_ERR_NONFINITE && isfinite(reports[b].dual) &&
-        (r = emd_certify(s, &reports[b], st)) != GP_OK)
+        (r = emd_stop_final(s, stops[b], o.tol_rel_gap > 0, &reports[b], st)) != GP_OK)
       return r;
   }
   gp_status worst = GP_OK;

@@ -286,6 +286,33 @@ __global__ void k_cnn_input(const float* __restrict__ f0, const float* __restric
 __global__ void k_add(float* __restrict__ phi, const float* __restrict__ prior, long NN) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < NN; i += (long)gridDim.x * blockDim.x) phi[i] += prior[i];
 }
+// ROF through the same network: *sum = sum I (FP64); the inputs a = 8 (I - mean),
+// b = -a (so that the input channels are I - mean and 0) and the prior
+// u_prior - mean; the start is u = mean + phi.
+__global__ void k_sum64(const float* __restrict__ x, long n, double* __restrict__ sum) {
+  double s = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) s += x[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(sum, s);
+}
+__global__ void k_rof_net_inputs(const float* __restrict__ I, const float* __restrict__ uprior,
+                                 const double* __restrict__ sum, float* __restrict__ a, float* __restrict__ b,
+                                 float* __restrict__ pr, long NN) {
+  const float mean = (float)(*sum / (double)NN);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < NN; i += (long)gridDim.x * blockDim.x) {
+    const float c = I[i] - mean;
+    a[i] = 8.f * c;
+    b[i] = -8.f * c;
+    if (uprior) pr[i] = uprior[i] - mean;
+  }
+}
+__global__ void k_rof_from_net(const float* __restrict__ phi, const double* __restrict__ sum, float* __restrict__ u,
+                               long NN) {
+  const float mean = (float)(*sum / (double)NN);
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < NN; i += (long)gridDim.x * blockDim.x)
+    u[i] = mean + phi[i];
+}
 // x[b] -= sum[b] / NN for B planes of NN values
 __global__ void k_sub_mean(float* __restrict__ x, long NN, int B, const double* __restrict__ sum) {
   const long n = (long)B * NN;
@@ -457,6 +484,7 @@ struct gp_cnn_s {
   float* grd[NACT] = {};
   float *phi = nullptr, *dphi = nullptr, *tgt = nullptr, *pw = nullptr, *prior = nullptr;
   double* dsc = nullptr;  // per-sample FP64 scalars
+  int* tc_err = nullptr;  // timeout flag of the tensor-core convolutions (BF16 mode)
   std::string err;
 };
 
@@ -547,8 +575,13 @@ struct Net {
   template <typename TO, bool RELU>
   void conv(int i, const T* x, long xbs, TO* y, long ybs, int l) const {
     const Conv& c = n->convs[i];
-    k_conv3x3<T, T, TO, RELU, false><<<cgrid(l, c.cout), TS * TS, 0, st>>>(x, xbs, c.cin, W(i), Bv(i), y, ybs, c.cout,
-                                                                           side(l), side(l));
+    if constexpr (sizeof(T) == 2) {  // BF16 mode: implicit GEMM on the tensor cores
+      gp::conv3x3_tc(x, xbs, c.cin, W(i), Bv(i), y, ybs, c.cout, side(l), side(l), B, RELU, sizeof(TO) == 4, n->tc_err,
+                 st);
+    } else {
+      k_conv3x3<T, T, TO, RELU, false><<<cgrid(l, c.cout), TS * TS, 0, st>>>(x, xbs, c.cin, W(i), Bv(i), y, ybs,
+                                                                             c.cout, side(l), side(l));
+    }
   }
   void pool(int src, long sch0, int dst, int C, int l) const {  // level l -> l + 1
     k_pool2<T><<<g1d((long)B * C * plane(l + 1)), 256, 0, st>>>(ptr(src, sch0), bs(src), ptr(dst), bs(dst), C, side(l), B);
@@ -725,7 +758,8 @@ GP_API gp_status gp_cnn_create(gp_handle h, int base_channels, int bf16, unsigne
   const size_t P = (size_t)n->nparam;
   if (!g.ok || cudaMalloc((void**)&n->w, P * 4) || cudaMalloc((void**)&n->m, P * 4) ||
       cudaMalloc((void**)&n->v, P * 4) || cudaMalloc((void**)&n->g, P * 4) ||
-      cudaMalloc(&n->wc, P * (n->bf16 ? 2 : 4))) {
+      cudaMalloc(&n->wc, P * (n->bf16 ? 2 : 4)) || cudaMalloc((void**)&n->tc_err, sizeof(int)) ||
+      cudaMemset(n->tc_err, 0, sizeof(int))) {
     cudaGetLastError();
     gp_cnn_destroy(n);
     return GP_ERR_CUDA;
@@ -760,6 +794,7 @@ GP_API gp_status gp_cnn_destroy(gp_cnn n) {
   cudaFree(n->v);
   cudaFree(n->g);
   cudaFree(n->wc);
+  cudaFree(n->tc_err);
   delete n;
   return GP_OK;
 }
@@ -928,6 +963,111 @@ GP_API gp_status emd_solve_learned(gp_handle h, gp_cnn n, const float* f0, const
   if (r != GP_OK && !(r == GP_ERR_MAXITER || r == GP_ERR_DIVERGED || r == GP_ERR_NONFINITE))
     return cfail(n, r, gp_last_error(h));
   if (r != GP_OK) n->err = gp_last_error(h);
+  rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (report) *report = rep;
+  if (start_used) *start_used = choice;
+  return r;
+}
+
+
+GP_API gp_status rof_solve_learned(gp_handle h, gp_cnn n, const float* I, float* u, float* p, int N, double lambda,
+                                   int coarse_factor, const gp_opts* coarse_opts, const gp_opts* opts,
+                                   gp_report* report, int* start_used, void* stream) {
+  if (!h || !n || n->h != h) return GP_ERR_ARG;
+  n->err.clear();
+  const auto t0 = std::chrono::steady_clock::now();
+  DevGuard g(n->device);
+  gp_status r = check_batch(n, 1, &I, &I, nullptr, N);
+  if (r != GP_OK) return r;
+  if ((r = check_dev(n, u, "u")) != GP_OK) return r;
+  if (p && (r = check_dev(n, p, "p")) != GP_OK) return r;
+  if (coarse_factor < 0 || coarse_factor == 1) return cfail(n, GP_ERR_ARG, "coarse_factor must be 0 (none) or >= 2");
+  if (!(lambda > 0)) return cfail(n, GP_ERR_ARG, "lambda must be > 0");
+  gp_opts o;
+  gp_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.warm_start) return cfail(n, GP_ERR_ARG, "opts.warm_start must be 0: the start is chosen here");
+  if ((r = reserve(n, 1, N)) != GP_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  const long NN = (long)N * N;
+  // scratch: the two network inputs (tgt, dphi), the centred prior, the learned u, the probe p
+  float* buf = nullptr;
+  CN_CUDA(n, cudaMalloc(&buf, 4 * (size_t)NN * sizeof(float)));
+  struct Free {
+    float* b;
+    ~Free() { cudaFree(b); }
+  } fr{buf};
+  float* pr = buf;
+  float* ul = buf + NN;
+  float* pp = buf + 2 * NN;
+  const float* uprior = nullptr;
+  const float* pprior = nullptr;
+  if (coarse_factor) {
+    gp_opts oc;
+    gp_default_opts(&oc);
+    oc.tol_rel_gap = 1e-4;
+    oc.max_iters = 100000;
+    oc.use_graph = o.use_graph;
+    if (coarse_opts) oc = *coarse_opts;
+    gp_report rc;
+    r = rof_coarse_start(h, I, N, coarse_factor, lambda, &oc, n->prior, n->pw, &rc, stream);
+    if (r != GP_OK && r != GP_ERR_MAXITER) return cfail(n, r, std::string("coarse start: ") + gp_last_error(h));
+    uprior = n->prior;
+    pprior = n->pw;
+  }
+  CN_CUDA(n, cudaMemsetAsync(n->dsc, 0, sizeof(double), st));
+  k_sum64<<<g1d(NN), 256, 0, st>>>(I, NN, n->dsc);
+  k_rof_net_inputs<<<g1d(NN), 256, 0, st>>>(I, uprior, n->dsc, n->tgt, n->dphi, pr, NN);
+  CN_CUDA(n, cudaGetLastError());
+  const float* fa = n->tgt;
+  const float* fb = n->dphi;
+  const float* prc = pr;
+  if ((r = forward(n, 1, &fa, &fb, uprior ? &prc : nullptr, N, st)) != GP_OK) return r;
+  k_rof_from_net<<<g1d(NN), 256, 0, st>>>(n->phi, n->dsc, ul, NN);
+  CN_CUDA(n, cudaGetLastError());
+  // Candidates: learned u (with the prior's p, else p = 0), the prior alone, zero;
+  // the smallest duality gap at n = 0 decides.
+  auto load = [&](const float* uc, const float* pc) -> gp_status {
+    CN_CUDA(n, cudaMemcpyAsync(u, uc, NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (pc) CN_CUDA(n, cudaMemcpyAsync(pp, pc, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else CN_CUDA(n, cudaMemsetAsync(pp, 0, 2 * NN * sizeof(float), st));
+    return GP_OK;
+  };
+  gp_opts probe = o;
+  probe.max_iters = 0;
+  probe.warm_start = 1;
+  double best = INFINITY;
+  int choice = 0;
+  const float* cu[2] = {ul, uprior};
+  for (int c = 0; c < 2; ++c) {
+    if (!cu[c]) continue;
+    if ((r = load(cu[c], pprior)) != GP_OK) return r;
+    gp_report rw;
+    r = rof_solve(h, I, u, pp, N, lambda, &probe, &rw, stream);
+    if (r != GP_OK && r != GP_ERR_MAXITER) return cfail(n, r, std::string("start probe: ") + gp_last_error(h));
+    if (rw.rel_gap < best) {
+      best = rw.rel_gap;
+      choice = c == 0 ? 1 : 2;
+    }
+  }
+  probe.warm_start = 0;
+  gp_report rz;
+  r = rof_solve(h, I, u, nullptr, N, lambda, &probe, &rz, stream);
+  if (r != GP_OK && r != GP_ERR_MAXITER) return cfail(n, r, std::string("zero probe: ") + gp_last_error(h));
+  if (!(best < rz.rel_gap)) choice = 0;
+  gp_report rep;
+  if (choice == 0) {
+    r = rof_solve(h, I, u, p, N, lambda, &o, &rep, stream);
+  } else {
+    if ((r = load(choice == 1 ? ul : uprior, pprior)) != GP_OK) return r;
+    o.warm_start = 1;
+    r = rof_solve(h, I, u, pp, N, lambda, &o, &rep, stream);
+    if (p) CN_CUDA(n, cudaMemcpyAsync(p, pp, 2 * NN * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  }
+  if (r != GP_OK && !(r == GP_ERR_MAXITER || r == GP_ERR_DIVERGED || r == GP_ERR_NONFINITE))
+    return cfail(n, r, gp_last_error(h));
+  if (r != GP_OK) n->err = gp_last_error(h);
+  CN_CUDA(n, cudaStreamSynchronize(st));
   rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (report) *report = rep;
   if (start_used) *start_used = choice;

@@ -1839,6 +1839,11 @@ void dct_plan_free(DctPlan& p) {
   if (p.CTs) cudaFree(p.CTs);
   if (p.Es) cudaFree(p.Es);
   if (p.ETs) cudaFree(p.ETs);
+  if (p.Cs16) cudaFree(p.Cs16);
+  if (p.CTs16) cudaFree(p.CTs16);
+  if (p.Es16) cudaFree(p.Es16);
+  if (p.ETs16) cudaFree(p.ETs16);
+  if (p.tc16) cudaFree(p.tc16);
   if (p.err) cudaFree(p.err);
   p = DctPlan();
 }

@@ -45,6 +45,13 @@ struct DctPlan {
   void* CTs = nullptr;
   void* Es = nullptr;
   void* ETs = nullptr;
+  // the same in hi / lo FP16, scaled by a power of two (FP16 split mode), and
+  // that mode's scale / maximum slots (32 floats, see tc_gemm.cu)
+  void* Cs16 = nullptr;
+  void* CTs16 = nullptr;
+  void* Es16 = nullptr;
+  void* ETs16 = nullptr;
+  float* tc16 = nullptr;
   int* err = nullptr;  // fast sizes: set to 1 by a transform kernel whose bulk copy never landed
 };
 
@@ -111,19 +118,27 @@ cudaError_t solve_grad3(const DctPlan& p, const float* b, float* g3, float* u, f
                         float alpha, float scale, cudaStream_t st, int* nlaunch);
 // Build C (and C^T) for a plan that lacks them (tensor-core path).
 cudaError_t dct_plan_dense(DctPlan& p);
-// Split-precision (hi + lo BF16) tensor-core form, N % 128 == 0: four tcgen05
-// GEMMs; tmp holds 2*N*N floats; *err is set to 1 if a wait timed out.
+// Split-precision (hi + lo BF16, or FP16 with power-of-two scales) tensor-core
+// form, N % 128 == 0: four tcgen05 GEMMs (FP16: each product staged in FP32
+// and split with its own scale, x used as the staging plane); tmp holds
+// 2*N*N floats; *err is set to 1 if a wait timed out.
 bool tc_solve_supported(int N);
+// Warm-start network (BF16 mode): 3x3 convolution as a tcgen05 implicit GEMM
+// (cnn_tc.cu); X, W BF16, Y BF16 (or FP32 when y_fp32), Cout <= 256; *err is
+// set to 1 if a wait timed out.
+cudaError_t conv3x3_tc(const void* X, long xbs, int Cin, const void* W, const float* bias, void* Y, long ybs, int Cout,
+                       int H, int Wd, int B, bool relu, bool y_fp32, int* err, cudaStream_t st);
 cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
-                         cudaStream_t st);
+                         cudaStream_t st, bool fp16);
 // Gradient of the split-precision solve, taken in the spectral domain with
 // tensor-core GEMMs (7, or 8 with phi): gx = C^T Q E, gy = E^T Q C with
 // Q = gain .* (C b C^T).  tmp holds 2*N*N floats; gy doubles as scratch.
 cudaError_t dct_plan_grad_dense(DctPlan& p);
-// Pre-split tile copies of the dense matrices the plan has (tensor-core path).
-cudaError_t dct_plan_tc_split(DctPlan& p, cudaStream_t st);
+// Pre-split tile copies of the dense matrices the plan has (tensor-core path;
+// fp16: the scaled FP16 copies and the mode's slot array).
+cudaError_t dct_plan_tc_split(DctPlan& p, cudaStream_t st, bool fp16);
 cudaError_t dct_grad_tc(const DctPlan& p, const float* b, float* gx, float* gy, float* phi, float* tmp, float alpha,
-                        float scale, int* err, cudaStream_t st);
+                        float scale, int* err, cudaStream_t st, bool fp16);
 // Dense-matrix form (any N): tmp must hold 2*N*N floats.
 cudaError_t dct_solve_dense_fp32(const DctPlan& p, const float* b, float* x, float* tmp,
                                  float alpha, float scale, cudaStream_t st);

@@ -610,6 +610,48 @@ inline int grid_1d(size_t n, int threads) {
   return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
+// Residual of the Helmholtz equation in FP64 from the stored FP32 solution:
+// r = b - inv_scale (alpha x - Lap x), Lap the 5-point Neumann stencil
+// (neighbours outside the grid omitted), h = 1/N.  The FP32 rounding of the
+// result is relative to r itself, which is small when x is close.
+__global__ void __launch_bounds__(256) k_helmholtz_residual(const float* __restrict__ b, const float* __restrict__ x,
+                                                            float* __restrict__ r, int N, double alpha,
+                                                            double inv_scale) {
+  const size_t NN = (size_t)N * N;
+  const double n2 = (double)N * N;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < NN; i += (size_t)gridDim.x * blockDim.x) {
+    const int row = (int)(i / N), col = (int)(i % N);
+    const double xc = x[i];
+    double lap = 0.0;
+    if (col > 0) lap += (double)x[i - 1] - xc;
+    if (col < N - 1) lap += (double)x[i + 1] - xc;
+    if (row > 0) lap += (double)x[i - N] - xc;
+    if (row < N - 1) lap += (double)x[i + N] - xc;
+    r[i] = (float)((double)b[i] - inv_scale * (alpha * xc - n2 * lap));
+  }
+}
+
+// Mean removal on the device (no host round trip): sum x, then out = x - sum / n.
+__global__ void __launch_bounds__(256) k_sum(const float* __restrict__ x, size_t n, double* __restrict__ part) {
+  CSum a;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    a.add(x[i]);
+  double v[1] = {a.value()};
+  block_reduce_store<1>(v, 0u, part);
+}
+__global__ void __launch_bounds__(256) k_center(const float* __restrict__ x, float* __restrict__ out, size_t n,
+                                                const double* __restrict__ sum) {
+  const float mean = (float)(*sum / (double)n);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = x[i] - mean;
+}
+
+// x += y
+__global__ void __launch_bounds__(256) k_add_inplace(float* __restrict__ x, const float* __restrict__ y, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    x[i] += y[i];
+}
+
 // ------------------------------------------------------------------- 3-D
 // The d = 3 instance of the updates above (Algorithm 2 for general d;
 // sections 3.1 / 3.2): volumes (z, y, x), x fastest, n3 = N^3 points;
@@ -976,6 +1018,22 @@ cudaError_t launch_copy_field(const float* a, float* b, int N, cudaStream_t st) 
 
 // ------------------------------------------------------------------ 3-D
 
+cudaError_t launch_helmholtz_residual(const float* b, const float* x, float* r, int N, double alpha, double inv_scale,
+                                     cudaStream_t st) {
+  k_helmholtz_residual<<<grid_1d((size_t)N * N, 256), 256, 0, st>>>(b, x, r, N, alpha, inv_scale);
+  return cudaGetLastError();
+}
+cudaError_t launch_center(const float* x, float* out, size_t n, double* part, double* sum, cudaStream_t st) {
+  const int nb = reduce_blocks_1d(n);
+  k_sum<<<nb, 256, 0, st>>>(x, n, part);
+  k_final_reduce<<<1, 256, 0, st>>>(part, nb, 1, 0u, sum);
+  k_center<<<grid_1d(n, 256), 256, 0, st>>>(x, out, n, sum);
+  return cudaGetLastError();
+}
+cudaError_t launch_add_inplace(float* x, const float* y, size_t n, cudaStream_t st) {
+  k_add_inplace<<<grid_1d(n, 256), 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
 cudaError_t launch_rof3_pstep(const float* gu, const float* pin, float* pout, int N, float sigma, cudaStream_t st) {
   k_rof3_pstep<<<grid_1d((size_t)N * N * N, 256), 256, 0, st>>>(gu, pin, pout, N, sigma);
   return cudaGetLastError();

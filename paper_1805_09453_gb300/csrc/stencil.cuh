@@ -70,6 +70,13 @@ cudaError_t launch_scale_sum(const double* sum, float* out, size_t n, double sca
 cudaError_t launch_emd_average_flux(const double* s_sum, const float* gq, float* m, size_t n2, double scale,
                                     cudaStream_t st);
 cudaError_t launch_grad(const float* x, float* g, int N, cudaStream_t st);
+// Refined split-precision solves: r = b - inv_scale (alpha - Lap) x in FP64; x += y.
+cudaError_t launch_helmholtz_residual(const float* b, const float* x, float* r, int N, double alpha, double inv_scale,
+                                     cudaStream_t st);
+cudaError_t launch_add_inplace(float* x, const float* y, size_t n, cudaStream_t st);
+// out = x - mean(x), the mean reduced on the device; part holds reduce_blocks_1d(n)
+// doubles, sum one double.
+cudaError_t launch_center(const float* x, float* out, size_t n, double* part, double* sum, cudaStream_t st);
 // 3-D (N^3 volumes, (z, y, x), vector fields as three volumes; see stencil.cu).
 cudaError_t launch_rof3_pstep(const float* gu, const float* pin, float* pout, int N, float sigma, cudaStream_t st);
 cudaError_t launch_rof3_rhs(const float* pout, const float* pin, const float* gu, const float* I, float* r, int N,

@@ -149,20 +149,51 @@ __host__ __device__ __forceinline__ size_t split_tile_offset(int rb, int kb, int
   return ((size_t)rb * (size_t)(N / BK) + (size_t)kb) * (size_t)(2 * TILE_BYTES);
 }
 
-// M (N x N, row-major FP32) -> pre-split tiles.  One thread per 4 consecutive
-// elements of a row.
-__global__ void k_split_tiles(const float* __restrict__ M, uint8_t* __restrict__ out, int N) {
+// M (N x N, row-major FP32) -> pre-split tiles of s M.  One thread per 4
+// consecutive elements of a row.  BF16 keeps FP32's exponent range: s = 1.
+// FP16 (5 exponent bits) takes a power of two from the largest |M| (amax,
+// written by an earlier kernel): with amax = f 2^e, f in [0.5, 1),
+// s = 2^(14 - e) puts |s M| below 2^14, far inside FP16's range, and keeps the
+// low parts normal down to 2^-17 of the largest entry (smaller entries keep
+// an absolute error below 2^-38 of it).  *scale_out receives s.
+template <bool BF16>
+__global__ void k_split_tiles(const float* __restrict__ M, uint8_t* __restrict__ out, int N,
+                              const unsigned* __restrict__ amax, float* __restrict__ scale_out) {
+  float sc = 1.f;
+  if (!BF16 && amax) {
+    const float a = __uint_as_float(__ldg(amax));
+    if (a > 0.f && a <= 3.0e38f) {
+      int e;
+      frexpf(a, &e);
+      sc = ldexpf(1.f, 14 - e);
+    }
+  }
+  if (scale_out && blockIdx.x == 0 && threadIdx.x == 0) *scale_out = sc;
   const long n4 = (long)N * N / 4;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
     const int r = (int)(i / (N / 4)), k = (int)(i % (N / 4)) * 4;
-    const float4 v = *reinterpret_cast<const float4*>(M + (size_t)r * N + k);
+    float4 v = *reinterpret_cast<const float4*>(M + (size_t)r * N + k);
+    v.x *= sc;
+    v.y *= sc;
+    v.z *= sc;
+    v.w *= sc;
     uint2 h, l;
-    split4<true>(v, h, l);
+    split4<BF16>(v, h, l);
     uint8_t* tile = out + split_tile_offset(r / BM, k / BK, N);
     const uint32_t off = kmajor_offset(r % BM, k % BK);
     *reinterpret_cast<uint2*>(tile + off) = h;
     *reinterpret_cast<uint2*>(tile + TILE_BYTES + off) = l;
   }
+}
+
+// *amax = max(*amax, max |x|) over n floats (non-negative floats order as integers).
+__global__ void k_amax(const float* __restrict__ x, size_t n, unsigned* __restrict__ amax) {
+  float m = 0.f;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));
 }
 
 // D(m0.., n0..) = epi( A(m0.., :) B(n0.., :)^T ), A: M x K, B: Nc x K, both
@@ -178,7 +209,8 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
                                                            const uint8_t* __restrict__ As,
                                                            const uint8_t* __restrict__ Bs, float* __restrict__ D,
                                                            int Nn, int K, int mode, const float* __restrict__ mu,
-                                                           float alpha, float gscale, float sa, float sb,
+                                                           float alpha, float gscale, const float* __restrict__ sap,
+                                                           const float* __restrict__ sbp, unsigned* __restrict__ amax,
                                                            int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + STAGES * 4 * TILE_BYTES);  // per stage: MMAs done
@@ -202,6 +234,7 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = instr_desc<BF16>();
+  const float sa = sap ? __ldg(sap) : 1.f, sb = sbp ? __ldg(sbp) : 1.f;
   bool ok = true;
   uint32_t phase[STAGES], fphase[STAGES];  // parity of each stage's next MMA / bulk-copy completion
 #pragma unroll
@@ -282,8 +315,9 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int quad = warp & 3;            // a warp reads the tensor-memory lanes of its quadrant
     const int m = m0 + quad * 32 + lane;  // this thread's accumulator row
-    const float inv = 1.f / (sa * sb);
+    const float inv = 1.f / (sa * sb);  // powers of two: exact
     const float mum = mu ? __ldg(&mu[m]) : 0.f;
+    float vmax = 0.f;
 #pragma unroll 1
     for (int c0 = (warp >> 2) * (BN / 2); c0 < (warp >> 2) * (BN / 2) + BN / 2; c0 += 32) {
       uint32_t r[32];
@@ -308,6 +342,7 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
           x = den > 0.f ? x * (gscale / den) : 0.f;
         }
         v[c] = x;
+        vmax = fmaxf(vmax, fabsf(x));
       }
       if constexpr (OSPLIT) {
         uint8_t* Ds = reinterpret_cast<uint8_t*>(D);
@@ -343,6 +378,11 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
         for (int c = 0; c < 32; ++c) D[(size_t)(n0 + c0 + c) * Nn + m] = v[c];
       }
     }
+    if (amax) {  // max |D| for the power-of-two scale of the next split (non-negative floats order as integers)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) vmax = fmaxf(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      if (lane == 0) atomicMax(amax, __float_as_uint(vmax));
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -354,31 +394,37 @@ __global__ void __launch_bounds__(THREADS) k_tc_gemm_split(const float* __restri
 
 template <bool BF16, int PRE, bool OSPLIT>
 cudaError_t gemm_launch(const float* A, const float* B, const void* As, const void* Bs, void* D, int N, int mode,
-                        const float* mu, float alpha, float gscale, int* err, cudaStream_t st) {
+                        const float* mu, float alpha, float gscale, const float* sap, const float* sbp,
+                        unsigned* amax, int* err, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k_tc_gemm_split<BF16, PRE, OSPLIT>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
   if (e != cudaSuccess) return e;
   dim3 grid(N / BN, N / BM);
   k_tc_gemm_split<BF16, PRE, OSPLIT><<<grid, THREADS, SMEM_BYTES, st>>>(
-      A, B, (const uint8_t*)As, (const uint8_t*)Bs, (float*)D, N, N, mode, mu, alpha, gscale, 1.f, 1.f, err);
+      A, B, (const uint8_t*)As, (const uint8_t*)Bs, (float*)D, N, N, mode, mu, alpha, gscale, sap, sbp, amax, err);
   return cudaGetLastError();
 }
 
-// An operand of a product: FP32 (split on the fly) or pre-split tiles.
+// An operand of a product: FP32 (split on the fly) or pre-split tiles with
+// their scale (device pointer; nullptr = 1).
 struct Op {
   const float* f = nullptr;
   const void* s = nullptr;
+  const float* sc = nullptr;
 };
-inline Op pre(const void* s) { return Op{nullptr, s}; }
+inline Op pre(const void* s, const float* sc = nullptr) { return Op{nullptr, s, sc}; }
 
-// D (FP32, or pre-split tiles when dsplit) = epi(A B^T).
+// D (FP32, or pre-split tiles when dsplit) = epi(A B^T); amax (FP32 output
+// only, may be nullptr) collects max |D|.
 template <bool BF16>
 cudaError_t gemm(Op A, Op B, void* D, bool dsplit, int N, int mode, const float* mu, float alpha, float gscale,
-                 int* err, cudaStream_t st) {
+                 int* err, cudaStream_t st, unsigned* amax = nullptr) {
   const int pre_mask = (A.s ? 1 : 0) | (B.s ? 2 : 0);
-#define GP_G(P)                                                                                            \
-  return dsplit ? gemm_launch<BF16, P, true>(A.f, B.f, A.s, B.s, D, N, mode, mu, alpha, gscale, err, st) \
-                : gemm_launch<BF16, P, false>(A.f, B.f, A.s, B.s, D, N, mode, mu, alpha, gscale, err, st)
+#define GP_G(P)                                                                                                \
+  return dsplit ? gemm_launch<BF16, P, true>(A.f, B.f, A.s, B.s, D, N, mode, mu, alpha, gscale, A.sc, B.sc,  \
+                                              nullptr, err, st)                                                \
+                : gemm_launch<BF16, P, false>(A.f, B.f, A.s, B.s, D, N, mode, mu, alpha, gscale, A.sc, B.sc, \
+                                              amax, err, st)
   switch (pre_mask) {
     case 1: GP_G(1);
     case 2: GP_G(2);
@@ -388,49 +434,92 @@ cudaError_t gemm(Op A, Op B, void* D, bool dsplit, int N, int mode, const float*
 #undef GP_G
 }
 
+int split_blocks(int N) { return (int)std::min<long>(((long)N * N / 4 + 255) / 256, 8192); }
+
+// FP32 M -> pre-split tiles (FP16: scaled by the power of two of *amax, stored in *scale_out).
+template <bool BF16>
+cudaError_t split(const float* M, void* out, int N, const unsigned* amax, float* scale_out, cudaStream_t st) {
+  k_split_tiles<BF16><<<split_blocks(N), 256, 0, st>>>(M, (uint8_t*)out, N, amax, scale_out);
+  return cudaGetLastError();
+}
+
+cudaError_t amax_of(const float* x, size_t n, unsigned* amax, cudaStream_t st) {
+  const size_t b = (n + 255) / 256;
+  k_amax<<<(unsigned)(b < 4096 ? b : 4096), 256, 0, st>>>(x, n, amax);
+  return cudaGetLastError();
+}
+
+// Scale and max slots of the FP16 mode (DctPlan::tc16): scales at [i], maxima
+// at [kAmax + i]: 0 b, 1..5 the intermediate products, 8 C / C^T, 9 E / E^T.
+constexpr int kAmax = 16, kSlotC = 8, kSlotE = 9, kTc16Floats = 32;
+
 }  // namespace
 
 bool tc_solve_supported(int N) { return N >= 128 && N <= 8192 && N % 128 == 0; }
 
-namespace {
-// The FP32 input of the first product as pre-split tiles (so that every
-// product's operands arrive by bulk copy).
-cudaError_t split_input(const float* b, void* out, int N, cudaStream_t st) {
-  const int blocks = (int)std::min<long>(((long)N * N / 4 + 255) / 256, 8192);
-  k_split_tiles<<<blocks, 256, 0, st>>>(b, (uint8_t*)out, N);
-  return cudaGetLastError();
-}
-}  // namespace
-
-cudaError_t dct_plan_tc_split(DctPlan& p, cudaStream_t st) {
+cudaError_t dct_plan_tc_split(DctPlan& p, cudaStream_t st, bool fp16) {
   const int N = p.N;
   const size_t bytes = (size_t)N * N * 4;
   const float* src[4] = {p.C, p.CT, p.E, p.ET};
-  void** dst[4] = {&p.Cs, &p.CTs, &p.Es, &p.ETs};
+  cudaError_t e;
+  if (!fp16) {
+    void** dst[4] = {&p.Cs, &p.CTs, &p.Es, &p.ETs};
+    for (int i = 0; i < 4; ++i) {
+      if (!src[i] || *dst[i]) continue;
+      if ((e = cudaMalloc(dst[i], bytes))) return e;
+      if ((e = split<true>(src[i], *dst[i], N, nullptr, nullptr, st))) return e;
+    }
+    return cudaSuccess;
+  }
+  if (!p.tc16) {
+    if ((e = cudaMalloc(&p.tc16, kTc16Floats * sizeof(float)))) return e;
+    if ((e = cudaMemsetAsync(p.tc16, 0, kTc16Floats * sizeof(float), st))) return e;
+  }
+  unsigned* am = reinterpret_cast<unsigned*>(p.tc16 + kAmax);
+  void** dst[4] = {&p.Cs16, &p.CTs16, &p.Es16, &p.ETs16};
+  const int slot[4] = {kSlotC, kSlotC, kSlotE, kSlotE};  // a matrix and its transpose share the maximum
   for (int i = 0; i < 4; ++i) {
     if (!src[i] || *dst[i]) continue;
-    cudaError_t e = cudaMalloc(dst[i], bytes);
-    if (e != cudaSuccess) return e;
-    const int blocks = (int)std::min<long>(((long)N * N / 4 + 255) / 256, 8192);
-    k_split_tiles<<<blocks, 256, 0, st>>>(src[i], (uint8_t*)*dst[i], N);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = cudaMalloc(dst[i], bytes))) return e;
+    if ((e = amax_of(src[i], (size_t)N * N, am + slot[i], st))) return e;
+    if ((e = split<false>(src[i], *dst[i], N, am + slot[i], p.tc16 + slot[i], st))) return e;
   }
   return cudaSuccess;
 }
 
 cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool fp16) {
   const int N = p.N;
-  if (!p.Cs || !p.CTs || !tc_solve_supported(N)) return cudaErrorInvalidValue;
+  if (!tc_solve_supported(N)) return cudaErrorInvalidValue;
   // intermediates are stored as pre-split tiles (4 bytes per element, as FP32)
   void* t0 = tmp;
   void* t1 = tmp + (size_t)N * N;
   cudaError_t e;
-  if ((e = split_input(b, t1, N, st))) return e;                                                         // t1 = split(b)
-  if ((e = gemm<true>(pre(t1), pre(p.Cs), t0, true, N, 1, nullptr, alpha, scale, err, st))) return e;  // T1^T = (b C^T)^T
-  if ((e = gemm<true>(pre(p.Cs), pre(t0), t1, true, N, 1, p.mu, alpha, scale, err, st))) return e;   // T2^T = (gain .* C T1)^T
-  if ((e = gemm<true>(pre(p.CTs), pre(t1), t0, true, N, 0, nullptr, alpha, scale, err, st))) return e;  // T3 = C^T T2
-  return gemm<true>(pre(t0), pre(p.CTs), x, false, N, 0, nullptr, alpha, scale, err, st);            // x = T3 C
+  if (!fp16) {
+    if (!p.Cs || !p.CTs) return cudaErrorInvalidValue;
+    if ((e = split<true>(b, t1, N, nullptr, nullptr, st))) return e;                                     // t1 = split(b)
+    if ((e = gemm<true>(pre(t1), pre(p.Cs), t0, true, N, 1, nullptr, alpha, scale, err, st))) return e;  // T1^T = (b C^T)^T
+    if ((e = gemm<true>(pre(p.Cs), pre(t0), t1, true, N, 1, p.mu, alpha, scale, err, st))) return e;   // T2^T = (gain .* C T1)^T
+    if ((e = gemm<true>(pre(p.CTs), pre(t1), t0, true, N, 0, nullptr, alpha, scale, err, st))) return e;  // T3 = C^T T2
+    return gemm<true>(pre(t0), pre(p.CTs), x, false, N, 0, nullptr, alpha, scale, err, st);            // x = T3 C
+  }
+  // FP16: each product is written in FP32 (x serves as the staging plane: b
+  // is consumed first) with its max |.|, then split with its own scale
+  if (!p.Cs16 || !p.CTs16 || !p.tc16) return cudaErrorInvalidValue;
+  float* sc = p.tc16;
+  unsigned* am = reinterpret_cast<unsigned*>(p.tc16 + kAmax);
+  const float* sC = sc + kSlotC;
+  if ((e = cudaMemsetAsync(am, 0, 8 * sizeof(unsigned), st))) return e;
+  if ((e = amax_of(b, (size_t)N * N, am, st))) return e;
+  if ((e = split<false>(b, t1, N, am, sc, st))) return e;
+  if ((e = gemm<false>(pre(t1, sc), pre(p.Cs16, sC), x, false, N, 1, nullptr, alpha, scale, err, st, am + 1))) return e;
+  if ((e = split<false>(x, t0, N, am + 1, sc + 1, st))) return e;
+  if ((e = gemm<false>(pre(p.Cs16, sC), pre(t0, sc + 1), x, false, N, 1, p.mu, alpha, scale, err, st, am + 2))) return e;
+  if ((e = split<false>(x, t1, N, am + 2, sc + 2, st))) return e;
+  if ((e = gemm<false>(pre(p.CTs16, sC), pre(t1, sc + 2), x, false, N, 0, nullptr, alpha, scale, err, st, am + 3)))
+    return e;
+  if ((e = split<false>(x, t0, N, am + 3, sc + 3, st))) return e;
+  return gemm<false>(pre(t0, sc + 3), pre(p.CTs16, sC), x, false, N, 0, nullptr, alpha, scale, err, st);
 }
 
 // Spectral gradient in the split-precision mode (the forward differences of
@@ -439,25 +528,55 @@ cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp,
 //   X = C b^T,  Q = gain .* (C X^T) (and Q^T),  U = C^T Q,
 //   gx = U E,  phi = U C (optional),  V^T = (Q C)^T,  gy = E^T V.
 // X, Z = tmp; Q lives in gy until the last product; intermediates are
-// pre-split tiles.
+// pre-split tiles (FP16: staged in FP32 in gx, then in X, and split with
+// their own scales).
 cudaError_t dct_grad_tc(const DctPlan& p, const float* b, float* gx, float* gy, float* phi, float* tmp, float alpha,
-                        float scale, int* err, cudaStream_t st) {
+                        float scale, int* err, cudaStream_t st, bool fp16) {
   const int N = p.N;
-  if (!p.Cs || !p.CTs || !p.ETs || !tc_solve_supported(N)) return cudaErrorInvalidValue;
+  if (!tc_solve_supported(N)) return cudaErrorInvalidValue;
   void* X = tmp;
   void* Z = tmp + (size_t)N * N;
   void* Q = gy;
   cudaError_t e;
-  if ((e = split_input(b, Z, N, st))) return e;                                                            // Z = split(b)
-  if ((e = gemm<true>(pre(Z), pre(p.Cs), X, true, N, 1, nullptr, alpha, scale, err, st))) return e;      // X = C b^T
-  if ((e = gemm<true>(pre(p.Cs), pre(X), Q, true, N, 0, p.mu, alpha, scale, err, st))) return e;        // Q
-  if ((e = gemm<true>(pre(p.Cs), pre(X), Z, true, N, 1, p.mu, alpha, scale, err, st))) return e;        // Z = Q^T
-  if ((e = gemm<true>(pre(p.CTs), pre(Z), X, true, N, 0, nullptr, alpha, scale, err, st))) return e;    // X = U = C^T Q
-  if ((e = gemm<true>(pre(X), pre(p.ETs), gx, false, N, 0, nullptr, alpha, scale, err, st))) return e;  // gx = U E
-  if (phi && (e = gemm<true>(pre(X), pre(p.CTs), phi, false, N, 0, nullptr, alpha, scale, err, st)))
-    return e;                                                                                            // phi = U C
-  if ((e = gemm<true>(pre(Q), pre(p.CTs), Z, true, N, 1, nullptr, alpha, scale, err, st))) return e;    // Z = (Q C)^T
-  return gemm<true>(pre(p.ETs), pre(Z), gy, false, N, 0, nullptr, alpha, scale, err, st);               // gy = E^T V
+  if (!fp16) {
+    if (!p.Cs || !p.CTs || !p.ETs) return cudaErrorInvalidValue;
+    if ((e = split<true>(b, Z, N, nullptr, nullptr, st))) return e;                                        // Z = split(b)
+    if ((e = gemm<true>(pre(Z), pre(p.Cs), X, true, N, 1, nullptr, alpha, scale, err, st))) return e;      // X = C b^T
+    if ((e = gemm<true>(pre(p.Cs), pre(X), Q, true, N, 0, p.mu, alpha, scale, err, st))) return e;        // Q
+    if ((e = gemm<true>(pre(p.Cs), pre(X), Z, true, N, 1, p.mu, alpha, scale, err, st))) return e;        // Z = Q^T
+    if ((e = gemm<true>(pre(p.CTs), pre(Z), X, true, N, 0, nullptr, alpha, scale, err, st))) return e;    // X = U = C^T Q
+    if ((e = gemm<true>(pre(X), pre(p.ETs), gx, false, N, 0, nullptr, alpha, scale, err, st))) return e;  // gx = U E
+    if (phi && (e = gemm<true>(pre(X), pre(p.CTs), phi, false, N, 0, nullptr, alpha, scale, err, st)))
+      return e;                                                                                            // phi = U C
+    if ((e = gemm<true>(pre(Q), pre(p.CTs), Z, true, N, 1, nullptr, alpha, scale, err, st))) return e;    // Z = (Q C)^T
+    return gemm<true>(pre(p.ETs), pre(Z), gy, false, N, 0, nullptr, alpha, scale, err, st);               // gy = E^T V
+  }
+  if (!p.Cs16 || !p.CTs16 || !p.ETs16 || !p.tc16) return cudaErrorInvalidValue;
+  float* sc = p.tc16;
+  unsigned* am = reinterpret_cast<unsigned*>(p.tc16 + kAmax);
+  const float* sC = sc + kSlotC;
+  const float* sE = sc + kSlotE;
+  float* F = gx;  // FP32 staging until gx is written
+  if ((e = cudaMemsetAsync(am, 0, 8 * sizeof(unsigned), st))) return e;
+  if ((e = amax_of(b, (size_t)N * N, am, st))) return e;
+  if ((e = split<false>(b, Z, N, am, sc, st))) return e;
+  if ((e = gemm<false>(pre(Z, sc), pre(p.Cs16, sC), F, false, N, 1, nullptr, alpha, scale, err, st, am + 1))) return e;
+  if ((e = split<false>(F, X, N, am + 1, sc + 1, st))) return e;                                         // X
+  if ((e = gemm<false>(pre(p.Cs16, sC), pre(X, sc + 1), F, false, N, 0, p.mu, alpha, scale, err, st, am + 2))) return e;
+  if ((e = split<false>(F, Q, N, am + 2, sc + 2, st))) return e;                                         // Q
+  if ((e = gemm<false>(pre(p.Cs16, sC), pre(X, sc + 1), F, false, N, 1, p.mu, alpha, scale, err, st, am + 3))) return e;
+  if ((e = split<false>(F, Z, N, am + 3, sc + 3, st))) return e;                                         // Z = Q^T
+  if ((e = gemm<false>(pre(p.CTs16, sC), pre(Z, sc + 3), F, false, N, 0, nullptr, alpha, scale, err, st, am + 4)))
+    return e;
+  if ((e = split<false>(F, X, N, am + 4, sc + 4, st))) return e;                                         // X = U
+  if ((e = gemm<false>(pre(X, sc + 4), pre(p.ETs16, sE), gx, false, N, 0, nullptr, alpha, scale, err, st))) return e;
+  if (phi && (e = gemm<false>(pre(X, sc + 4), pre(p.CTs16, sC), phi, false, N, 0, nullptr, alpha, scale, err, st)))
+    return e;
+  float* G = reinterpret_cast<float*>(X);  // U is consumed: X stages (Q C)^T
+  if ((e = gemm<false>(pre(Q, sc + 2), pre(p.CTs16, sC), G, false, N, 1, nullptr, alpha, scale, err, st, am + 5)))
+    return e;
+  if ((e = split<false>(G, Z, N, am + 5, sc + 5, st))) return e;                                         // Z = (Q C)^T
+  return gemm<false>(pre(p.ETs16, sE), pre(Z, sc + 5), gy, false, N, 0, nullptr, alpha, scale, err, st);  // gy = E^T V
 }
 
 }  // namespace gp

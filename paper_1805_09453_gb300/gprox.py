@@ -18,7 +18,7 @@ _lib = None
 GP_OK, GP_ERR_ARG, GP_ERR_CUDA, GP_ERR_MAXITER, GP_ERR_NONFINITE, GP_ERR_DIVERGED, GP_ERR_MASS, GP_ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = {0: "GP_OK", 1: "GP_ERR_ARG", 2: "GP_ERR_CUDA", 3: "GP_ERR_MAXITER", 4: "GP_ERR_NONFINITE",
                 5: "GP_ERR_DIVERGED", 6: "GP_ERR_MASS", 7: "GP_ERR_UNSUPPORTED"}
-PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2}
+PREC = {"fp32": 0, "split_bf16": 1, "split_fp16": 2, "split_bf16_refined": 3, "split_fp16_refined": 4}
 ABI_VERSION = 2  # GP_ABI_VERSION of include/gprox.h that these signatures follow
 
 EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_last_error", "dct2_poisson",
@@ -28,7 +28,8 @@ EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_l
            "gp_cnn_create", "gp_cnn_destroy", "gp_cnn_last_error", "gp_cnn_num_params", "gp_cnn_get_params",
            "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned",
            "emd_coarse_start", "gp_gap_schedule_next", "gp_rof_image_stats", "gp_state_average",
-           "gp_state_read_average", "rof_solve_cp2", "rof_solve3d", "emd_solve3d", "gp_state_certify"]
+           "gp_state_read_average", "rof_solve_cp2", "rof_solve3d", "emd_solve3d", "gp_state_certify",
+           "rof_coarse_start", "rof_solve_learned"]
 
 
 class Opts(C.Structure):
@@ -106,6 +107,9 @@ def lib():
     L.emd_solve_learned.argtypes = [vp, vp, vp, vp, vp, vp, vp, i, i, C.POINTER(Opts), C.POINTER(Opts),
                                     C.POINTER(Report), C.POINTER(i), vp]
     L.emd_coarse_start.argtypes = [vp, vp, vp, i, i, C.POINTER(Opts), vp, C.POINTER(Report), vp]
+    L.rof_coarse_start.argtypes = [vp, vp, i, i, d, C.POINTER(Opts), vp, vp, C.POINTER(Report), vp]
+    L.rof_solve_learned.argtypes = [vp, vp, vp, vp, vp, i, d, i, C.POINTER(Opts), C.POINTER(Opts),
+                                    C.POINTER(Report), C.POINTER(i), vp]
     L.gp_gap_schedule_next.argtypes = [i, d, i, d, d]
     L.gp_state_average.argtypes = [vp, vp, i, vp]
     L.gp_state_read_average.argtypes = [vp, vp, vp, vp, C.POINTER(C.c_longlong), vp]
@@ -552,6 +556,42 @@ def emd_solve_learned(h: Handle, net: Cnn, f0, f1, m, p=None, phi=None, opts: Op
     d = rep.as_dict()
     d["start"] = ("zero", "learned", "prior")[used.value]
     return st, d
+
+
+def rof_solve_learned(h: Handle, net: Cnn, I, u, p=None, lam: float = 8.0, opts: Opts | None = None,
+                      coarse_factor: int = 4, coarse_opts: Opts | None = None, stream=None):
+    """ROF solve from the best (by the gap at n = 0) of the learned, prior and zero
+    starts; returns (status, report dict with 'start': 'zero' | 'learned' | 'prior')."""
+    N = _side(I, "I")
+    _shape(u, (N, N), "u")
+    _shape(p, (2, N, N), "p")
+    rep = Report()
+    used = C.c_int(0)
+    st = lib().rof_solve_learned(h.ptr, net._n, _ptr(I), _ptr(u), _ptr(p), N, float(lam), int(coarse_factor),
+                                 C.byref(coarse_opts) if coarse_opts is not None else None,
+                                 C.byref(opts) if opts is not None else None, C.byref(rep), C.byref(used),
+                                 _stream(stream))
+    d = rep.as_dict()
+    d["start"] = ("zero", "learned", "prior")[used.value]
+    return st, d
+
+
+def rof_coarse_start(h: Handle, I, factor: int, lam: float = 8.0, opts: Opts | None = None, u=None, p=None,
+                     stream=None):
+    """ROF (u, p) solved on an N/factor grid, interpolated to N x N (p made
+    feasible); returns (status, u, p, coarse report dict)."""
+    N = _side(I, "I")
+    _shape(u, (N, N), "u")
+    _shape(p, (2, N, N), "p")
+    if u is None:
+        u = torch.empty((N, N), device=I.device, dtype=torch.float32)
+    if p is None:
+        p = torch.empty((2, N, N), device=I.device, dtype=torch.float32)
+    rep = Report()
+    st = lib().rof_coarse_start(h.ptr, _ptr(I), N, int(factor), float(lam),
+                                C.byref(opts) if opts is not None else None, _ptr(u), _ptr(p), C.byref(rep),
+                                _stream(stream))
+    return st, u, p, rep.as_dict()
 
 
 def emd_coarse_start(h: Handle, f0, f1, factor: int, opts: Opts | None = None, phi=None, stream=None):

@@ -1,4 +1,5 @@
-"""Training and evaluation driver of the learned EMD warm start.
+"""Training and evaluation driver of the learned warm starts (EMD, and ROF
+with ``--problem rof``).
 
 Every step runs in the library: the training targets come from the library's
 own EMD solve (the converged dual potential phi* = Lap^{-1} div p*), the
@@ -13,7 +14,12 @@ with the smallest duality gap at n = 0 among learned, prior and zero).
         --steps 2000 --out warm.npz --report warm.json
 
 Inputs are seeded Gaussian-mixture density pairs (``synth.gaussian_mixture_pair``);
-training seeds are 0.., held-out seeds start at 1_000_000.
+training seeds are 0.., held-out seeds start at 1_000_000.  ``--problem rof``
+trains the same network on ROF images (``synth.rof_image``, fidelity weight
+``--lam``) against u* - mean(I) and evaluates ``rof_solve_learned``:
+
+    python -m paper_1805_09453_gb300.learn --problem rof --N 512 --train 256 --test 32 \
+        --steps 1500 --report rof_warm.json
 """
 from __future__ import annotations
 
@@ -78,6 +84,83 @@ def _generate(h, N, f0, f1, phi, prior, tol, max_iters, gap_every, coarse_factor
             print(f"generated {i + 1}/{len(seeds)} pairs (median iterations {statistics.median(iters)})", flush=True)
     torch.cuda.synchronize()
     return f0, f1, phi, prior, iters, gaps
+
+
+# --------------------------------------------------------------------- ROF
+# The same network proposes the ROF primal iterate (rof_solve_learned): the
+# inputs are a = 8 (I - mean), b = -a (channels I - mean and 0), the prior
+# u_prior - mean, and the target u* - mean (a fidelity minimiser keeps the
+# mean).  Swapping a and b negates I, and the ROF minimiser is odd in I, so
+# the symmetries of `augment` hold for these samples too.
+
+def images(N: int, seeds, device="cuda"):
+    """ROF images (S, N, N) on the device (``synth.rof_image``)."""
+    out = torch.empty((len(seeds), N, N), device=device)
+    for i, s in enumerate(seeds):
+        out[i].copy_(torch.from_numpy(synth.rof_image(N, int(s))))
+    return out
+
+
+def generate_rof(h: gprox.Handle, N: int, seeds, lam: float = 8.0, tol: float = 1e-6, max_iters: int = 20000,
+                 gap_every: int = 10, coarse_factor: int = 4, coarse_tol: float = 1e-4):
+    """Solve each image with the plain method; returns the network's inputs
+    (a, b), targets u* - mean, priors u_prior - mean (S, N, N), the images,
+    the iteration counts and the gaps."""
+    I = images(N, seeds)
+    tgt = torch.empty_like(I)
+    prior = torch.zeros_like(I)
+    u = torch.empty((N, N), device=I.device)
+    o = gprox.default_opts(max_iters=max_iters, tol_rel_gap=tol, gap_every=gap_every, use_graph=1)
+    oc = coarse_opts(coarse_tol)
+    iters, gaps = [], []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(torch.cuda.Stream()):
+        for i in range(I.shape[0]):
+            st, rep = gprox.rof_solve(h, I[i], u, None, lam, o)
+            h.check(st, allow=(gprox.GP_OK, gprox.GP_ERR_MAXITER))
+            iters.append(rep["iters"])
+            gaps.append(rep["rel_gap"])
+            mean = I[i].double().mean().float()
+            tgt[i].copy_(u - mean)
+            if coarse_factor:
+                st, uc, _, _ = gprox.rof_coarse_start(h, I[i], coarse_factor, lam, oc)
+                h.check(st, allow=(gprox.GP_OK, gprox.GP_ERR_MAXITER))
+                prior[i].copy_(uc - mean)
+    torch.cuda.synchronize()
+    c = I - I.double().mean(dim=(1, 2), keepdim=True).float()
+    return 8.0 * c, -8.0 * c, tgt, prior, I, iters, gaps
+
+
+def evaluate_rof(h: gprox.Handle, net: gprox.Cnn, I, lam: float = 8.0, tol: float = 1e-5, max_iters: int = 20000,
+                 gap_every: int = 10, coarse_factor: int = 4, coarse_tol: float = 1e-4):
+    """Per image: iterations, seconds, status and primal to `tol` from zero, from
+    the prior alone and from the learned start (rof_solve_learned)."""
+    N = I.shape[-1]
+    u = torch.empty((N, N), device=I.device)
+    o = gprox.default_opts(max_iters=max_iters, tol_rel_gap=tol, gap_every=gap_every, use_graph=1)
+    oc = coarse_opts(coarse_tol)
+    base = gprox.Cnn(h, 1, seed=0)
+    base.set_params(np.zeros(base.num_params, np.float32))  # output = prior
+    name = gprox.STATUS_NAMES
+    rows = []
+    torch.cuda.synchronize()
+    with torch.cuda.stream(torch.cuda.Stream()):
+        for i in range(I.shape[0]):
+            (st, rz), tz = _timed(lambda: gprox.rof_solve(h, I[i], u, None, lam, o))
+            row = {"zero_iters": rz["iters"], "zero_s": tz, "zero_gap": rz["rel_gap"], "zero_status": name[st],
+                   "zero_primal": rz["primal"]}
+            if coarse_factor:
+                (st, rp), tp = _timed(lambda: gprox.rof_solve_learned(h, base, I[i], u, None, lam, o,
+                                                                       coarse_factor, oc))
+                row.update(prior_iters=rp["iters"], prior_s=tp, prior_gap=rp["rel_gap"], prior_status=name[st],
+                           prior_start=rp["start"], prior_primal=rp["primal"])
+            (st, rw), tw = _timed(lambda: gprox.rof_solve_learned(h, net, I[i], u, None, lam, o, coarse_factor, oc))
+            row.update(warm_iters=rw["iters"], warm_s=tw, warm_gap=rw["rel_gap"], warm_status=name[st],
+                       warm_start=rw["start"], warm_primal=rw["primal"])
+            rows.append(row)
+    torch.cuda.synchronize()
+    base.close()
+    return rows
 
 
 def augment(f0, f1, phi, prior, g: int):
@@ -206,6 +289,8 @@ def summarize(rows):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--problem", default="emd", choices=["emd", "rof"])
+    ap.add_argument("--lam", type=float, default=8.0, help="ROF fidelity weight")
     ap.add_argument("--N", type=int, default=512)
     ap.add_argument("--C", type=int, default=32)
     ap.add_argument("--fp32", action="store_true", help="FP32 storage instead of BF16")
@@ -233,7 +318,9 @@ def main(argv=None):
     net = gprox.Cnn(h, a.C, bf16=not a.fp32, seed=a.seed)
     if a.init:
         net.set_params(np.load(a.init)["w"])
-    rep = {"N": a.N, "C": a.C, "bf16": not a.fp32, "params": net.num_params}
+    rep = {"N": a.N, "C": a.C, "bf16": not a.fp32, "params": net.num_params, "problem": a.problem}
+    if a.problem == "rof":
+        return _main_rof(a, h, net, rep)
     t0 = time.perf_counter()
     f0, f1, phi, pri, it, gaps = generate(h, a.N, range(a.train), a.data_tol, a.data_max_iters,
                                           coarse_factor=a.coarse, coarse_tol=a.coarse_tol, verbose=True)
@@ -266,6 +353,34 @@ def main(argv=None):
         with open(a.report, "w") as f:
             json.dump(rep, f, indent=1)
     print(json.dumps({k: v for k, v in rep.items() if k not in ("rows", "eval_large")}, default=str))
+    return rep
+
+
+def _main_rof(a, h, net, rep):
+    t0 = time.perf_counter()
+    f0, f1, tgt, pri, _, it, gaps = generate_rof(h, a.N, range(a.train), a.lam, a.data_tol,
+                                                  coarse_factor=a.coarse, coarse_tol=a.coarse_tol)
+    rep["data"] = {"images": a.train, "lambda": a.lam, "seconds": time.perf_counter() - t0,
+                   "median_iters": statistics.median(it), "max_gap": max(gaps)}
+    g0, g1, gt, gp, gI, _, _ = generate_rof(h, a.N, range(TEST_SEED0, TEST_SEED0 + a.test), a.lam, a.data_tol,
+                                            coarse_factor=a.coarse, coarse_tol=a.coarse_tol)
+    rep["test_loss_init"] = test_loss(net, g0, g1, gt, gp)
+    t0 = time.perf_counter()
+    hist = train(net, f0, f1, tgt, pri, a.steps, a.batch, a.lr, a.seed)
+    rep["train"] = {"steps": a.steps, "batch": a.batch, "lr": a.lr, "seconds": time.perf_counter() - t0,
+                    "loss": hist[-1][1], "history": hist}
+    rep["test_loss"] = test_loss(net, g0, g1, gt, gp)
+    rep["network_seconds"] = network_cost(net, g0, g1, gp)
+    if a.out:
+        np.savez(a.out, w=net.get_params(), C=a.C, N=a.N, coarse=a.coarse, problem="rof", lam=a.lam)
+    rows = evaluate_rof(h, net, gI, a.lam, a.tol, coarse_factor=a.coarse, coarse_tol=a.coarse_tol)
+    rep["eval"] = summarize(rows)
+    rep["eval"]["tol"] = a.tol
+    rep["rows"] = rows
+    if a.report:
+        with open(a.report, "w") as f:
+            json.dump(rep, f, indent=1)
+    print(json.dumps({k: v for k, v in rep.items() if k != "rows"}, default=str))
     return rep
 
 

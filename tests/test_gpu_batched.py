@@ -82,3 +82,38 @@ def test_batched_equals_individual_solves():
     # problems stop independently: not all at the same iteration count
     assert len({r["iters"] for r in reps}) > 1
     h.close()
+
+
+def test_batched_split_bf16_equals_individual_and_oracle():
+    """The batched solve with the split-precision (BF16 tensor-core) transform:
+    each problem equals its one-at-a-time solve bit for bit (the branches
+    share no scratch) and sits within the split mode's bars of the FP64
+    oracle after a fixed number of iterations (m 1e-3 relative L2, P 1e-4)."""
+    from paper_1805_09453_gb300 import build, gprox
+
+    build.build()
+    h = gprox.Handle(0)
+    sizes, iters = [128, 256, 128], 60
+    pairs = [synth.gaussian_mixture_pair(N, 300 + b) for b, N in enumerate(sizes)]
+    f0s = [torch.from_numpy(a).cuda() for a, _ in pairs]
+    f1s = [torch.from_numpy(b).cuda() for _, b in pairs]
+    ms = [torch.empty((2, N, N), device="cuda") for N in sizes]
+    opts = gprox.default_opts(max_iters=iters, tol_rel_gap=0.0, gap_every=20, prec="split_bf16")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        st, reps = gprox.emd_solve_batched(h, f0s, f1s, ms, opts)
+        stream.synchronize()
+        h.check(st)
+        for b, N in enumerate(sizes):
+            m1 = torch.empty((2, N, N), device="cuda")
+            h.check(gprox.emd_solve(h, f0s[b], f1s[b], m1, None, opts=opts)[0])
+            stream.synchronize()
+            assert torch.equal(ms[b], m1)
+            ref = O.emd_solve(pairs[b][0], pairs[b][1], n_iters=iters)
+            assert rel_l2(ms[b].cpu().numpy(), np.stack([ref["mx"], ref["my"]])) < 1e-3
+            assert abs(reps[b]["primal"] - ref["primal"]) < 1e-4 * ref["primal"]
+    o16 = gprox.default_opts(max_iters=10, tol_rel_gap=0.0, prec="split_fp16")
+    with torch.cuda.stream(stream):
+        st, _ = gprox.emd_solve_batched(h, f0s, f1s, ms, o16)
+    assert st == gprox.GP_ERR_UNSUPPORTED
+    h.close()
