@@ -1447,7 +1447,8 @@ __global__ void k_dct3_lines(const float* in, float* out, int axis,
   constexpr int N = C::N, PADN = C::PADN, TPF = C::TPF;
   constexpr int NF = MODE == 2 ? kLines3 : kLines3 / 2;  // FFTs per CTA
   extern __shared__ float2 sm3[];
-  float* stg = reinterpret_cast<float*>(sm3 + NF * PADN);  // [line][n]
+  float* stg = reinterpret_cast<float*>(sm3 + NF * PADN);  // [line][n], row stride SN
+  constexpr int SN = N + 1;  // odd stride: the 16 lines of a y / z column fall into 16 banks
   const int f = (int)threadIdx.x / TPF, t = (int)threadIdx.x % TPF;
   const int nthr = (int)blockDim.x;
   const size_t NN = (size_t)N * N;
@@ -1461,19 +1462,19 @@ __global__ void k_dct3_lines(const float* in, float* out, int axis,
     if (axis == 0) { l = e / N; n = e % N; }
     else { l = e % kLines3; n = e / kLines3; }
     const size_t g = axis == 0 ? base + (size_t)l * N + n : base + (size_t)l + (size_t)n * stride;
-    stg[l * N + n] = in[g];
+    stg[l * SN + n] = in[g];
   }
   __syncthreads();
   float2* buf = sm3 + f * PADN;
   const float fN = (float)N;
   if (MODE == 0) {
-    const float* xa = stg + (2 * f) * N;
-    const float* xb = xa + N;
+    const float* xa = stg + (2 * f) * SN;
+    const float* xb = xa + SN;
     for (int n = t; n < N; n += TPF) buf[padi(mk_pos(n, N))] = make_float2(xa[n], xb[n]);
   } else {
     // pre-step from the line spectra (MODE 1: lines 2f, 2f+1; MODE 2: line f)
-    const float* xa = stg + (MODE == 1 ? 2 * f : f) * N;
-    const float* xb = xa + N;
+    const float* xa = stg + (MODE == 1 ? 2 * f : f) * SN;
+    const float* xb = xa + SN;
     for (int k = t; k <= N / 2; k += TPF) {
       if (MODE == 1) {
         if (k == 0) buf[0] = make_float2(xa[0], xb[0]);
@@ -1501,8 +1502,8 @@ __global__ void k_dct3_lines(const float* in, float* out, int axis,
   else fft_smem<LOG2N, +1, TPF>(buf, t, tw, 0);
   // results back into the staging lines (each FFT group writes only its own lines)
   if (MODE == 0) {
-    float* xa = stg + (2 * f) * N;
-    float* xb = xa + N;
+    float* xa = stg + (2 * f) * SN;
+    float* xb = xa + SN;
     for (int k = t; k <= N / 2; k += TPF) {
       if (k == 0 || k == N / 2) {
         const float sc = k == 0 ? 1.f : kRsqrt2;
@@ -1519,15 +1520,15 @@ __global__ void k_dct3_lines(const float* in, float* out, int axis,
       }
     }
   } else if (MODE == 1) {
-    float* xa = stg + (2 * f) * N;
-    float* xb = xa + N;
+    float* xa = stg + (2 * f) * SN;
+    float* xb = xa + SN;
     for (int n = t; n < N; n += TPF) {
       const float2 z = buf[padi(mk_pos(n, N))];
       xa[n] = z.x;
       xb[n] = z.y;
     }
   } else {
-    float* xa = stg + f * N;
+    float* xa = stg + f * SN;
     for (int n = t; n < N; n += TPF) {
       const float2 z = buf[padi(mk_pos(n, N))];
       xa[n] = n == N - 1 ? 0.f : fN * (z.x - ((n & 1) ? -z.y : z.y));
@@ -1539,7 +1540,7 @@ __global__ void k_dct3_lines(const float* in, float* out, int axis,
     if (axis == 0) { l = e / N; n = e % N; }
     else { l = e % kLines3; n = e / kLines3; }
     const size_t g = axis == 0 ? base + (size_t)l * N + n : base + (size_t)l + (size_t)n * stride;
-    out[g] = stg[l * N + n];
+    out[g] = stg[l * SN + n];
   }
 }
 
@@ -1559,7 +1560,7 @@ cudaError_t launch_dct3_lines(const DctPlan& p, const float* in, float* out, int
   using C = FftCfg<LOG2N>;
   constexpr int N = C::N;
   const int nf = mode == 2 ? kLines3 : kLines3 / 2;
-  const size_t sm = (size_t)nf * C::PADN * sizeof(float2) + (size_t)kLines3 * N * sizeof(float);
+  const size_t sm = (size_t)nf * C::PADN * sizeof(float2) + (size_t)kLines3 * (N + 1) * sizeof(float);
   const int grid = N * N / kLines3, thr = nf * C::TPF;
   cudaError_t e;
   if (mode == 0) {
