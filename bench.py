@@ -710,7 +710,7 @@ def main():
     ap.add_argument("--no-prec", action="store_true")
     ap.add_argument("--no-cp2", action="store_true")
     ap.add_argument("--cp2-iters", type=int, default=20000)
-    ap.add_argument("--ttg-cap", type=int, default=100000)
+    ap.add_argument("--ttg-cap", type=int, default=200000)
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--size3", type=int, default=256)
     ap.add_argument("--ttg3-cap", type=int, default=5000, help="iteration cap of the 3-D runs to a gap")
