@@ -60,7 +60,7 @@ typedef enum gp_status {
   GP_ERR_NONFINITE = 4,   /* NaN / Inf met in an objective or gap reduction */
   GP_ERR_DIVERGED = 5,    /* relative gap grew 10x over 5 consecutive checks */
   GP_ERR_MASS = 6,        /* EMD densities differ in total mass by more than 1e-3 relative */
-  GP_ERR_UNSUPPORTED = 7  /* option not available in this build (e.g. a precision mode) */
+  GP_ERR_UNSUPPORTED = 7  /* option not available for these arguments (e.g. a precision mode at this N) */
 } gp_status;
 
 /* Arithmetic of the cosine-transform (Helmholtz / Poisson) solve. */

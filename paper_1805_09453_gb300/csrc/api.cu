@@ -312,7 +312,7 @@ gp_status solve(gp_handle h, int N, const float* b, float* x, float* tmp, double
     }
     return GP_OK;
   }
-  if (prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available in this build");
+  if (prec != GP_PREC_FP32) return fail(h, GP_ERR_UNSUPPORTED, "precision mode not available for this size");
   if (p->fft && allow_fast) {
     GP_CUDA(h, plaunch(h, PK_DCT_ROWS_FWD, st, [&] { return dct_fft_pass(*p, 0, b, tmp, a, sc, st); }));
     GP_CUDA(h, plaunch(h, PK_DCT_COLS, st, [&] { return dct_fft_pass(*p, 1, tmp, tmp, a, sc, st); }));

@@ -530,6 +530,17 @@ void free_bufs(gp_cnn n) {
   n->cap_B = n->cap_N = 0;
 }
 
+// The tensor-core convolutions' timeout flag (BF16 mode): read (synchronising
+// the stream) and cleared; a wait that timed out fails the call.
+gp_status tc_flag(gp_cnn n, cudaStream_t st) {
+  int f = 0;
+  CN_CUDA(n, cudaMemcpyAsync(&f, n->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CN_CUDA(n, cudaStreamSynchronize(st));
+  if (!f) return GP_OK;
+  CN_CUDA(n, cudaMemsetAsync(n->tc_err, 0, sizeof(int), st));
+  return cfail(n, GP_ERR_CUDA, "tensor-core convolution: a wait timed out");
+}
+
 // Activation, gradient and scratch buffers for batches of up to B samples of side N.
 gp_status reserve(gp_cnn n, int B, int N) {
   if (n->cap_N == N && n->cap_B >= B) return GP_OK;
@@ -621,8 +632,13 @@ struct Net {
     const int t = (side(l) + TS - 1) / TS, tiles = t * t;
     const int cg = (c.cout + WG_CO - 1) / WG_CO, kg = (c.cin + WG_CI - 1) / WG_CI;
     const int gx = std::max(1, std::min(tiles, (4 * 152 + cg * kg - 1) / (cg * kg)));
-    k_conv3x3_wgrad<T><<<dim3(gx, cg, kg), 256, 0, st>>>(dy, dybs, c.cout, ptr(xa, xch0), bs(xa), c.cin, side(l),
-                                                        side(l), B, n->g + c.woff, n->g + c.boff);
+    if constexpr (sizeof(T) == 2) {  // BF16 mode: weight gradient on the tensor cores
+      gp::conv3x3_wgrad_tc(dy, dybs, c.cout, ptr(xa, xch0), bs(xa), c.cin, side(l), side(l), B, n->g + c.woff,
+                           n->g + c.boff, n->tc_err, st);
+    } else {
+      k_conv3x3_wgrad<T><<<dim3(gx, cg, kg), 256, 0, st>>>(dy, dybs, c.cout, ptr(xa, xch0), bs(xa), c.cin, side(l),
+                                                          side(l), B, n->g + c.woff, n->g + c.boff);
+    }
     if (dx)
       k_conv3x3<float, T, float, false, true><<<cgrid(l, c.cin), TS * TS, 0, st>>>(dy, dybs, c.cout, W(i), nullptr, dx,
                                                                                   bs(xa), c.cin, side(l), side(l));
@@ -877,6 +893,7 @@ GP_API gp_status gp_cnn_loss_grad(gp_cnn n, int B, const float* const* f0, const
     CN_CUDA(n, cudaMemcpyAsync(grad, n->g, (size_t)n->nparam * 4, cudaMemcpyDeviceToHost, st));
     CN_CUDA(n, cudaStreamSynchronize(st));
   }
+  if ((loss || grad) && n->bf16) return tc_flag(n, st);
   return GP_OK;
 }
 
@@ -963,6 +980,10 @@ GP_API gp_status emd_solve_learned(gp_handle h, gp_cnn n, const float* f0, const
   if (r != GP_OK && !(r == GP_ERR_MAXITER || r == GP_ERR_DIVERGED || r == GP_ERR_NONFINITE))
     return cfail(n, r, gp_last_error(h));
   if (r != GP_OK) n->err = gp_last_error(h);
+  if (n->bf16) {
+    const gp_status q = tc_flag(n, st);
+    if (q != GP_OK) return q;
+  }
   rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (report) *report = rep;
   if (start_used) *start_used = choice;
@@ -1068,6 +1089,10 @@ GP_API gp_status rof_solve_learned(gp_handle h, gp_cnn n, const float* I, float*
     return cfail(n, r, gp_last_error(h));
   if (r != GP_OK) n->err = gp_last_error(h);
   CN_CUDA(n, cudaStreamSynchronize(st));
+  if (n->bf16) {
+    const gp_status q = tc_flag(n, st);
+    if (q != GP_OK) return q;
+  }
   rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (report) *report = rep;
   if (start_used) *start_used = choice;

@@ -1261,7 +1261,7 @@ cudaError_t set_smem(K k, size_t bytes) {
 }
 
 // Tensor map of an interleaved-spectra plane as {4 rows, N columns, N/4 row
-// blocks}, box {4, ncols, min(256, N/4)}; false when the driver's encoder is
+// blocks}, box {4, ncols, min(256, N/4)}; false when the CUDA driver's encoder is
 // unavailable or refuses.
 template <int LOG2N>
 cudaError_t launch_fft_pass(const DctPlan& p, int pass, const float* in, float* out, float alpha, float scale,

@@ -128,6 +128,10 @@ bool tc_solve_supported(int N);
 // set to 1 if a wait timed out.
 cudaError_t conv3x3_tc(const void* X, long xbs, int Cin, const void* W, const float* bias, void* Y, long ybs, int Cout,
                        int H, int Wd, int B, bool relu, bool y_fp32, int* err, cudaStream_t st);
+// Its weight and bias gradients (accumulated into dW [Cout][Cin][3][3] and db):
+// dY FP32 as a hi + lo BF16 pair, X BF16.
+cudaError_t conv3x3_wgrad_tc(const float* dY, long dybs, int Cout, const void* X, long xbs, int Cin, int H, int Wd,
+                             int B, float* dW, float* db, int* err, cudaStream_t st);
 cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
                          cudaStream_t st, bool fp16);
 // Gradient of the split-precision solve, taken in the spectral domain with

@@ -80,7 +80,7 @@ def test_inputs_of_the_experiments():
 
 
 def test_paper_tables_match_the_cited_fixture():
-    """The driver's copy of the paper's section-4 iteration counts equals the
+    """The experiments module's copy of the paper's section-4 iteration counts equals the
     cited fixture tests/golden/section4_iterations.json."""
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "section4_iterations.json")))
     assert set(g["tables"]) == set(PE.PAPER_TABLES)
