@@ -639,9 +639,14 @@ struct Net {
       k_conv3x3_wgrad<T><<<dim3(gx, cg, kg), 256, 0, st>>>(dy, dybs, c.cout, ptr(xa, xch0), bs(xa), c.cin, side(l),
                                                           side(l), B, n->g + c.woff, n->g + c.boff);
     }
-    if (dx)
-      k_conv3x3<float, T, float, false, true><<<cgrid(l, c.cin), TS * TS, 0, st>>>(dy, dybs, c.cout, W(i), nullptr, dx,
-                                                                                  bs(xa), c.cin, side(l), side(l));
+    if (dx) {
+      if constexpr (sizeof(T) == 2) {  // BF16 mode: data gradient on the tensor cores
+        gp::conv3x3_dgrad_tc(dy, dybs, c.cout, W(i), dx, bs(xa), c.cin, side(l), side(l), B, n->tc_err, st);
+      } else {
+        k_conv3x3<float, T, float, false, true><<<cgrid(l, c.cin), TS * TS, 0, st>>>(dy, dybs, c.cout, W(i), nullptr,
+                                                                                    dx, bs(xa), c.cin, side(l), side(l));
+      }
+    }
   }
   void relu_bwd(int a, long ch0, long C) const {
     k_relu_bwd<T><<<g1d((long)B * C * plane(d.lev[a])), 256, 0, st>>>(gptr(a, ch0), bs(a), ptr(a, ch0), bs(a),

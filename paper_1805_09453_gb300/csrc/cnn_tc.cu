@@ -1,5 +1,5 @@
 // 3x3 convolution of the warm-start network on the 5th-generation tensor
-// cores (BF16 storage mode): the forward pass and the weight gradient.
+// cores (BF16 storage mode): forward pass, weight gradient and data gradient.
 //
 // Implicit GEMM: Y[co][p] = act(bias[co] + sum_k W[co][k] X_col[p][k]) with
 // k = ci * 9 + t over the Cin x 3 x 3 receptive field (t = 3 (dy + 1) +
@@ -215,6 +215,150 @@ cudaError_t launch(const __nv_bfloat16* X, long xbs, int Cin, const __nv_bfloat1
   return cudaGetLastError();
 }
 
+// Data gradient on the tensor cores: the adjoint of the convolution is the
+// convolution with the transposed, flipped kernel,
+//   dX[ci][q] = sum_co sum_t W[co][ci][8 - t] dY[co][q + o_t],
+// so D = A B^T with A = dY_col (M = 128 pixels, k = co * 9 + t) and
+// B[ci][k] = W[co][ci][8 - t] (N = up to 256 input channels per CTA,
+// blockIdx.z tiles the rest).  dY is FP32 and enters as a hi + lo BF16 pair
+// (two MMAs per step); dX is written (not accumulated), FP32.
+__global__ void __launch_bounds__(CTHREADS) k_conv3x3_dgrad_tc(const float* __restrict__ dY, long dybs, int Cout,
+                                                               const __nv_bfloat16* __restrict__ W,
+                                                               float* __restrict__ dX, long dxbs, int Cin, int NP,
+                                                               int tcols, int H, int Wd, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* Ah = smem;                // 128 x 64 bf16
+  uint8_t* Al = smem + A_BYTES;      // 128 x 64 bf16
+  uint8_t* Bs = smem + 2 * A_BYTES;  // NP x 64 bf16
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Bs + (size_t)NP * CK * 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long plane = (long)H * Wd;
+  const long m0 = (long)blockIdx.x * CM;
+  const int b = blockIdx.y, ci0 = blockIdx.z * 256;
+  const float* dYb = dY + (long)b * dybs;
+  const int K = Cout * 9;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"((uint32_t)tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tslot;
+  const uint32_t id = idesc_bf16(NP);
+  const long pm = m0 + threadIdx.x;
+  const bool pin = pm < plane;
+  const int py = pin ? (int)(pm / Wd) : 0, px = pin ? (int)(pm % Wd) : 0;
+  bool ok = true;
+  uint32_t phase = 0;
+  const int nslab = (K + CK - 1) / CK;
+  for (int ks = 0; ks < nslab; ++ks) {
+    const int k0 = ks * CK;
+    for (int kk = 0; kk < CK; kk += 8) {
+      __align__(16) __nv_bfloat16 hi[8], lo[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + kk + e;
+        float v = 0.f;
+        if (pin && k < K) {
+          const int co = k / 9, t = k - 9 * co;
+          const int yy = py + t / 3 - 1, xx = px + t % 3 - 1;
+          if (yy >= 0 && yy < H && xx >= 0 && xx < Wd) v = dYb[(long)co * plane + (long)yy * Wd + xx];
+        }
+        hi[e] = __float2bfloat16(v);
+        lo[e] = __float2bfloat16(v - __bfloat162float(hi[e]));
+      }
+      *reinterpret_cast<uint4*>(Ah + kmaj(threadIdx.x, kk)) = *reinterpret_cast<const uint4*>(hi);
+      *reinterpret_cast<uint4*>(Al + kmaj(threadIdx.x, kk)) = *reinterpret_cast<const uint4*>(lo);
+    }
+    for (int r = threadIdx.x; r < NP * (CK / 8); r += CTHREADS) {
+      const int row = r / (CK / 8), kk = (r % (CK / 8)) * 8;
+      const int ci = ci0 + row;
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + kk + e;
+        __nv_bfloat16 w = __float2bfloat16(0.f);
+        if (ci < Cin && k < K) {
+          const int co = k / 9, t = k - 9 * co;
+          w = W[((long)co * Cin + ci) * 9 + (8 - t)];
+        }
+        v[e] = w;
+      }
+      *reinterpret_cast<uint4*>(Bs + kmaj(row, kk)) = *reinterpret_cast<const uint4*>(v);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int j = 0; j < CK / 16; ++j) {
+        const uint32_t off = (uint32_t)j * 256;
+        const uint64_t bd = sdesc(su32(Bs) + off);
+        const uint32_t acc0 = (ks > 0 || j > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(sdesc(su32(Ah) + off)), "l"(bd), "r"(id), "r"(acc0));
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+            "l"(sdesc(su32(Al) + off)), "l"(bd), "r"(id), "r"(1u));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+                   : "memory");
+    }
+    if (threadIdx.x == 0 && !wait_bar(su32(bar), phase)) {
+      ok = false;
+      wait_bar(su32(bar), phase);  // once more (bounded) before the memory is released
+    }
+    phase ^= 1u;
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+  }
+  if (!ok) {
+    if (threadIdx.x == 0) atomicExch(err, 1);
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const long p = m0 + warp * 32 + lane;
+    float* dXb = dX + (long)b * dxbs;
+    for (int c0 = 0; c0 < NP; c0 += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (p < plane) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int ci = ci0 + c0 + c;
+          if (ci < Cin) dXb[(long)ci * plane + p] = __uint_as_float(r[c]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)tcols));
+  }
+}
+
 // Weight and bias gradients on the tensor cores:
 //   dW[co][k] += sum_q dY[co][q] X_col[k][q],  db[co] += sum_q dY[co][q],
 // q over the pixels of one sample's chunk (blockIdx.z = sample * chunks +
@@ -402,6 +546,26 @@ cudaError_t conv3x3_wgrad_tc(const float* dY, long dybs, int Cout, const void* X
   cudaError_t e = cudaFuncSetAttribute(k_conv3x3_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   k_conv3x3_wgrad_tc<<<grid, CTHREADS, sm, st>>>(dY, dybs, Cout, x, xbs, Cin, H, Wd, chunks, NT, tcols, dW, db, err);
+  return cudaGetLastError();
+}
+
+}  // namespace gp
+
+namespace gp {
+
+cudaError_t conv3x3_dgrad_tc(const float* dY, long dybs, int Cout, const void* W, float* dX, long dxbs, int Cin,
+                             int H, int Wd, int B, int* err, cudaStream_t st) {
+  const int ntile = Cin < 256 ? Cin : 256;
+  const int NP = (ntile + 15) / 16 * 16;
+  int tcols = 32;
+  while (tcols < NP) tcols *= 2;
+  const size_t sm = (size_t)2 * A_BYTES + (size_t)NP * CK * 2 + 64;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3x3_dgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  const long plane = (long)H * Wd;
+  dim3 grid((unsigned)((plane + CM - 1) / CM), (unsigned)B, (unsigned)((Cin + 255) / 256));
+  k_conv3x3_dgrad_tc<<<grid, CTHREADS, sm, st>>>(dY, dybs, Cout, static_cast<const __nv_bfloat16*>(W), dX, dxbs, Cin,
+                                                 NP, tcols, H, Wd, err);
   return cudaGetLastError();
 }
 

@@ -132,6 +132,10 @@ cudaError_t conv3x3_tc(const void* X, long xbs, int Cin, const void* W, const fl
 // dY FP32 as a hi + lo BF16 pair, X BF16.
 cudaError_t conv3x3_wgrad_tc(const float* dY, long dybs, int Cout, const void* X, long xbs, int Cin, int H, int Wd,
                              int B, float* dW, float* db, int* err, cudaStream_t st);
+// Its data gradient dX (written, FP32) from dY (FP32, hi + lo BF16) and the
+// flipped, transposed BF16 weights.
+cudaError_t conv3x3_dgrad_tc(const float* dY, long dybs, int Cout, const void* W, float* dX, long dxbs, int Cin,
+                             int H, int Wd, int B, int* err, cudaStream_t st);
 cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
                          cudaStream_t st, bool fp16);
 // Gradient of the split-precision solve, taken in the spectral domain with

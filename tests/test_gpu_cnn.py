@@ -5,10 +5,10 @@ Tolerances.  FP32 mode: the kernels accumulate in FP32 (unit roundoff 6e-8)
 over at most 12C * 9 terms per output and through 15 layers; a relative L2
 error of 1e-5 on phi and 1e-4 on the parameter gradient (whose wgrad sums run
 over B * N^2 terms with atomics) leaves an order of magnitude of headroom.
-The BF16 mode stores weights and activations in BF16 and runs the forward
-convolutions and the weight gradient as tcgen05 implicit GEMMs (FP32
-accumulation in tensor memory; dY enters the weight gradient as a hi + lo
-BF16 pair), the data gradient on the CUDA cores.  There an
+The BF16 mode stores weights and activations in BF16 and runs every
+convolution product (forward, weight and data gradients) as a tcgen05
+implicit GEMM (FP32 accumulation in tensor memory; the FP32 gradient dY
+enters as a hi + lo BF16 pair).  There an
 element-wise bar does not exist: a BF16 rounding decision flips under an
 FP32-vs-FP64 accumulation difference, and the random network's mean-free
 output is a small difference of large terms, so each flip is amplified (in
