@@ -424,6 +424,26 @@ GP_API gp_status gp_rof_image_stats(gp_handle h, const float* I, int N, double* 
 GP_API int gp_gap_schedule_next(int n_prev, double g_prev, int n, double g, double tol);
 
 /*
+ * Step rules of the paper's experiments, host only (no GPU work).
+ * gp_rof_step_tau: section 4.1's ROF rule from the image norms of
+ * gp_rof_image_stats (stats[0] = ||I||_TV, stats[1] = ||grad I||_L2,
+ * stats[2] = ||I - mean I||^2_L2):
+ *   tau = sqrt(lambda) T / sqrt(eps),  T = ||I||_TV, or, with
+ *   GP_RULE_FIDELITY_BOUND, T = min(||I||_TV, lambda/2 ||I - mean I||^2)
+ *   (section 3.1's a-priori bound on ||u*||_TV); with GP_RULE_GRID_CAP the
+ *   result is capped by ||grad I||_L2 (the grid-dependent rule).  1 for a
+ *   constant image; NaN for bad arguments.  rof_solve uses both flags.
+ * gp_emd_delta_tau: section 4.2's rule for delta measures,
+ *   tau = min(sqrt(1 / (eps |log eps|)), 2 M^(1/4)),
+ *   M = N^2 grid points (m_points != 0) or N (the other reading, see the
+ *   design notes).  NaN unless N >= 1 and 0 < eps < 1.
+ */
+#define GP_RULE_GRID_CAP 1
+#define GP_RULE_FIDELITY_BOUND 2
+GP_API double gp_rof_step_tau(const double* stats, double lambda, double eps, int flags);
+GP_API double gp_emd_delta_tau(int N, double eps, int m_points);
+
+/*
  * Launch profiler (tracing).  gp_profile(h, 1) clears the counters and starts
  * recording: every kernel the handle launches is bracketed by CUDA events on
  * its stream (CUDA-graph replay is disabled while recording); gp_profile(h, 0)

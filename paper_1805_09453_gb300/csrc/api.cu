@@ -946,11 +946,9 @@ gp_status rof_rule(gp_handle h, const float* I, int N, double lambda, const gp_o
   double stats[3];
   gp_status r = rof_image_stats(h, I, N, stats, st);
   if (r != GP_OK) return r;
-  const double tv = stats[0], grad_l2 = stats[1], fid = 0.5 * lambda * stats[2];
-  if (!isfinite(tv) || !isfinite(fid)) return fail(h, GP_ERR_NONFINITE, "non-finite image");
+  if (!isfinite(stats[0]) || !isfinite(stats[2])) return fail(h, GP_ERR_NONFINITE, "non-finite image");
   const double eps = o.eps > 0 ? o.eps : 1e-3;
-  double tau = fmin(sqrt(lambda) * fmin(tv, fid) / sqrt(eps), grad_l2);
-  if (!(tau > 0)) tau = 1.0;  // constant image
+  const double tau = gp_rof_step_tau(stats, lambda, eps, GP_RULE_GRID_CAP | GP_RULE_FIDELITY_BOUND);
   *tau_out = tau * (o.tau_scale > 0 ? o.tau_scale : 1.0);
   return GP_OK;
 }
@@ -2249,6 +2247,21 @@ gp_status gp_rof_image_stats(gp_handle h, const float* I, int N, double* out, vo
   DeviceGuard g(h->device);
   if (!g.ok) return fail(h, GP_ERR_CUDA, "cudaSetDevice failed");
   return rof_image_stats(h, I, N, out, (cudaStream_t)stream);
+}
+
+double gp_rof_step_tau(const double* stats, double lambda, double eps, int flags) {
+  if (!stats || !(lambda > 0) || !(eps > 0)) return NAN;
+  const double tv = stats[0], grad_l2 = stats[1], fid = 0.5 * lambda * stats[2];
+  const double T = (flags & GP_RULE_FIDELITY_BOUND) ? fmin(tv, fid) : tv;
+  double tau = sqrt(lambda) * T / sqrt(eps);
+  if (flags & GP_RULE_GRID_CAP) tau = fmin(tau, grad_l2);
+  return tau > 0 ? tau : 1.0;  // a constant image: any step
+}
+
+double gp_emd_delta_tau(int N, double eps, int m_points) {
+  if (N < 1 || !(eps > 0) || !(eps < 1)) return NAN;
+  const double M = m_points ? (double)N * N : (double)N;
+  return fmin(sqrt(1.0 / (eps * fabs(log(eps)))), 2.0 * pow(M, 0.25));
 }
 
 int gp_gap_schedule_next(int n_prev, double g_prev, int n, double g, double tol) {

@@ -29,7 +29,7 @@ EXPORTS = ["gp_abi_version", "gp_default_opts", "gp_create", "gp_destroy", "gp_l
            "gp_cnn_set_params", "gp_cnn_forward", "gp_cnn_loss_grad", "gp_cnn_adam_step", "emd_solve_learned",
            "emd_coarse_start", "gp_gap_schedule_next", "gp_rof_image_stats", "gp_state_average",
            "gp_state_read_average", "rof_solve_cp2", "rof_solve3d", "emd_solve3d", "gp_state_certify",
-           "rof_coarse_start", "rof_solve_learned"]
+           "rof_coarse_start", "rof_solve_learned", "gp_rof_step_tau", "gp_emd_delta_tau"]
 
 
 class Opts(C.Structure):
@@ -116,12 +116,17 @@ def lib():
     L.gp_rof_image_stats.argtypes = [vp, vp, i, C.POINTER(d), vp]
     L.rof_solve3d.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(Opts), C.POINTER(Report), vp]
     L.emd_solve3d.argtypes = [vp, vp, vp, vp, vp, i, C.POINTER(Opts), C.POINTER(Report), vp]
+    L.gp_rof_step_tau.argtypes = [C.POINTER(d), d, d, i]
+    L.gp_emd_delta_tau.argtypes = [i, d, i]
     L.gp_profile_kernels.restype = i
     L.gp_profile_query.argtypes = [vp, i, C.POINTER(C.c_char_p), C.POINTER(d), C.POINTER(C.c_longlong)]
     for name in EXPORTS:
         if name not in ("gp_abi_version", "gp_default_opts", "gp_last_error", "gp_profile_kernels",
-                        "gp_tuned_row_block", "gp_cnn_last_error", "gp_cnn_num_params"):
+                        "gp_tuned_row_block", "gp_cnn_last_error", "gp_cnn_num_params", "gp_rof_step_tau",
+                        "gp_emd_delta_tau"):
             getattr(L, name).restype = i
+    L.gp_rof_step_tau.restype = d
+    L.gp_emd_delta_tau.restype = d
     _lib = L
     return L
 
@@ -419,6 +424,21 @@ def rof_image_stats(h: Handle, I, stream=None):
     out = (C.c_double * 3)()
     h.check(lib().gp_rof_image_stats(h.ptr, _ptr(I), _side(I, "I"), out, _stream(stream)))
     return float(out[0]), float(out[1]), float(out[2])
+
+
+RULE_GRID_CAP, RULE_FIDELITY_BOUND = 1, 2
+
+
+def rof_step_tau(stats, lam: float, eps: float, grid_cap: bool = True, fidelity_bound: bool = False) -> float:
+    """Section 4.1's ROF step rule from (||I||_TV, ||grad I||_L2, ||I - mean I||^2) -- see include/gprox.h."""
+    arr = (C.c_double * 3)(*[float(x) for x in stats])
+    flags = (RULE_GRID_CAP if grid_cap else 0) | (RULE_FIDELITY_BOUND if fidelity_bound else 0)
+    return float(lib().gp_rof_step_tau(arr, float(lam), float(eps), flags))
+
+
+def emd_delta_tau(N: int, eps: float, m_points: bool = True) -> float:
+    """Section 4.2's step rule for delta measures -- see include/gprox.h."""
+    return float(lib().gp_emd_delta_tau(int(N), float(eps), 1 if m_points else 0))
 
 
 def gap_schedule_next(n_prev: int, g_prev: float, n: int, g: float, tol: float) -> int:

@@ -55,14 +55,15 @@ PAPER_TABLES = {
 
 
 def rof_tau(stats, lam: float, eps: float, grid_dependent: bool = True) -> float:
-    """Section 4.1 step rule from (||I||_TV, ||grad I||_L2, .)."""
-    tv, grad_l2 = stats[0], stats[1]
-    tau = math.sqrt(lam) * tv / math.sqrt(eps)
-    return min(tau, grad_l2) if grid_dependent else tau
+    """Section 4.1's step rule from (||I||_TV, ||grad I||_L2, .), computed by
+    the library (gp_rof_step_tau): sqrt(lam) ||I||_TV / sqrt(eps), capped by
+    ||grad I||_L2 for the grid-dependent rule."""
+    return gprox.rof_step_tau(stats, lam, eps, grid_cap=grid_dependent)
 
 
 def emd_delta_tau(N: int, eps: float, m_points: bool = True) -> float:
-    """Section 4.2 step rule for delta measures, min(sqrt(1/(eps |log eps|)), 2 M^(1/4)).
+    """Section 4.2's step rule for delta measures, min(sqrt(1/(eps |log eps|)), 2 M^(1/4)),
+    computed by the library (gp_emd_delta_tau).
 
     Section 4.2 defines M as the number of grid points (M = N^2), but its
     statements about which term is the smaller on which grid (eps = 1e-3: the
@@ -73,8 +74,7 @@ def emd_delta_tau(N: int, eps: float, m_points: bool = True) -> float:
     against its 121; M = N: 219), so it is the default; m_points=False takes
     M = N.
     """
-    M = N * N if m_points else N
-    return min(math.sqrt(1.0 / (eps * abs(math.log(eps)))), 2.0 * M ** 0.25)
+    return gprox.emd_delta_tau(N, eps, m_points)
 
 
 def _state(h, kind, N, inputs, tau, lam=None):

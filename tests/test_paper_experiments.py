@@ -129,3 +129,23 @@ def test_ground_truth_certified_by_the_gap(monkeypatch):
     assert gt["certified"] and gt["iters"] == 13350 and abs(gt["F"] - (2.0 + 1.0 / 13350)) < 1e-15
     gt = PE.ground_truth(None, "emd", 8, None, 1.0, 1e-3, max_iters=1000)
     assert not gt["certified"] and gt["iters"] == 1000 and abs(gt["F"] - 2.001) < 1e-12  # smallest primal seen
+
+
+@pytest.mark.parametrize("N,lam,eps", [(32, 8.0, 1e-3), (64, 20.0, 1e-2), (48, 0.5, 1e-3)])
+def test_rof_step_rule_in_the_library_matches_the_oracle(N, lam, eps):
+    """gp_rof_step_tau (host only) with both flags is rof_solve's rule; on the
+    oracle's image norms it gives the oracle's tau, and without the flags the
+    plain section-4.1 rule sqrt(lam) ||I||_TV / sqrt(eps)."""
+    from oracle import gprox_oracle as O
+    from paper_1805_09453_gb300 import gprox
+
+    I = synth.rof_image(N, N).astype(np.float64)
+    tau, _, st = O.rof_step_rule(I, lam, eps)
+    stats = (st["tv"], st["grad_l2"], st["fid"] / (0.5 * lam))
+    got = gprox.rof_step_tau(stats, lam, eps, grid_cap=True, fidelity_bound=True)
+    assert abs(got - tau) <= 1e-14 * tau
+    plain = gprox.rof_step_tau(stats, lam, eps, grid_cap=False)
+    assert abs(plain - math.sqrt(lam) * st["tv"] / math.sqrt(eps)) <= 1e-14 * plain
+    assert gprox.rof_step_tau((0.0, 0.0, 0.0), lam, eps) == 1.0  # a constant image
+    assert math.isnan(gprox.rof_step_tau(stats, -1.0, eps))
+    assert math.isnan(gprox.emd_delta_tau(0, eps))
