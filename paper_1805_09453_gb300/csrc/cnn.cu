@@ -424,6 +424,7 @@ inline int g1d(long n) { return (int)std::min<long>((n + 255) / 256, 8192); }
 struct Conv {
   int cin, cout;
   long woff, boff;  // offsets of W [cout][cin][3][3] and b [cout] in the parameter vector
+  long imoff;       // offset of its tensor-core weight images (BF16 mode)
 };
 
 // Activations of one sample, with their channel counts and pyramid level
@@ -457,7 +458,7 @@ std::vector<Conv> build_convs(int C, long* nparam) {
   std::vector<Conv> v;
   long off = 0;
   for (auto& s : spec) {
-    Conv c{s[0], s[1], off, 0};
+    Conv c{s[0], s[1], off, 0, 0};
     off += (long)s[0] * s[1] * 9;
     c.boff = off;
     off += s[1];
@@ -478,6 +479,7 @@ struct gp_cnn_s {
   long nparam = 0;
   float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr;  // master weights, Adam moments, gradients
   void* wc = nullptr;                                            // compute copy of the weights
+  void* wimg = nullptr;  // the convolutions' tensor-core weight images (BF16 mode)
   long step = 0;
   int cap_B = 0, cap_N = 0;
   void* act[NACT] = {};
@@ -577,6 +579,7 @@ struct Net {
   T* ptr(int a, long ch0 = 0) const { return reinterpret_cast<T*>(n->act[a]) + ch0 * plane(d.lev[a]); }
   float* gptr(int a, long ch0 = 0) const { return n->grd[a] + ch0 * plane(d.lev[a]); }
   const T* W(int i) const { return reinterpret_cast<const T*>(n->wc) + n->convs[i].woff; }
+  const void* img(int i) const { return reinterpret_cast<const __nv_bfloat16*>(n->wimg) + n->convs[i].imoff; }
   const float* Bv(int i) const { return n->w + n->convs[i].boff; }
   dim3 cgrid(int l, int cout) const {
     const int t = (side(l) + TS - 1) / TS;
@@ -587,8 +590,8 @@ struct Net {
   void conv(int i, const T* x, long xbs, TO* y, long ybs, int l) const {
     const Conv& c = n->convs[i];
     if constexpr (sizeof(T) == 2) {  // BF16 mode: implicit GEMM on the tensor cores
-      gp::conv3x3_tc(x, xbs, c.cin, W(i), Bv(i), y, ybs, c.cout, side(l), side(l), B, RELU, sizeof(TO) == 4, n->tc_err,
-                 st);
+      gp::conv3x3_tc(x, xbs, c.cin, img(i), Bv(i), y, ybs, c.cout, side(l), side(l), B, RELU, sizeof(TO) == 4,
+                     n->tc_err, st);
     } else {
       k_conv3x3<T, T, TO, RELU, false><<<cgrid(l, c.cout), TS * TS, 0, st>>>(x, xbs, c.cin, W(i), Bv(i), y, ybs,
                                                                              c.cout, side(l), side(l));
@@ -641,7 +644,7 @@ struct Net {
     }
     if (dx) {
       if constexpr (sizeof(T) == 2) {  // BF16 mode: data gradient on the tensor cores
-        gp::conv3x3_dgrad_tc(dy, dybs, c.cout, W(i), dx, bs(xa), c.cin, side(l), side(l), B, n->tc_err, st);
+        gp::conv3x3_dgrad_tc(dy, dybs, c.cout, img(i), dx, bs(xa), c.cin, side(l), side(l), B, n->tc_err, st);
       } else {
         k_conv3x3<float, T, float, false, true><<<cgrid(l, c.cin), TS * TS, 0, st>>>(dy, dybs, c.cout, W(i), nullptr,
                                                                                     dx, bs(xa), c.cin, side(l), side(l));
@@ -753,11 +756,19 @@ void backward_impl(gp_cnn n, int B, int N, cudaStream_t st) {
   Net<T>(n, B, N, st).backward();
 }
 
+// BF16 mode: the tensor-core weight images of every convolution, from the compute copy.
+gp_status pack_images(gp_cnn n, cudaStream_t st) {
+  for (const Conv& c : n->convs)
+    CN_CUDA(n, gp::conv3x3_tc_pack(reinterpret_cast<const __nv_bfloat16*>(n->wc) + c.woff, c.cin, c.cout,
+                                   reinterpret_cast<__nv_bfloat16*>(n->wimg) + c.imoff, st));
+  return GP_OK;
+}
+
 gp_status refresh_copy(gp_cnn n, cudaStream_t st) {
   if (n->bf16) k_copy_params<__nv_bfloat16><<<g1d(n->nparam), 256, 0, st>>>(n->w, (__nv_bfloat16*)n->wc, n->nparam);
   else k_copy_params<float><<<g1d(n->nparam), 256, 0, st>>>(n->w, (float*)n->wc, n->nparam);
   CN_CUDA(n, cudaGetLastError());
-  return GP_OK;
+  return n->bf16 ? pack_images(n, st) : GP_OK;
 }
 
 }  // namespace
@@ -775,11 +786,17 @@ GP_API gp_status gp_cnn_create(gp_handle h, int base_channels, int bf16, unsigne
   n->C = base_channels;
   n->bf16 = bf16 != 0;
   n->convs = build_convs(n->C, &n->nparam);
+  size_t nimg = 0;
+  for (Conv& c : n->convs) {
+    c.imoff = (long)nimg;
+    nimg += gp::conv3x3_tc_image_elems(c.cin, c.cout);
+  }
   DevGuard g(n->device);
   const size_t P = (size_t)n->nparam;
   if (!g.ok || cudaMalloc((void**)&n->w, P * 4) || cudaMalloc((void**)&n->m, P * 4) ||
       cudaMalloc((void**)&n->v, P * 4) || cudaMalloc((void**)&n->g, P * 4) ||
-      cudaMalloc(&n->wc, P * (n->bf16 ? 2 : 4)) || cudaMalloc((void**)&n->tc_err, sizeof(int)) ||
+      cudaMalloc(&n->wc, P * (n->bf16 ? 2 : 4)) || (n->bf16 && cudaMalloc(&n->wimg, nimg * 2)) ||
+      cudaMalloc((void**)&n->tc_err, sizeof(int)) ||
       cudaMemset(n->tc_err, 0, sizeof(int))) {
     cudaGetLastError();
     gp_cnn_destroy(n);
@@ -815,6 +832,7 @@ GP_API gp_status gp_cnn_destroy(gp_cnn n) {
   cudaFree(n->v);
   cudaFree(n->g);
   cudaFree(n->wc);
+  cudaFree(n->wimg);
   cudaFree(n->tc_err);
   delete n;
   return GP_OK;
@@ -918,7 +936,7 @@ GP_API gp_status gp_cnn_adam_step(gp_cnn n, double lr, void* stream) {
     k_adam<float><<<g1d(n->nparam), 256, 0, st>>>(n->w, n->m, n->v, n->g, (float*)n->wc, n->nparam, (float)lr, b1, b2,
                                                   1e-8f, c1, c2);
   CN_CUDA(n, cudaGetLastError());
-  return GP_OK;
+  return n->bf16 ? pack_images(n, st) : GP_OK;
 }
 
 GP_API gp_status emd_solve_learned(gp_handle h, gp_cnn n, const float* f0, const float* f1, float* m, float* p,

@@ -123,18 +123,22 @@ cudaError_t dct_plan_dense(DctPlan& p);
 // and split with its own scale, x used as the staging plane); tmp holds
 // 2*N*N floats; *err is set to 1 if a wait timed out.
 bool tc_solve_supported(int N);
-// Warm-start network (BF16 mode): 3x3 convolution as a tcgen05 implicit GEMM
-// (cnn_tc.cu); X, W BF16, Y BF16 (or FP32 when y_fp32), Cout <= 256; *err is
-// set to 1 if a wait timed out.
-cudaError_t conv3x3_tc(const void* X, long xbs, int Cin, const void* W, const float* bias, void* Y, long ybs, int Cout,
+// Warm-start network (BF16 mode): 3x3 convolutions as tcgen05 implicit GEMMs
+// (cnn_tc.cu).  A convolution's BF16 weights W [Cout][Cin][3][3] are first
+// packed into two tensor-core images (conv3x3_tc_image_elems elements, 16-byte
+// aligned): the forward image, then the data-gradient (flipped, transposed)
+// image.  *err is set to 1 if a wait timed out.
+size_t conv3x3_tc_image_elems(int Cin, int Cout);
+cudaError_t conv3x3_tc_pack(const void* W, int Cin, int Cout, void* img, cudaStream_t st);
+// Y = act(conv(X) + bias): X BF16, Y BF16 (or FP32 when y_fp32).
+cudaError_t conv3x3_tc(const void* X, long xbs, int Cin, const void* img, const float* bias, void* Y, long ybs, int Cout,
                        int H, int Wd, int B, bool relu, bool y_fp32, int* err, cudaStream_t st);
-// Its weight and bias gradients (accumulated into dW [Cout][Cin][3][3] and db):
+// Weight and bias gradients (accumulated into dW [Cout][Cin][3][3] and db, which may be null):
 // dY FP32 as a hi + lo BF16 pair, X BF16.
 cudaError_t conv3x3_wgrad_tc(const float* dY, long dybs, int Cout, const void* X, long xbs, int Cin, int H, int Wd,
                              int B, float* dW, float* db, int* err, cudaStream_t st);
-// Its data gradient dX (written, FP32) from dY (FP32, hi + lo BF16) and the
-// flipped, transposed BF16 weights.
-cudaError_t conv3x3_dgrad_tc(const float* dY, long dybs, int Cout, const void* W, float* dX, long dxbs, int Cin,
+// Data gradient dX (written, FP32) from dY (FP32, hi + lo BF16) and the data-gradient image.
+cudaError_t conv3x3_dgrad_tc(const float* dY, long dybs, int Cout, const void* img, float* dX, long dxbs, int Cin,
                              int H, int Wd, int B, int* err, cudaStream_t st);
 cudaError_t dct_solve_tc(const DctPlan& p, const float* b, float* x, float* tmp, float alpha, float scale, int* err,
                          cudaStream_t st, bool fp16);
