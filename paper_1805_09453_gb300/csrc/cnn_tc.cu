@@ -150,29 +150,36 @@ __device__ __forceinline__ void tmem_ld16(uint32_t tmem, int c0, float* v) {
 // zero outside [0, Wd): x0 % 8 == 0, x0 + 8 <= Wd, the row 16-byte aligned.
 // BF16 pairs are 32-bit words (the lower address in the low half), so a
 // shift by one element is a 16-bit funnel shift across neighbouring words.
-__device__ __forceinline__ uint4 row8(const __nv_bfloat16* row, int x0, int dx, int Wd) {
-  const uint4 c = __ldg(reinterpret_cast<const uint4*>(row + x0));
-  if (dx == 0) return c;
-  if (dx < 0) {
-    const uint32_t p = x0 > 0 ? __ldg(reinterpret_cast<const uint32_t*>(row + x0 - 2)) : 0u;
-    return make_uint4(__funnelshift_r(p, c.x, 16), __funnelshift_r(c.x, c.y, 16), __funnelshift_r(c.y, c.z, 16),
-                      __funnelshift_r(c.z, c.w, 16));
-  }
-  const uint32_t n = x0 + 8 < Wd ? __ldg(reinterpret_cast<const uint32_t*>(row + x0 + 8)) : 0u;
-  return make_uint4(__funnelshift_r(c.x, c.y, 16), __funnelshift_r(c.y, c.z, 16), __funnelshift_r(c.z, c.w, 16),
-                    __funnelshift_r(c.w, n, 16));
+// The loads (issued for all of a slab's items before any is used) and the
+// combination are separate steps.
+__device__ __forceinline__ void row8_load(const __nv_bfloat16* row, int x0, int dx, int Wd, uint4& c, uint32_t& nb) {
+  c = __ldg(reinterpret_cast<const uint4*>(row + x0));
+  nb = 0u;
+  if (dx < 0 && x0 > 0) nb = __ldg(reinterpret_cast<const uint32_t*>(row + x0 - 2));
+  if (dx > 0 && x0 + 8 < Wd) nb = __ldg(reinterpret_cast<const uint32_t*>(row + x0 + 8));
 }
-__device__ __forceinline__ void row8(const float* row, int x0, int dx, int Wd, float* o) {
-  const float4 a = __ldg(reinterpret_cast<const float4*>(row + x0));
-  const float4 b = __ldg(reinterpret_cast<const float4*>(row + x0 + 4));
+__device__ __forceinline__ uint4 row8_combine(const uint4& c, uint32_t nb, int dx) {
+  if (dx == 0) return c;
+  if (dx < 0)
+    return make_uint4(__funnelshift_r(nb, c.x, 16), __funnelshift_r(c.x, c.y, 16), __funnelshift_r(c.y, c.z, 16),
+                      __funnelshift_r(c.z, c.w, 16));
+  return make_uint4(__funnelshift_r(c.x, c.y, 16), __funnelshift_r(c.y, c.z, 16), __funnelshift_r(c.z, c.w, 16),
+                    __funnelshift_r(c.w, nb, 16));
+}
+__device__ __forceinline__ void row8_load(const float* row, int x0, int dx, int Wd, float4& a, float4& b, float& nb) {
+  a = __ldg(reinterpret_cast<const float4*>(row + x0));
+  b = __ldg(reinterpret_cast<const float4*>(row + x0 + 4));
+  nb = 0.f;
+  if (dx < 0 && x0 > 0) nb = __ldg(row + x0 - 1);
+  if (dx > 0 && x0 + 8 < Wd) nb = __ldg(row + x0 + 8);
+}
+__device__ __forceinline__ void row8_combine(const float4& a, const float4& b, float nb, int dx, float* o) {
   if (dx == 0) {
     o[0] = a.x, o[1] = a.y, o[2] = a.z, o[3] = a.w, o[4] = b.x, o[5] = b.y, o[6] = b.z, o[7] = b.w;
   } else if (dx < 0) {
-    o[0] = x0 > 0 ? __ldg(row + x0 - 1) : 0.f;
-    o[1] = a.x, o[2] = a.y, o[3] = a.z, o[4] = a.w, o[5] = b.x, o[6] = b.y, o[7] = b.z;
+    o[0] = nb, o[1] = a.x, o[2] = a.y, o[3] = a.z, o[4] = a.w, o[5] = b.x, o[6] = b.y, o[7] = b.z;
   } else {
-    o[0] = a.y, o[1] = a.z, o[2] = a.w, o[3] = b.x, o[4] = b.y, o[5] = b.z, o[6] = b.w;
-    o[7] = x0 + 8 < Wd ? __ldg(row + x0 + 8) : 0.f;
+    o[0] = a.y, o[1] = a.z, o[2] = a.w, o[3] = b.x, o[4] = b.y, o[5] = b.z, o[6] = b.w, o[7] = nb;
   }
 }
 
@@ -281,39 +288,43 @@ __global__ void __launch_bounds__(CTHREADS) k_conv_tc(const TX* __restrict__ X, 
       for (int i = threadIdx.x; i < nloc * 8; i += CTHREADS) cp16(su32(Bs) + 16 * i, src + 8 * i);
     }
     if (vec) {
+      int dxj[8];
       if constexpr (!SPLIT) {
-        uint4 v[8];
+        uint4 c[8];
+        uint32_t nb[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const unsigned k = kb + 8 * j, c = k / 9, t = k - 9 * c;
-          const int dy = (int)(t / 3) - 1, dx = (int)(t % 3) - 1, yy = py + dy;
-          v[j] = make_uint4(0u, 0u, 0u, 0u);
-          if (pin && (int)c < Cx && yy >= 0 && yy < H) v[j] = row8(Xb + c * plane + (long)yy * Wd, px, dx, Wd);
+          const unsigned k = kb + 8 * j, ch = k / 9, t = k - 9 * ch;
+          const int yy = py + (int)(t / 3) - 1;
+          dxj[j] = (int)(t % 3) - 1;
+          c[j] = make_uint4(0u, 0u, 0u, 0u);
+          nb[j] = 0u;
+          if (pin && (int)ch < Cx && yy >= 0 && yy < H) row8_load(Xb + ch * plane + (long)yy * Wd, px, dxj[j], Wd, c[j], nb[j]);
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) *reinterpret_cast<uint4*>(As + mnmaj(8 * pg, 8 * j + kr)) = v[j];
+        for (int j = 0; j < 8; ++j)
+          *reinterpret_cast<uint4*>(As + mnmaj(8 * pg, 8 * j + kr)) = row8_combine(c[j], nb[j], dxj[j]);
       } else {
+        float4 a[8], bb[8];
+        float nb[8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float o[4][8];
+        for (int j = 0; j < 8; ++j) {
+          const unsigned k = kb + 8 * j, ch = k / 9, t = k - 9 * ch;
+          const int yy = py + (int)(t / 3) - 1;
+          dxj[j] = (int)(t % 3) - 1;
+          a[j] = bb[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+          nb[j] = 0.f;
+          if (pin && (int)ch < Cx && yy >= 0 && yy < H)
+            row8_load(Xb + ch * plane + (long)yy * Wd, px, dxj[j], Wd, a[j], bb[j], nb[j]);
+        }
 #pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            const unsigned k = kb + 8 * (4 * h + jj), c = k / 9, t = k - 9 * c;
-            const int dy = (int)(t / 3) - 1, dx = (int)(t % 3) - 1, yy = py + dy;
-            if (pin && (int)c < Cx && yy >= 0 && yy < H) {
-              row8(Xb + c * plane + (long)yy * Wd, px, dx, Wd, o[jj]);
-            } else {
-#pragma unroll
-              for (int e = 0; e < 8; ++e) o[jj][e] = 0.f;
-            }
-          }
-#pragma unroll
-          for (int jj = 0; jj < 4; ++jj) {
-            uint4 hi, lo;
-            split8(o[jj], hi, lo);
-            *reinterpret_cast<uint4*>(As + mnmaj(8 * pg, 8 * (4 * h + jj) + kr)) = hi;
-            *reinterpret_cast<uint4*>(As + A_BYTES + mnmaj(8 * pg, 8 * (4 * h + jj) + kr)) = lo;
-          }
+        for (int j = 0; j < 8; ++j) {
+          float o[8];
+          row8_combine(a[j], bb[j], nb[j], dxj[j], o);
+          uint4 hi, lo;
+          split8(o, hi, lo);
+          *reinterpret_cast<uint4*>(As + mnmaj(8 * pg, 8 * j + kr)) = hi;
+          *reinterpret_cast<uint4*>(As + A_BYTES + mnmaj(8 * pg, 8 * j + kr)) = lo;
         }
       }
     } else {  // scalar gather, same layout
@@ -442,25 +453,28 @@ __global__ void __launch_bounds__(CTHREADS) k_conv_wgrad_tc(const float* __restr
       ph ^= 1u << b;
     }
     const long qs = q0 + (long)s * CK;
+    uint4 ac[2][4];
+    uint32_t an[2][4];
+    if (vec) {  // A loads first; a group lies in one row and wholly inside or outside [q0, q1)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int g = gl + 4 * h;
-      const long q = qs + 8 * g;
-      if (vec) {  // the group lies in one row and is wholly inside or outside [q0, q1)
-        const bool qin = q < q1;
-        const int y = qin ? (int)(q / Wd) : 0, x0 = qin ? (int)(q % Wd) : 0;
-        uint4 v[4];
+      for (int h = 0; h < 2; ++h) {
+        const unsigned q = (unsigned)(qs + 8 * (gl + 4 * h));
+        const bool qin = q < (unsigned)q1;
+        const int y = (int)(q / (unsigned)Wd), x0 = (int)(q % (unsigned)Wd);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int yy = y + tdy[i];
-          v[i] = make_uint4(0u, 0u, 0u, 0u);
-          if (qin && tcn[i] == -2) v[i] = ones;
-          else if (qin && tcn[i] >= 0 && yy >= 0 && yy < H)
-            v[i] = row8(Xb + tcn[i] * plane + (long)yy * Wd, x0, tdx[i], Wd);
+          ac[h][i] = (qin && tcn[i] == -2) ? ones : make_uint4(0u, 0u, 0u, 0u);
+          an[h][i] = 0u;
+          if (qin && tcn[i] >= 0 && yy >= 0 && yy < H)
+            row8_load(Xb + tcn[i] * plane + (long)yy * Wd, x0, tdx[i], Wd, ac[h][i], an[h][i]);
         }
+      }
+    } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) *reinterpret_cast<uint4*>(As + kmaj(ml[i], 8 * g)) = v[i];
-      } else {
+      for (int h = 0; h < 2; ++h) {
+        const int g = gl + 4 * h;
+        const long q = qs + 8 * g;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           float o[8];
@@ -479,25 +493,49 @@ __global__ void __launch_bounds__(CTHREADS) k_conv_wgrad_tc(const float* __restr
         }
       }
     }
-    // B: rows r = 8 (it >> 6) + (it & 7), groups g = (it >> 3) & 7
-#pragma unroll 4
-    for (int it = threadIdx.x; it < nloc * 8; it += CTHREADS) {
-      const int r = 8 * (it >> 6) + (it & 7), g = (it >> 3) & 7;
-      const int co = n0 + r;
-      const long q = qs + 8 * g;
-      float o[8];
-      if (vec && co < Cout && q < q1) {
-        const float4 a = __ldg(reinterpret_cast<const float4*>(dYb + (long)co * plane + q));
-        const float4 c = __ldg(reinterpret_cast<const float4*>(dYb + (long)co * plane + q + 4));
-        o[0] = a.x, o[1] = a.y, o[2] = a.z, o[3] = a.w, o[4] = c.x, o[5] = c.y, o[6] = c.z, o[7] = c.w;
-      } else {
+    // B: rows r = 8 (it >> 6) + (it & 7), groups g = (it >> 3) & 7, four items' loads at a time
+    for (int it0 = threadIdx.x; it0 < nloc * 8; it0 += 4 * CTHREADS) {
+      float4 lo4[4], hi4[4];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) o[e] = (co < Cout && q + e < q1) ? dYb[(long)co * plane + q + e] : 0.f;
+      for (int u = 0; u < 4; ++u) {
+        const int it = it0 + u * CTHREADS;
+        const int r = 8 * (it >> 6) + (it & 7), g = (it >> 3) & 7;
+        const int co = n0 + r;
+        const long q = qs + 8 * g;
+        lo4[u] = hi4[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (it < nloc * 8 && co < Cout && q < q1) {
+          const float* src = dYb + (long)co * plane + q;
+          if (vec) {
+            lo4[u] = __ldg(reinterpret_cast<const float4*>(src));
+            hi4[u] = __ldg(reinterpret_cast<const float4*>(src + 4));
+          } else {
+            float o[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) o[e] = q + e < q1 ? src[e] : 0.f;
+            lo4[u] = make_float4(o[0], o[1], o[2], o[3]);
+            hi4[u] = make_float4(o[4], o[5], o[6], o[7]);
+          }
+        }
       }
-      uint4 hi, lo;
-      split8(o, hi, lo);
-      *reinterpret_cast<uint4*>(Bh + kmaj(r, 8 * g)) = hi;
-      *reinterpret_cast<uint4*>(Bl + kmaj(r, 8 * g)) = lo;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int it = it0 + u * CTHREADS;
+        if (it < nloc * 8) {
+          const int r = 8 * (it >> 6) + (it & 7), g = (it >> 3) & 7;
+          const float o[8] = {lo4[u].x, lo4[u].y, lo4[u].z, lo4[u].w, hi4[u].x, hi4[u].y, hi4[u].z, hi4[u].w};
+          uint4 hi, lo;
+          split8(o, hi, lo);
+          *reinterpret_cast<uint4*>(Bh + kmaj(r, 8 * g)) = hi;
+          *reinterpret_cast<uint4*>(Bl + kmaj(r, 8 * g)) = lo;
+        }
+      }
+    }
+    if (vec) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          *reinterpret_cast<uint4*>(As + kmaj(ml[i], 8 * (gl + 4 * h))) = row8_combine(ac[h][i], an[h][i], tdx[i]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (!__syncthreads_and(ok)) {
