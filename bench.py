@@ -511,7 +511,7 @@ def run_ours(args):
             t0 = time.perf_counter()
             st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, o)
             ttg["emd"] = dict(emd_row(rep, time.perf_counter() - t0), certificate=cert, cap=args.ttg_cap)
-            for tol, key in ((1e-4, "emd_1e-4"), (2e-5, "emd_2e-5")):  # above the FP32 certification floor
+            for tol, key in ((1e-4, "emd_1e-4"), (2e-5, "emd_2e-5")):  # the looser tolerances
                 o4 = gprox.default_opts(max_iters=args.ttg_cap, tol_rel_gap=tol, gap_every=0, use_graph=1)
                 t0 = time.perf_counter()
                 st, rep = gprox.emd_solve(h, f0d, f1d, m, None, None, o4)

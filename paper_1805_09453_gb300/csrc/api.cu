@@ -799,12 +799,41 @@ void finish_report(gp_report* rep, double P, double D) {
   rep->rel_gap = sc > 0 ? (P - D) / sc : 0.0;
 }
 
+// EMD dual bound of a p whose e = -div p is in s->e (section 3.2 with the
+// weak duality of section 2.1): any phi with max |D phi| <= 1 gives the lower
+// bound h^2 sum phi (f1 - f0), so D = h^2 sum phi (f1 - f0) / max(1, max |D phi|)
+// for phi = Lap^{-1} div p.  phi is held as two FP32 planes, phi_hi from the
+// FP32 cosine solve and phi_lo from a second solve of the first one's FP64
+// residual, and both sums are taken in FP64 from the planes: the bound is
+// exact for the phi represented, and FP32 rounding no longer inflates
+// max |D phi| (near the optimum |D phi| = 1 on the whole transport region, so
+// the largest of millions of rounding errors lands in the normalisation).
+// Writes the two partial sums (sum, max) to dst; uses prim and tmp (free
+// between steps); phi_hi + phi_lo is left in phi.
+gp_status emd_dual_enqueue(gp_state s, float* phi, double* part, double* dst, cudaStream_t st) {
+  gp_handle h = s->h;
+  const int N = s->N;
+  const size_t NN = (size_t)N * N;
+  float* r = s->prim;
+  float* lo = s->prim + NN;
+  gp_status q = solve(h, N, s->e, phi, s->tmp, 0.0, 1.0, GP_PREC_FP32, true, st);
+  if (q != GP_OK) return q;
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_helmholtz_residual(s->e, phi, r, N, 0.0, 1.0, st); }));
+  if ((q = solve(h, N, r, lo, s->tmp, 0.0, 1.0, GP_PREC_FP32, true, st)) != GP_OK) return q;
+  const int nd = reduce_blocks_1d(NN);
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st,
+                     [&] { return launch_emd_dual_hilo(phi, lo, s->f0, s->f1, N, part, nd, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(part, nd, 2, 2u, dst, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_add_inplace(phi, lo, NN, st); }));
+  return GP_OK;
+}
+
 // Gap of the current iterate, in two halves so that a CUDA graph can hold the
 // device half: state_gap_enqueue writes the four reduced scalars to `dst`
 // (device); state_gap_finish turns their host copy into P, D and the gap.
 // The fused partials are used when the last step left them, else the terms
 // are recomputed with the unfused kernels.
-gp_status state_gap_enqueue(gp_state s, double* dst, int prec, cudaStream_t st) {
+gp_status state_gap_enqueue(gp_state s, double* dst, cudaStream_t st) {
   gp_handle h = s->h;
   const int N = s->N;
   const size_t NN = (size_t)N * N;
@@ -822,16 +851,8 @@ gp_status state_gap_enqueue(gp_state s, double* dst, int prec, cudaStream_t st) 
               return launch_emd_primal(s->m, s->p[s->cur], s->f0, s->f1, s->e, N, s->part, nb, st);
             }));
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 2, 0u, dst, st); }));
-  // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p = e; grad phi into prim (free between steps)
-  gp_status r = solve_grad(h, N, s->e, s->prim, s->phi, true, s->tmp, 0.0, 1.0, prec, st, false, s->s[1 - s->cur],
-                           s->part);
-  if (r != GP_OK) return r;
-  const int nd = reduce_blocks_1d(NN);
-  double* pd = s->part + (size_t)nb * 4;
-  GP_CUDA(h, plaunch(h, PK_REDUCE, st,
-                     [&] { return launch_emd_dual(s->phi, s->prim, s->f0, s->f1, N, pd, nd, st); }));
-  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(pd, nd, 2, 2u, dst + 2, st); }));
-  return GP_OK;
+  // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p = e
+  return emd_dual_enqueue(s, s->phi, s->part + (size_t)nb * 4, dst + 2, st);
 }
 
 void state_gap_finish(gp_state s, const double* v, gp_report* rep) {
@@ -886,11 +907,11 @@ gp_status emd_certify(gp_state s, gp_report* rep, cudaStream_t st) {
   return GP_OK;
 }
 
-gp_status state_gap(gp_state s, gp_report* rep, int prec, cudaStream_t st) {
+gp_status state_gap(gp_state s, gp_report* rep, cudaStream_t st) {
   gp_handle h = s->h;
   gp_status r = ensure_res(h);
   if (r != GP_OK) return r;
-  if ((r = state_gap_enqueue(s, h->dres, prec, st)) != GP_OK) return r;
+  if ((r = state_gap_enqueue(s, h->dres, st)) != GP_OK) return r;
   if ((r = fetch(h, 4, st)) != GP_OK) return r;
   state_gap_finish(s, h->hres, rep);
   return GP_OK;
@@ -1031,10 +1052,7 @@ gp_status emd_window_dual(gp_state s, long long n, double* D, cudaStream_t st) {
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] {
             return launch_emd_primal(s->m, s->prim, s->f0, s->f1, s->e, N, s->part, nd, st);  // e = -div p_bar
           }));
-  if ((r = solve_grad(h, N, s->e, s->prim, s->phiwin, true, s->tmp, 0.0, 1.0, GP_PREC_FP32, st)) != GP_OK) return r;
-  GP_CUDA(h, plaunch(h, PK_REDUCE, st,
-                     [&] { return launch_emd_dual(s->phiwin, s->prim, s->f0, s->f1, N, s->part, nd, st); }));
-  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nd, 2, 2u, h->dres, st); }));
+  if ((r = emd_dual_enqueue(s, s->phiwin, s->part, h->dres, st)) != GP_OK) return r;
   if ((r = fetch(h, 2, st)) != GP_OK) return r;
   *D = h->hres[0] / ((double)N * N) / fmax(1.0, h->hres[1]);
   s->partials_valid = false;
@@ -1133,14 +1151,14 @@ gp_status run_loop(gp_state s, const gp_opts& o, gp_report* rep, cudaStream_t st
   bool certified = false;  // the report's certificate belongs to the current iterate
   EmdStop z;
   gp_status r;
-  if (o.max_iters == 0 && (r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
+  if (o.max_iters == 0 && (r = state_gap(s, rep, st)) != GP_OK) return r;
   int k_next = o.gap_every > 0 ? o.gap_every : kAdaptiveMinChunk;
   int n_prev = -1;
   double g_prev = 0;
   while (s->n < o.max_iters) {
     const int k = std::min(k_next, o.max_iters - s->n);
     if ((r = run_steps(s, k, o.prec, true, o.use_graph != 0, st)) != GP_OK) return r;
-    if ((r = state_gap(s, rep, o.prec, st)) != GP_OK) return r;
+    if ((r = state_gap(s, rep, st)) != GP_OK) return r;
     certified = false;
     if (!isfinite(rep->primal) || !isfinite(rep->dual)) {
       status = GP_ERR_NONFINITE;
@@ -1527,7 +1545,7 @@ gp_status gp_state_gap(gp_handle h, gp_state s, gp_report* rep, void* stream) {
   DeviceGuard g(h->device);
   Timer t;
   memset(rep, 0, sizeof(*rep));
-  gp_status r = state_gap(s, rep, GP_PREC_FP32, (cudaStream_t)stream);
+  gp_status r = state_gap(s, rep, (cudaStream_t)stream);
   rep->iters = s->n;
   rep->tau = s->tau;
   rep->sigma = s->sigma;
@@ -1542,7 +1560,7 @@ gp_status gp_state_certify(gp_handle h, gp_state s, gp_report* rep, void* stream
   DeviceGuard g(h->device);
   Timer t;
   memset(rep, 0, sizeof(*rep));
-  gp_status r = state_gap(s, rep, GP_PREC_FP32, (cudaStream_t)stream);
+  gp_status r = state_gap(s, rep, (cudaStream_t)stream);
   if (r == GP_OK && s->kind == KIND_EMD && isfinite(rep->dual)) r = emd_certify(s, rep, (cudaStream_t)stream);
   rep->iters = s->n;
   rep->tau = s->tau;
@@ -2027,7 +2045,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
         for (int b : active) {
           gp_state s = h->batch[b];
           if ((r = run_steps(s, k, o.prec, true, false, st)) != GP_OK) return r;
-          if ((r = state_gap_enqueue(s, h->bres_d + 4 * b, o.prec, st)) != GP_OK) return r;
+          if ((r = state_gap_enqueue(s, h->bres_d + 4 * b, st)) != GP_OK) return r;
         }
         GP_CUDA(h, cudaMemcpyAsync(h->bres_h, h->bres_d, 4 * B * sizeof(double), cudaMemcpyDeviceToHost, st));
         GP_CUDA(h, cudaStreamSynchronize(st));
@@ -2046,7 +2064,7 @@ gp_status emd_solve_batched(gp_handle h, int B, const float* const* f0, const fl
           cudaStream_t a = h->aux[b];
           cudaStreamWaitEvent(a, h->evs[0], 0);
           cr = run_steps(h->batch[b], k, o.prec, true, false, a);
-          if (cr == GP_OK) cr = state_gap_enqueue(h->batch[b], h->bres_d + 4 * b, o.prec, a);
+          if (cr == GP_OK) cr = state_gap_enqueue(h->batch[b], h->bres_d + 4 * b, a);
           cudaEventRecord(h->evs[1 + i], a);
           cudaStreamWaitEvent(st, h->evs[1 + i], 0);
         }

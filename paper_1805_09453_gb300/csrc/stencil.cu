@@ -331,41 +331,26 @@ __global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ gq,
   }
 }
 
-// EMD dual bound inputs: sum phi (f1 - f0) and max |grad phi| (grad phi from
-// the spectral gradient of the solve: two planes).
-__global__ void __launch_bounds__(256) k_emd_dual(const float* __restrict__ phi, const float* __restrict__ gphi,
-                                                  const float* __restrict__ f0, const float* __restrict__ f1, int N,
-                                                  double* __restrict__ part) {
-  CSum s;
-  float gmax = 0.f;
+// EMD dual bound inputs for a potential held as two FP32 planes,
+// phi = hi + lo: sum phi (f1 - f0) and max |D phi| (forward differences with
+// h = 1/N, zero last slots), all in FP64, so that both are exact for the phi
+// the planes represent (weak duality then holds for the bound as computed).
+__global__ void __launch_bounds__(256) k_emd_dual_hilo(const float* __restrict__ hi, const float* __restrict__ lo,
+                                                       const float* __restrict__ f0, const float* __restrict__ f1,
+                                                       int N, double* __restrict__ part) {
+  double sum = 0.0, g2 = 0.0;
   const size_t NN = (size_t)N * N;
+  const double n = (double)N;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
-    s.add(phi[idx] * (f1[idx] - f0[idx]));
-    const float gx = gphi[idx], gy = gphi[NN + idx];
-    gmax = fmaxf(gmax, sqrtf(gx * gx + gy * gy));
+    const unsigned row = (unsigned)(idx / (unsigned)N), col = (unsigned)(idx % (unsigned)N);
+    const double h0 = hi[idx], l0 = lo[idx];
+    sum += (h0 + l0) * ((double)f1[idx] - (double)f0[idx]);
+    double gx = 0.0, gy = 0.0;
+    if (col + 1 < (unsigned)N) gx = n * (((double)hi[idx + 1] - h0) + ((double)lo[idx + 1] - l0));
+    if (row + 1 < (unsigned)N) gy = n * (((double)hi[idx + N] - h0) + ((double)lo[idx + N] - l0));
+    g2 = fmax(g2, gx * gx + gy * gy);
   }
-  double v[2] = {s.value(), (double)gmax};
-  block_reduce_store<2>(v, 2u, part);
-}
-
-// The same with 128-bit loads (all pointers 16-byte aligned, N^2 % 4 == 0):
-// a quarter of the load instructions for this bandwidth-bound pass.
-__global__ void __launch_bounds__(256) k_emd_dual4(const float4* __restrict__ phi, const float4* __restrict__ gx,
-                                                   const float4* __restrict__ gy, const float4* __restrict__ f0,
-                                                   const float4* __restrict__ f1, size_t n4,
-                                                   double* __restrict__ part) {
-  CSum s;
-  float gmax = 0.f;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n4; idx += (size_t)gridDim.x * blockDim.x) {
-    const float4 p = phi[idx], a = f0[idx], b = f1[idx], x = gx[idx], y = gy[idx];
-    s.add(p.x * (b.x - a.x));
-    s.add(p.y * (b.y - a.y));
-    s.add(p.z * (b.z - a.z));
-    s.add(p.w * (b.w - a.w));
-    gmax = fmaxf(gmax, fmaxf(fmaxf(sqrtf(x.x * x.x + y.x * y.x), sqrtf(x.y * x.y + y.y * y.y)),
-                             fmaxf(sqrtf(x.z * x.z + y.z * y.z), sqrtf(x.w * x.w + y.w * y.w))));
-  }
-  double v[2] = {s.value(), (double)gmax};
+  double v[2] = {sum, sqrt(g2)};
   block_reduce_store<2>(v, 2u, part);
 }
 
@@ -890,17 +875,9 @@ cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pi
 
 int reduce_blocks_1d(size_t n) { return grid_1d(n, 256) < 1024 ? grid_1d(n, 256) : 1024; }
 
-cudaError_t launch_emd_dual(const float* phi, const float* gphi, const float* f0, const float* f1, int N, double* part,
-                            int nblk, cudaStream_t st) {
-  const size_t NN = (size_t)N * N;
-  auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
-  if (NN % 4 == 0 && a16(phi) && a16(gphi) && a16(f0) && a16(f1)) {
-    k_emd_dual4<<<nblk, 256, 0, st>>>(reinterpret_cast<const float4*>(phi), reinterpret_cast<const float4*>(gphi),
-                                      reinterpret_cast<const float4*>(gphi + NN), reinterpret_cast<const float4*>(f0),
-                                      reinterpret_cast<const float4*>(f1), NN / 4, part);
-  } else {
-    k_emd_dual<<<nblk, 256, 0, st>>>(phi, gphi, f0, f1, N, part);
-  }
+cudaError_t launch_emd_dual_hilo(const float* hi, const float* lo, const float* f0, const float* f1, int N,
+                                 double* part, int nblk, cudaStream_t st) {
+  k_emd_dual_hilo<<<nblk, 256, 0, st>>>(hi, lo, f0, f1, N, part);
   return cudaGetLastError();
 }
 

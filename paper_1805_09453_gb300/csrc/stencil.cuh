@@ -42,8 +42,10 @@ cudaError_t launch_rof_fused(const float* gu, const float* u, const float* pin, 
 cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pin, const float* g, float* sout,
                              float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
                              bool gap, int rb, cudaStream_t st);
-cudaError_t launch_emd_dual(const float* phi, const float* gphi, const float* f0, const float* f1, int N, double* part,
-                            int nblk, cudaStream_t st);
+// EMD dual bound inputs (sum phi (f1 - f0), max |D phi|) for phi = hi + lo, two
+// FP32 planes, in FP64 with forward differences.
+cudaError_t launch_emd_dual_hilo(const float* hi, const float* lo, const float* f0, const float* f1, int N,
+                                 double* part, int nblk, cudaStream_t st);
 cudaError_t launch_rof_stats(const float* I, int N, double* part, int nblk, cudaStream_t st);
 cudaError_t launch_sq_dev(const float* I, size_t NN, float mean, double* part, int nblk, cudaStream_t st);
 cudaError_t launch_rof_gap(const float* u, const float* p, const float* I, int N, double* part, int nblk,
