@@ -799,26 +799,27 @@ void finish_report(gp_report* rep, double P, double D) {
   rep->rel_gap = sc > 0 ? (P - D) / sc : 0.0;
 }
 
-// EMD dual bound of a p whose e = -div p is in s->e (section 3.2 with the
-// weak duality of section 2.1): any phi with max |D phi| <= 1 gives the lower
-// bound h^2 sum phi (f1 - f0), so D = h^2 sum phi (f1 - f0) / max(1, max |D phi|)
-// for phi = Lap^{-1} div p.  phi is held as two FP32 planes, phi_hi from the
-// FP32 cosine solve and phi_lo from a second solve of the first one's FP64
-// residual, and both sums are taken in FP64 from the planes: the bound is
-// exact for the phi represented, and FP32 rounding no longer inflates
-// max |D phi| (near the optimum |D phi| = 1 on the whole transport region, so
-// the largest of millions of rounding errors lands in the normalisation).
-// Writes the two partial sums (sum, max) to dst; uses prim and tmp (free
-// between steps); phi_hi + phi_lo is left in phi.
-gp_status emd_dual_enqueue(gp_state s, float* phi, double* part, double* dst, cudaStream_t st) {
+// EMD dual bound of p, whose e = -div p (FP32) is in s->e (section 3.2 with
+// the weak duality of section 2.1): any phi with max |D phi| <= 1 gives the
+// lower bound h^2 sum phi (f1 - f0), so D = h^2 sum phi (f1 - f0) /
+// max(1, max |D phi|) for phi = Lap^{-1} div p.  phi is held as two FP32
+// planes, phi_hi from the FP32 cosine solve of e and phi_lo from a second
+// solve of the residual -div p + Lap phi_hi taken in FP64 from p itself, and
+// both sums are taken in FP64 from the planes: the bound is exact for the phi
+// represented, and FP32 rounding no longer inflates max |D phi| (near the
+// optimum |D phi| = 1 on the whole transport region, so the largest of
+// millions of rounding errors would land in the normalisation).  Writes the
+// two partial sums (sum, max) to dst; uses e, prim and tmp (free between
+// steps; p may be in prim); phi_hi + phi_lo is left in phi.
+gp_status emd_dual_enqueue(gp_state s, const float* p, float* phi, double* part, double* dst, cudaStream_t st) {
   gp_handle h = s->h;
   const int N = s->N;
   const size_t NN = (size_t)N * N;
-  float* r = s->prim;
-  float* lo = s->prim + NN;
+  float* r = s->e;
+  float* lo = s->prim;
   gp_status q = solve(h, N, s->e, phi, s->tmp, 0.0, 1.0, GP_PREC_FP32, true, st);
   if (q != GP_OK) return q;
-  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_helmholtz_residual(s->e, phi, r, N, 0.0, 1.0, st); }));
+  GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_dual_residual(p, phi, r, N, st); }));
   if ((q = solve(h, N, r, lo, s->tmp, 0.0, 1.0, GP_PREC_FP32, true, st)) != GP_OK) return q;
   const int nd = reduce_blocks_1d(NN);
   GP_CUDA(h, plaunch(h, PK_REDUCE, st,
@@ -852,7 +853,7 @@ gp_status state_gap_enqueue(gp_state s, double* dst, cudaStream_t st) {
             }));
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] { return launch_final_reduce(s->part, nb, 2, 0u, dst, st); }));
   // phi = Lap^{-1} div p  <=>  (0 - Lap) phi = -div p = e
-  return emd_dual_enqueue(s, s->phi, s->part + (size_t)nb * 4, dst + 2, st);
+  return emd_dual_enqueue(s, s->p[s->cur], s->phi, s->part + (size_t)nb * 4, dst + 2, st);
 }
 
 void state_gap_finish(gp_state s, const double* v, gp_report* rep) {
@@ -1052,7 +1053,7 @@ gp_status emd_window_dual(gp_state s, long long n, double* D, cudaStream_t st) {
   GP_CUDA(h, plaunch(h, PK_REDUCE, st, [&] {
             return launch_emd_primal(s->m, s->prim, s->f0, s->f1, s->e, N, s->part, nd, st);  // e = -div p_bar
           }));
-  if ((r = emd_dual_enqueue(s, s->phiwin, s->part, h->dres, st)) != GP_OK) return r;
+  if ((r = emd_dual_enqueue(s, s->prim, s->phiwin, s->part, h->dres, st)) != GP_OK) return r;
   if ((r = fetch(h, 2, st)) != GP_OK) return r;
   *D = h->hres[0] / ((double)N * N) / fmax(1.0, h->hres[1]);
   s->partials_valid = false;

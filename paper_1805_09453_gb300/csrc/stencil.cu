@@ -331,6 +331,30 @@ __global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ gq,
   }
 }
 
+// Residual of the dual potential's equation (0 - Lap) phi = -div p in FP64
+// from the stored FP32 arrays: r = -div p + Lap phi, div p with forward
+// differences and zero last slots, Lap the 5-point Neumann stencil, h = 1/N.
+// Taking div p here (not from an FP32 plane of it) makes phi_hi + phi_lo the
+// potential of the p given, to the second solve's accuracy.
+__global__ void __launch_bounds__(256) k_dual_residual(const float* __restrict__ p, const float* __restrict__ phi,
+                                                       float* __restrict__ r, int N) {
+  const size_t NN = (size_t)N * N;
+  const double n = (double)N, n2 = n * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
+    const unsigned row = (unsigned)(idx / (unsigned)N), col = (unsigned)(idx % (unsigned)N);
+    const bool xr = col + 1 < (unsigned)N, xl = col > 0, yd = row + 1 < (unsigned)N, yu = row > 0;
+    const double dv = (((xr ? (double)p[idx] : 0.0) - (xl ? (double)p[idx - 1] : 0.0)) +
+                       ((yd ? (double)p[NN + idx] : 0.0) - (yu ? (double)p[NN + idx - N] : 0.0))) * n;
+    const double c = phi[idx];
+    double lap = 0.0;
+    if (xl) lap += (double)phi[idx - 1] - c;
+    if (xr) lap += (double)phi[idx + 1] - c;
+    if (yu) lap += (double)phi[idx - N] - c;
+    if (yd) lap += (double)phi[idx + N] - c;
+    r[idx] = (float)(n2 * lap - dv);
+  }
+}
+
 // EMD dual bound inputs for a potential held as two FP32 planes,
 // phi = hi + lo: sum phi (f1 - f0) and max |D phi| (forward differences with
 // h = 1/N, zero last slots), all in FP64, so that both are exact for the phi
@@ -874,6 +898,11 @@ cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pi
 }
 
 int reduce_blocks_1d(size_t n) { return grid_1d(n, 256) < 1024 ? grid_1d(n, 256) : 1024; }
+
+cudaError_t launch_dual_residual(const float* p, const float* phi, float* r, int N, cudaStream_t st) {
+  k_dual_residual<<<grid_1d((size_t)N * N, 256), 256, 0, st>>>(p, phi, r, N);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_emd_dual_hilo(const float* hi, const float* lo, const float* f0, const float* f1, int N,
                                  double* part, int nblk, cudaStream_t st) {

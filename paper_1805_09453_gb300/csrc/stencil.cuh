@@ -42,6 +42,8 @@ cudaError_t launch_rof_fused(const float* gu, const float* u, const float* pin, 
 cudaError_t launch_emd_fused(const float* gq, const float* sin_, const float* pin, const float* g, float* sout,
                              float* pout, float* d, float* m, float* e, double* part, const EmdParams& P, bool vec,
                              bool gap, int rb, cudaStream_t st);
+// r = -div p + Lap phi in FP64 (the dual potential's residual), stored FP32.
+cudaError_t launch_dual_residual(const float* p, const float* phi, float* r, int N, cudaStream_t st);
 // EMD dual bound inputs (sum phi (f1 - f0), max |D phi|) for phi = hi + lo, two
 // FP32 planes, in FP64 with forward differences.
 cudaError_t launch_emd_dual_hilo(const float* hi, const float* lo, const float* f0, const float* f1, int N,

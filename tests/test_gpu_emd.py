@@ -268,3 +268,48 @@ def test_emd_1024_to_gap_certified(h):
     assert rep["dual"] <= rep["primal_feasible"]
     assert rep["mass_residual_feasible"] < 1e-6
     assert abs(rep["primal_feasible"] - rep["primal"]) <= 1e-5 * rep["primal"]
+
+
+@pytest.mark.parametrize("N", [256, 1024, 2048])
+def test_emd_dual_bound_of_a_given_p_matches_the_oracle(h, N):
+    """The dual bound h^2 sum phi (f1 - f0) / max(1, max |D phi|), phi =
+    Lap^-1 div p, for a p that is the gradient of phi = 0.6 x + 0.8 y: |D phi|
+    = 1 on the whole grid, the situation of an EMD optimum's transport region,
+    where the largest of N^2 rounding errors lands in the normalisation.  The
+    library holds phi as two FP32 planes and takes the sums in FP64, so its
+    bound equals the FP64 oracle's for the same (FP32) p to within 1e-8
+    relative; an FP32 max |grad phi| is off by a few 1e-6 at 1024^2."""
+    from paper_1805_09453_gb300 import gprox
+
+    hh = 1.0 / N
+    x = (np.arange(N) + 0.5) * hh
+    phi = 0.6 * x[None, :] + 0.8 * x[:, None]
+    px, py = (a.astype(np.float32) for a in O.grad(phi, hh))
+    f0, f1 = (a.astype(np.float32) for a in _pair(N, 3))
+    ref, _, sc = O.emd_dual(px.astype(np.float64), py.astype(np.float64), f0.astype(np.float64),
+                            f1.astype(np.float64))
+    assert abs(sc - 1.0) < 1e-6  # the normalisation is the rounding of p itself
+    p = _t(np.stack([px, py]))
+    s = gprox.State(h, "emd", N, f0=_t(f0), f1=_t(f1), tau=1.0, sigma=1.0, primal0=torch.zeros_like(p), p0=p,
+                    pbar0=p)
+    D = s.gap()["dual"]
+    s.close()
+    assert abs(D - ref) <= 1e-8 * abs(ref), (D, ref, (D - ref) / ref)
+
+
+def test_emd_dual_bound_of_an_oracle_iterate_matches_the_oracle(h):
+    """The same for the dual iterate of 400 oracle steps at 64^2 (structured p,
+    |p| = 1 on part of the grid)."""
+    from paper_1805_09453_gb300 import gprox
+
+    N = 64
+    f0, f1 = (a.astype(np.float32).astype(np.float64) for a in _pair(N, 4))
+    ref = O.emd_solve(f0, f1, n_iters=400)
+    px, py = ref["px"].astype(np.float32), ref["py"].astype(np.float32)
+    D_ref, _, _ = O.emd_dual(px.astype(np.float64), py.astype(np.float64), f0, f1)
+    p = _t(np.stack([px, py]))
+    s = gprox.State(h, "emd", N, f0=_t(f0), f1=_t(f1), tau=1.0, sigma=1.0, primal0=torch.zeros_like(p), p0=p,
+                    pbar0=p)
+    D = s.gap()["dual"]
+    s.close()
+    assert abs(D - D_ref) <= 1e-8 * abs(D_ref), (D, D_ref)
