@@ -52,37 +52,50 @@ def coarse_opts(tol: float = 1e-4, max_iters: int = 100000, gap_every: int = 50)
 
 
 def generate(h: gprox.Handle, N: int, seeds, tol: float = 1e-6, max_iters: int = 40000, gap_every: int = 50,
-             coarse_factor: int = 4, coarse_tol: float = 1e-4, verbose: bool = False):
-    """Solve each pair with the plain method and compute its coarse-grid prior;
-    returns f0, f1, phi*, prior (S, N, N), the iteration counts and the gaps."""
+             coarse_factor: int = 4, coarse_tol: float = 1e-4, verbose: bool = False, warm: bool = False):
+    """Solve each pair and compute its coarse-grid prior; returns f0, f1,
+    phi*, prior (S, N, N), the iteration counts and the gaps.  The solve
+    starts from zero, or with warm from the prior (emd_solve_learned with a
+    network whose output is its prior: the same certified stop, fewer
+    iterations on large grids)."""
     f0, f1 = pairs(N, seeds)
     phi = torch.empty_like(f0)
     prior = torch.zeros_like(f0)
     torch.cuda.synchronize()
     with torch.cuda.stream(torch.cuda.Stream()):  # a non-default stream: the solves replay CUDA graphs
-        out = _generate(h, N, f0, f1, phi, prior, tol, max_iters, gap_every, coarse_factor, coarse_tol, verbose)
+        out = _generate(h, N, f0, f1, phi, prior, tol, max_iters, gap_every, coarse_factor, coarse_tol, verbose,
+                        warm)
     torch.cuda.synchronize()
     return out
 
 
-def _generate(h, N, f0, f1, phi, prior, tol, max_iters, gap_every, coarse_factor, coarse_tol, verbose):
+def _generate(h, N, f0, f1, phi, prior, tol, max_iters, gap_every, coarse_factor, coarse_tol, verbose, warm):
     seeds = range(f0.shape[0])
     m = torch.empty((2, N, N), device=f0.device)
     p = torch.empty((2, N, N), device=f0.device)
     o = gprox.default_opts(max_iters=max_iters, tol_rel_gap=tol, gap_every=gap_every, use_graph=1)
     oc = coarse_opts(coarse_tol)
+    base = None
+    if warm and coarse_factor:
+        base = gprox.Cnn(h, 1, seed=0)
+        base.set_params(np.zeros(base.num_params, np.float32))  # output = prior
     iters, gaps = [], []
     for i in range(len(seeds)):
-        st, rep = gprox.emd_solve(h, f0[i], f1[i], m, p, phi[i], o)
+        if base is not None:
+            st, rep = gprox.emd_solve_learned(h, base, f0[i], f1[i], m, p, phi[i], o, coarse_factor, oc)
+        else:
+            st, rep = gprox.emd_solve(h, f0[i], f1[i], m, p, phi[i], o)
         h.check(st, allow=(gprox.GP_OK, gprox.GP_ERR_MAXITER))
         iters.append(rep["iters"])
         gaps.append(rep["rel_gap"])
         if coarse_factor:
             st, _, _ = gprox.emd_coarse_start(h, f0[i], f1[i], coarse_factor, oc, phi=prior[i])
             h.check(st, allow=(gprox.GP_OK, gprox.GP_ERR_MAXITER))
-        if verbose and (i + 1) % 32 == 0:
+        if verbose and ((i + 1) % 32 == 0 or (base is not None and (i + 1) % 4 == 0)):
             print(f"generated {i + 1}/{len(seeds)} pairs (median iterations {statistics.median(iters)})", flush=True)
     torch.cuda.synchronize()
+    if base is not None:
+        base.close()
     return f0, f1, phi, prior, iters, gaps
 
 
@@ -179,18 +192,34 @@ def augment(f0, f1, phi, prior, g: int):
     return [t.contiguous() for t in out]
 
 
+def crop_sample(f0, f1, phi, prior, y: int, x: int, c: int):
+    """The c x c window at (y, x) of one sample.  The network's inputs are
+    pointwise in (f0, f1, prior) and its output is made mean-free, so a window
+    of a large grid is a sample with that grid's local statistics (features
+    as many cells wide as there); the target is made mean-free in the window."""
+    out = [t[y:y + c, x:x + c] for t in (f0, f1, phi, prior)]
+    out[2] = out[2] - out[2].double().mean().float()
+    return out
+
+
 def train(net: gprox.Cnn, f0, f1, phi, prior, steps: int, batch: int, lr: float, seed: int = 0,
-          log_every: int = 50, lr_final: float | None = None, augment_data: bool = True):
-    """Adam on random mini-batches (random symmetries when augment_data);
-    cosine decay of the step size to lr_final."""
+          log_every: int = 50, lr_final: float | None = None, augment_data: bool = True, crop: int = 0):
+    """Adam on random mini-batches (random symmetries when augment_data; with
+    crop, random crop x crop windows at multiples of 8); cosine decay of the
+    step size to lr_final."""
     rng = np.random.default_rng(seed)
-    S = f0.shape[0]
+    S, N = f0.shape[0], f0.shape[-1]
     lr_final = lr * 0.05 if lr_final is None else lr_final
     hist = []
     for k in range(steps):
-        idx = rng.choice(S, size=min(batch, S), replace=False)
+        idx = rng.choice(S, size=min(batch, S), replace=False) if not crop else rng.integers(0, S, size=batch)
         gs = rng.integers(0, 16, size=len(idx)) if augment_data else np.zeros(len(idx), int)
-        smp = [augment(f0[i], f1[i], phi[i], prior[i], int(g)) for i, g in zip(idx, gs)]
+        if crop:
+            yx = rng.integers(0, (N - crop) // 8 + 1, size=(len(idx), 2)) * 8
+            smp = [augment(*crop_sample(f0[i], f1[i], phi[i], prior[i], int(y), int(x), crop), int(g))
+                   for i, g, (y, x) in zip(idx, gs, yx)]
+        else:
+            smp = [augment(f0[i], f1[i], phi[i], prior[i], int(g)) for i, g in zip(idx, gs)]
         want = (k % log_every == 0) or k == steps - 1
         L, _ = net.loss_grad([a[0] for a in smp], [a[1] for a in smp], [a[2] for a in smp], [a[3] for a in smp],
                              want_loss=want)
@@ -298,6 +327,9 @@ def main(argv=None):
     ap.add_argument("--test", type=int, default=64, help="held-out pairs (seeds 1e6..)")
     ap.add_argument("--data-tol", type=float, default=1e-6)
     ap.add_argument("--data-max-iters", type=int, default=40000)
+    ap.add_argument("--data-warm", action="store_true", help="solve the training pairs from the coarse start")
+    ap.add_argument("--crop", type=int, default=0, help="train on random crop x crop windows (0: whole grids)")
+    ap.add_argument("--eval-gap-every", type=int, default=10, help="gap checks of the evaluation (0: adaptive)")
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
@@ -322,23 +354,28 @@ def main(argv=None):
     if a.problem == "rof":
         return _main_rof(a, h, net, rep)
     t0 = time.perf_counter()
-    f0, f1, phi, pri, it, gaps = generate(h, a.N, range(a.train), a.data_tol, a.data_max_iters,
-                                          coarse_factor=a.coarse, coarse_tol=a.coarse_tol, verbose=True)
+    dge = 0 if a.data_warm else 50
+    f0, f1, phi, pri, it, gaps = generate(h, a.N, range(a.train), a.data_tol, a.data_max_iters, dge,
+                                          coarse_factor=a.coarse, coarse_tol=a.coarse_tol, verbose=True,
+                                          warm=a.data_warm)
     rep["data"] = {"pairs": a.train, "seconds": time.perf_counter() - t0, "median_iters": statistics.median(it),
-                   "max_gap": max(gaps)}
+                   "max_gap": max(gaps), "warm": a.data_warm, "crop": a.crop}
     g0, g1, gphi, gpri, _, _ = generate(h, a.N, range(TEST_SEED0, TEST_SEED0 + a.test), a.data_tol,
-                                        a.data_max_iters, coarse_factor=a.coarse, coarse_tol=a.coarse_tol)
-    rep["test_loss_init"] = test_loss(net, g0, g1, gphi, gpri)
+                                        a.data_max_iters, dge, coarse_factor=a.coarse, coarse_tol=a.coarse_tol,
+                                        warm=a.data_warm)
+    tb = 1 if a.N > 1024 else 8
+    rep["test_loss_init"] = test_loss(net, g0, g1, gphi, gpri, tb)
     t0 = time.perf_counter()
-    hist = train(net, f0, f1, phi, pri, a.steps, a.batch, a.lr, a.seed)
+    hist = train(net, f0, f1, phi, pri, a.steps, a.batch, a.lr, a.seed, crop=a.crop)
     print(f"trained {a.steps} steps in {time.perf_counter() - t0:.1f} s, loss {hist[-1][1]:.4g}", flush=True)
     rep["train"] = {"steps": a.steps, "batch": a.batch, "lr": a.lr, "seconds": time.perf_counter() - t0,
                     "loss": hist[-1][1], "history": hist}
-    rep["test_loss"] = test_loss(net, g0, g1, gphi, gpri)
+    rep["test_loss"] = test_loss(net, g0, g1, gphi, gpri, tb)
     rep["network_seconds"] = network_cost(net, g0, g1, gpri)
     if a.out:
-        np.savez(a.out, w=net.get_params(), C=a.C, N=a.N, coarse=a.coarse)
-    rows = evaluate(h, net, g0, g1, a.tol, coarse_factor=a.coarse, coarse_tol=a.coarse_tol)
+        np.savez(a.out, w=net.get_params(), C=a.C, N=a.N, coarse=a.coarse, crop=a.crop)
+    rows = evaluate(h, net, g0, g1, a.tol, max_iters=max(40000, a.data_max_iters), gap_every=a.eval_gap_every,
+                    coarse_factor=a.coarse, coarse_tol=a.coarse_tol)
     rep["eval"] = summarize(rows)
     rep["eval"]["tol"] = a.tol
     rep["rows"] = rows
