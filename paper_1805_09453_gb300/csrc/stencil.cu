@@ -331,50 +331,97 @@ __global__ void __launch_bounds__(128) k_emd_fused(const float* __restrict__ gq,
   }
 }
 
-// Residual of the dual potential's equation (0 - Lap) phi = -div p in FP64
-// from the stored FP32 arrays: r = -div p + Lap phi, div p with forward
-// differences and zero last slots, Lap the 5-point Neumann stencil, h = 1/N.
+// Double-FP32 arithmetic for the dual bound's per-point work: a value is a
+// pair hi + lo (|lo| <= ulp(hi) / 2, about 48 significant bits) built from
+// the error-free transformations (Knuth's TwoSum and the FMA form of
+// TwoProduct), with the intrinsics' explicit rounding so that no addition
+// or product is contracted or reassociated.  GB300's FP64 rate is a small
+// fraction of its FP32 rate, and FP64 per grid point made the EMD gap check
+// cost more than an iteration.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_fast(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = df_two_sum(x.hi, y.hi);
+  return df_fast(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ DF df_mul(DF x, float b) {  // x * b
+  const float p = __fmul_rn(x.hi, b);
+  return df_fast(p, __fmaf_rn(x.lo, b, __fmaf_rn(x.hi, b, -p)));
+}
+__device__ __forceinline__ DF df_sq(DF x) {  // x * x
+  const float p = __fmul_rn(x.hi, x.hi);
+  return df_fast(p, __fmaf_rn(__fmul_rn(2.f, x.hi), x.lo, __fmaf_rn(x.hi, x.hi, -p)));
+}
+
+// Residual of the dual potential's equation (0 - Lap) phi = -div p, to about
+// 48 bits from the stored FP32 arrays: r = -div p + Lap phi with div p by
+// forward differences with zero last slots and Lap the 5-point Neumann
+// stencil (h = 1/N), i.e. r = N (N l - d) with l = sum (phi_nb - phi) over
+// the neighbours and d = (px - px_left) + (py - py_up).  Neighbouring
+// differences are exact pairs, the sums are pair sums, and r is rounded once.
 // Taking div p here (not from an FP32 plane of it) makes phi_hi + phi_lo the
 // potential of the p given, to the second solve's accuracy.
 __global__ void __launch_bounds__(256) k_dual_residual(const float* __restrict__ p, const float* __restrict__ phi,
                                                        float* __restrict__ r, int N) {
   const size_t NN = (size_t)N * N;
-  const double n = (double)N, n2 = n * n;
+  const float n = (float)N;  // exact for N <= 2^24
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
     const unsigned row = (unsigned)(idx / (unsigned)N), col = (unsigned)(idx % (unsigned)N);
     const bool xr = col + 1 < (unsigned)N, xl = col > 0, yd = row + 1 < (unsigned)N, yu = row > 0;
-    const double dv = (((xr ? (double)p[idx] : 0.0) - (xl ? (double)p[idx - 1] : 0.0)) +
-                       ((yd ? (double)p[NN + idx] : 0.0) - (yu ? (double)p[NN + idx - N] : 0.0))) * n;
-    const double c = phi[idx];
-    double lap = 0.0;
-    if (xl) lap += (double)phi[idx - 1] - c;
-    if (xr) lap += (double)phi[idx + 1] - c;
-    if (yu) lap += (double)phi[idx - N] - c;
-    if (yd) lap += (double)phi[idx + N] - c;
-    r[idx] = (float)(n2 * lap - dv);
+    const DF dv = df_add(df_two_sum(xr ? p[idx] : 0.f, -(xl ? p[idx - 1] : 0.f)),
+                         df_two_sum(yd ? p[NN + idx] : 0.f, -(yu ? p[NN + idx - N] : 0.f)));
+    const float c = phi[idx];
+    DF lap = {0.f, 0.f};
+    if (xl) lap = df_add(lap, df_two_sum(phi[idx - 1], -c));
+    if (xr) lap = df_add(lap, df_two_sum(phi[idx + 1], -c));
+    if (yu) lap = df_add(lap, df_two_sum(phi[idx - N], -c));
+    if (yd) lap = df_add(lap, df_two_sum(phi[idx + N], -c));
+    const DF t = df_add(df_mul(lap, n), {-dv.hi, -dv.lo});
+    const DF rr = df_mul(t, n);
+    r[idx] = __fadd_rn(rr.hi, rr.lo);
   }
 }
 
 // EMD dual bound inputs for a potential held as two FP32 planes,
-// phi = hi + lo: sum phi (f1 - f0) and max |D phi| (forward differences with
-// h = 1/N, zero last slots), all in FP64, so that both are exact for the phi
-// the planes represent (weak duality then holds for the bound as computed).
+// phi = hi + lo: sum phi (f1 - f0) and max |D phi|^2 (forward differences,
+// h = 1/N, zero last slots), both in pair arithmetic: the neighbouring
+// differences of each plane are exact pairs and the squares and sums keep
+// about 48 bits, so the maximum is within ~1e-13 relative and is raised by
+// 2^-40 to bound it from above.  Both inputs of the bound are then exact,
+// or an upper bound, for the phi the planes represent, and weak duality
+// holds for the bound as computed.
 __global__ void __launch_bounds__(256) k_emd_dual_hilo(const float* __restrict__ hi, const float* __restrict__ lo,
                                                        const float* __restrict__ f0, const float* __restrict__ f1,
                                                        int N, double* __restrict__ part) {
-  double sum = 0.0, g2 = 0.0;
+  DF sum = {0.f, 0.f}, g2m = {0.f, 0.f};
   const size_t NN = (size_t)N * N;
-  const double n = (double)N;
+  const float n = (float)N;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < NN; idx += (size_t)gridDim.x * blockDim.x) {
     const unsigned row = (unsigned)(idx / (unsigned)N), col = (unsigned)(idx % (unsigned)N);
-    const double h0 = hi[idx], l0 = lo[idx];
-    sum += (h0 + l0) * ((double)f1[idx] - (double)f0[idx]);
-    double gx = 0.0, gy = 0.0;
-    if (col + 1 < (unsigned)N) gx = n * (((double)hi[idx + 1] - h0) + ((double)lo[idx + 1] - l0));
-    if (row + 1 < (unsigned)N) gy = n * (((double)hi[idx + N] - h0) + ((double)lo[idx + N] - l0));
-    g2 = fmax(g2, gx * gx + gy * gy);
+    const float h0 = hi[idx], l0 = lo[idx];
+    const DF t = df_two_sum(f1[idx], -f0[idx]);
+    const float pr = __fmul_rn(h0, t.hi);
+    const float pe = __fmaf_rn(h0, t.lo, __fmaf_rn(l0, t.hi, __fmaf_rn(h0, t.hi, -pr)));
+    sum = df_add(sum, df_fast(pr, pe));
+    DF gx = {0.f, 0.f}, gy = {0.f, 0.f};
+    if (col + 1 < (unsigned)N)
+      gx = df_mul(df_add(df_two_sum(hi[idx + 1], -h0), df_two_sum(lo[idx + 1], -l0)), n);
+    if (row + 1 < (unsigned)N)
+      gy = df_mul(df_add(df_two_sum(hi[idx + N], -h0), df_two_sum(lo[idx + N], -l0)), n);
+    const DF g2 = df_add(df_sq(gx), df_sq(gy));
+    if (g2.hi > g2m.hi || (g2.hi == g2m.hi && g2.lo > g2m.lo)) g2m = g2;
   }
-  double v[2] = {sum, sqrt(g2)};
+  double v[2] = {(double)sum.hi + (double)sum.lo, sqrt((double)g2m.hi + (double)g2m.lo) * (1.0 + 0x1p-40)};
   block_reduce_store<2>(v, 2u, part);
 }
 
