@@ -1065,12 +1065,17 @@ gp_status emd_window_dual(gp_state s, long long n, double* D, cudaStream_t st) {
 // and over averages of those p's (windows that open once the gap is within
 // 30 x tol and restart whenever the iteration count has doubled since their
 // start); each is a lower bound of the optimum, and the last iterate's p
-// lags it.  A candidate (gap with the best bound within 2 x tol: the
-// corrected primal is usually a little below the stored one) is certified
-// at most every 100 iterations unless the plain gap already meets tol; the
-// solve stops once the certified gap does.
+// lags it.  The current flux is certified (its corrected primal taken) at
+// every window restart and whenever it is a candidate: the stored primal,
+// less the rounding cost P - P(m~) the last certificate measured, within
+// 2 x tol of the best bound (at most every 100 iterations unless within
+// tol).  The solve stops once a certified gap meets tol.  The offset matters:
+// the stored FP32 flux's primal can exceed the corrected one by more than
+// tol (2e-5 relative on some 4096^2 pairs), which would keep every candidate
+// test from passing.
 struct EmdStop {
   double d_best = -INFINITY;
+  double p_off = 0.0;  // P - P(m~) at the last certificate
   int win_start = -1, last_cert = -1000000;
   long long win_n = 0;
 };
@@ -1097,11 +1102,13 @@ gp_status emd_stop_check(gp_state s, EmdStop& z, double tol, gp_report* rep, cud
   *stop = false;
   if (rep->dual > z.d_best) z.d_best = rep->dual;
   if (z.win_start < 0 && rep->rel_gap <= 30.0 * tol) z.win_start = s->n;
+  bool restarted = false;
   if (z.win_start >= 0) {
     if (s->n >= 2 * z.win_start && z.win_n > 0) {  // restart the window
       if ((r = emd_close_window(s, z, st)) != GP_OK) return r;
       z.win_n = 0;
       z.win_start = s->n;
+      restarted = true;
     }
     if (!s->pwin) GP_CUDA(h, cudaMalloc(&s->pwin, 2 * NN * sizeof(double)));
     if (!s->phiwin) GP_CUDA(h, cudaMalloc(&s->phiwin, NN * sizeof(float)));
@@ -1111,10 +1118,12 @@ gp_status emd_stop_check(gp_state s, EmdStop& z, double tol, gp_report* rep, cud
   }
   rep->dual = z.d_best;
   rep->rel_gap = rel_gap_of(rep->primal, z.d_best);
-  if (rep->rel_gap <= 2.0 * tol && (rep->rel_gap <= tol || s->n - z.last_cert >= 100)) {
+  const double g_est = rel_gap_of(rep->primal - z.p_off, z.d_best);
+  if (restarted || (g_est <= 2.0 * tol && (g_est <= tol || s->n - z.last_cert >= 100))) {
     z.last_cert = s->n;
-    if ((r = emd_close_window(s, z, st)) != GP_OK) return r;
+    if (!restarted && (r = emd_close_window(s, z, st)) != GP_OK) return r;
     if ((r = emd_certify(s, rep, st)) != GP_OK) return r;
+    z.p_off = fmax(0.0, rep->primal - rep->primal_feasible);
     rep->dual = z.d_best;
     rep->rel_gap = rel_gap_of(rep->primal, z.d_best);
     rep->rel_gap_feasible = rel_gap_of(rep->primal_feasible, z.d_best);
