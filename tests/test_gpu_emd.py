@@ -315,3 +315,21 @@ def test_emd_dual_bound_of_an_oracle_iterate_matches_the_oracle(h):
     D = s.gap()["dual"]
     s.close()
     assert D_ref * (1 - 1e-8) <= D <= D_ref * (1 + 1e-9), (D, D_ref, (D - D_ref) / D_ref)
+
+
+def test_emd_4096_pair_whose_stored_flux_costs_more_than_tol_certifies(h):
+    """A 4096^2 pair whose stored FP32 flux costs 2e-5 relative in primal
+    over its corrected flux, twice the tolerance: the stop rule judges its
+    candidates on the corrected primal (and certifies at every window
+    restart), so it stops on a certified 1e-5.  Judged on the stored primal
+    it never became a candidate and ran past 100 000 iterations."""
+    from paper_1805_09453_gb300 import gprox
+
+    N = 4096
+    f0, f1 = _pair(N, 1000002)
+    m = torch.empty((2, N, N), device="cuda")
+    st, rep = gprox.emd_solve(h, _t(f0), _t(f1), m, opts=gprox.default_opts(max_iters=40000, tol_rel_gap=1e-5,
+                                                                             gap_every=0))
+    assert st == gprox.GP_OK and rep["iters"] < 40000, rep
+    assert rep["rel_gap_feasible"] <= 1e-5 and rep["dual"] <= rep["primal_feasible"], rep
+    assert rep["primal"] - rep["primal_feasible"] > 1e-5 * rep["primal_feasible"], rep
