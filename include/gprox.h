@@ -104,7 +104,12 @@ typedef struct gp_report {
   int iters;             /* iterations run */
   int status;            /* gp_status of the solve */
   double primal;         /* P at the last check: ROF energy or EMD cost sum |m| h^2 */
-  double dual;           /* D at the last check (a lower bound on the optimum) */
+  double dual;           /* D at the last check (a lower bound on the optimum).  EMD: for a p,
+                            D = h^2 sum phi (f1 - f0) / max(1, max |D phi|), phi = Lap^{-1} div p
+                            held as two FP32 planes (an FP32 solve plus a solve of its residual,
+                            taken from p itself), the sum and max |D phi| (forward differences)
+                            in double-FP32 pair arithmetic, the max raised by 2^-40 to bound its
+                            rounding: a valid bound for the phi the planes hold */
   double rel_gap;        /* (P - D) / max(|P|, |D|) */
   double mass_residual;  /* EMD: h^2 sum |div m - (f0 - f1)| / h^2 sum |f0 - f1| (FP32 terms at a
                             plain check, FP64 at a certified one, see below); ROF: 0 */
@@ -112,8 +117,8 @@ typedef struct gp_report {
   double seconds;        /* host wall time of the call */
   /* Feasibility certificate (section 3.2: P(m) bounds the optimum from above
    * only for an m with div m = f0 - f1 exactly; D bounds it from below for
-   * any p).  EMD: at the final check, and at every check whose rel_gap met
-   * tol_rel_gap, the residual rho = (f0 - f1) - div m of the returned FP32 m
+   * any p).  EMD: at the final check, and at the checks the stop test picks
+   * (below), the residual rho = (f0 - f1) - div m of the returned FP32 m
    * is evaluated in FP64 (mass_residual then reports it), c = Lap^{-1} rho is
    * solved, and m~ = m + grad c is the corrected, feasible flux:
    *   primal_feasible        = h^2 sum |m~|  (>= the optimum)
@@ -128,7 +133,11 @@ typedef struct gp_report {
    * within 30 x tol_rel_gap and restarts whenever the iteration count has
    * doubled since it opened), and rel_gap / rel_gap_feasible use it; the
    * last iterate's own dual value lags the optimum far more than its primal
-   * does.  ROF (unconstrained): primal, rel_gap and 0. */
+   * does.  The flux is certified at every window restart and whenever the
+   * stored primal, less the offset primal - primal_feasible of the last
+   * certificate, is within 2 x tol_rel_gap of that bound (at most every 100
+   * iterations unless within tol_rel_gap).  ROF (unconstrained): primal,
+   * rel_gap and 0. */
   double primal_feasible;
   double rel_gap_feasible;
   double mass_residual_feasible;
