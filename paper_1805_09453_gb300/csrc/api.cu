@@ -1065,8 +1065,11 @@ gp_status emd_window_dual(gp_state s, long long n, double* D, cudaStream_t st) {
 // and over averages of those p's (windows that open once the gap is within
 // 30 x tol and restart whenever the iteration count has doubled since their
 // start); each is a lower bound of the optimum, and the last iterate's p
-// lags it.  The current flux is certified (its corrected primal taken) at
-// every window restart and whenever it is a candidate: the stored primal,
+// lags it.  The open window's bound is also taken whenever the window has
+// grown by a quarter since it was last taken (at least 100 iterations and 4
+// samples apart), so that a window can certify before it restarts.  The
+// current flux is certified (its corrected primal taken) at every window
+// evaluation and whenever it is a candidate: the stored primal,
 // less the rounding cost P - P(m~) the last certificate measured, within
 // 2 x tol of the best bound (at most every 100 iterations unless within
 // tol).  The solve stops once a certified gap meets tol.  The offset matters:
@@ -1077,6 +1080,7 @@ struct EmdStop {
   double d_best = -INFINITY;
   double p_off = 0.0;  // P - P(m~) at the last certificate
   int win_start = -1, last_cert = -1000000;
+  int win_eval = 0;    // iteration count from which the open window is taken again
   long long win_n = 0;
 };
 
@@ -1102,26 +1106,33 @@ gp_status emd_stop_check(gp_state s, EmdStop& z, double tol, gp_report* rep, cud
   *stop = false;
   if (rep->dual > z.d_best) z.d_best = rep->dual;
   if (z.win_start < 0 && rep->rel_gap <= 30.0 * tol) z.win_start = s->n;
-  bool restarted = false;
+  bool fresh = false;
   if (z.win_start >= 0) {
     if (s->n >= 2 * z.win_start && z.win_n > 0) {  // restart the window
       if ((r = emd_close_window(s, z, st)) != GP_OK) return r;
       z.win_n = 0;
       z.win_start = s->n;
-      restarted = true;
+      z.win_eval = s->n + 100;
+      fresh = true;
     }
     if (!s->pwin) GP_CUDA(h, cudaMalloc(&s->pwin, 2 * NN * sizeof(double)));
     if (!s->phiwin) GP_CUDA(h, cudaMalloc(&s->phiwin, NN * sizeof(float)));
     if (z.win_n == 0) GP_CUDA(h, cudaMemsetAsync(s->pwin, 0, 2 * NN * sizeof(double), st));
     GP_CUDA(h, plaunch(h, PK_SETUP, st, [&] { return launch_accumulate(s->pwin, s->p[s->cur], 2 * NN, st); }));
     ++z.win_n;
+    if (!fresh && z.win_n >= 4 && s->n >= z.win_eval) {  // take the open window's bound
+      if ((r = emd_close_window(s, z, st)) != GP_OK) return r;
+      const int grow = (s->n - z.win_start) / 4;
+      z.win_eval = s->n + (grow > 100 ? grow : 100);
+      fresh = true;
+    }
   }
   rep->dual = z.d_best;
   rep->rel_gap = rel_gap_of(rep->primal, z.d_best);
   const double g_est = rel_gap_of(rep->primal - z.p_off, z.d_best);
-  if (restarted || (g_est <= 2.0 * tol && (g_est <= tol || s->n - z.last_cert >= 100))) {
+  if (fresh || (g_est <= 2.0 * tol && (g_est <= tol || s->n - z.last_cert >= 100))) {
     z.last_cert = s->n;
-    if (!restarted && (r = emd_close_window(s, z, st)) != GP_OK) return r;
+    if (!fresh && (r = emd_close_window(s, z, st)) != GP_OK) return r;
     if ((r = emd_certify(s, rep, st)) != GP_OK) return r;
     z.p_off = fmax(0.0, rep->primal - rep->primal_feasible);
     rep->dual = z.d_best;
