@@ -144,3 +144,24 @@ def test_translated_discs_near_the_translation_length():
     f0, f1 = synth.translated_discs(48)
     st = O.emd_solve(f0, f1, tol=1e-4, max_iters=20000)
     assert abs(st["primal"] - g["emd_distance"]) < 0.03 * g["emd_distance"]
+
+
+@pytest.mark.parametrize("N", [16, 64])
+def test_dual_of_a_gradient_field_is_its_potential(N):
+    """Closed form of the dual bound (weak duality, section 2.1, for the
+    constraint of section 3.2): for p = D phi with phi = 0.6 x + 0.8 y at the
+    cell centres (forward differences, zero last slots), div p is the
+    5-point Neumann Laplacian of phi, so Lap^-1 div p is phi less its mean,
+    max |D phi| = |(0.6, 0.8)| = 1 (no normalisation), and the bound is
+    h^2 sum (phi - mean) (f1 - f0)."""
+    h = 1.0 / N
+    x = (np.arange(N) + 0.5) * h
+    phi = 0.6 * x[None, :] + 0.8 * x[:, None]
+    px, py = O.grad(phi, h)
+    f0, f1 = synth.gaussian_mixture_pair(N, 7)
+    D, pot, s = O.emd_dual(px, py, f0, f1)
+    c = phi - phi.mean()
+    assert np.abs(pot - c).max() < 1e-12
+    assert abs(s - 1.0) < 1e-12
+    exact = h * h * float(np.sum(c * (f1.astype(np.float64) - f0.astype(np.float64))))
+    assert abs(D - exact) <= 1e-12 * abs(exact)
